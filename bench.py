@@ -1,0 +1,380 @@
+"""Benchmark: stable GPU merge sort of 2^28 uint32 keys under five distributions.
+
+One step = one out-of-place sort of each of the five 2^28-key arrays
+(uniform, already sorted, reverse sorted, 16 distinct values, Zipf(1.1) over
+2^20 ranks), keys only: the tile sort plus ceil(log2(2^28 / T)) merge passes,
+all in the library's kernels.  value = keys sorted per second (Gkeys/s) over
+the timed steps, inputs resident in HBM.  Each input is 1 GiB, larger than
+the 126 MB L2, so no L2 flush is needed between steps.
+
+Printed as one JSON line on rank 0.  Also reported:
+  e2e           the same sort through msort_sort_host: pinned host keys in,
+                host keys out, copies inside the timed region;
+  roofline      the merge pass (the dominant kernel) against measured HBM
+                copy bandwidth, its duration from CUDA events on its stream;
+  cpu_baseline  the CPU oracle (chunked merge sort with a pairwise merge tree
+                on every host core) on a bounded sample of the same inputs;
+  clocks        nvidia-smi samples taken during the timed region.
+
+--impl reference times the CPU oracle itself on the same metric (there is no
+GPU reference implementation of this method).
+Multi-GPU (torchrun): every rank sorts its own copy of the workload
+(replicas; the sort has no cross-GPU exchange), value = all ranks' keys /
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 1 << 28
+DISTS = ("uniform", "sorted", "reverse", "distinct16", "zipf")
+METRIC = "Gkeys/s sorted (stable merge sort, 2^28 uint32 keys x 5 distributions)"
+UNIT = "Gkeys/s"
+NOMINAL_HBM_GBS = 8000.0
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    for rel in ("paper_2211_16479_gb300/csrc/sort_kernels.cuh",):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic():
+    """dram bytes per merge-pass launch from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_merge_pass_u32_2p28.txt")
+    try:
+        fields = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    fields[k.strip()] = v.strip()
+        if fields.get("kernel_source_sha256_16") != _kernel_source_hash():
+            return None
+        return float(fields["dram_bytes_per_launch_full_size"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    mx = max(mx, float(parts[1]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[4:8]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_rate(sample_keys, seconds_target=12.0):
+    """Time the oracle's chunked merge sort on all host cores; returns
+    (Gkeys/s, cores, description)."""
+    import numpy as np
+
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    lib = oracle.load()
+    total_keys, total_t, reps = 0, 0.0, 0
+    while total_t < seconds_target or reps < 1:
+        for a in sample_keys:
+            work = np.array(a, copy=True)
+            t0 = time.perf_counter()
+            oracle.sort_inplace(work, None, workers=cores, lib=lib)
+            total_t += time.perf_counter() - t0
+            total_keys += len(a)
+        reps += 1
+        if reps >= 50:
+            break
+    return total_keys / total_t / 1e9, cores, reps
+
+
+def run_reference(args):
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import synth
+    m = 1 << 22
+    samples = [synth.u32_distribution(d, m, 1) for d in DISTS]
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm state; warm-up steps are not needed
+    cores = len(os.sched_getaffinity(0))
+    import oracle
+    lib = oracle.load()
+    t_total, keys = 0.0, 0
+    for _ in range(args.steps):
+        for a in samples:
+            w = np.array(a, copy=True)
+            t0 = time.perf_counter()
+            oracle.sort_inplace(w, None, workers=cores, lib=lib)
+            t_total += time.perf_counter() - t0
+            keys += m
+    v = keys / t_total / 1e9
+    sample = f"first 2^22 keys of each of the 5 distributions (1/64 of the 2^28 arrays), per step"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (seeded SplitMix64 recipes)",
+            "config": {"workload": "2^28 uint32 keys x 5 distributions, keys only, stable sort (sampled)",
+                       "n": N, "distributions": list(DISTS)},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2211_16479_gb300 as ms
+    from synth import torch_gen
+
+    rank, world, local = _dist_env()
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n
+    opts = {"tile": args.tile} if args.tile else None
+
+    inputs = [torch_gen.u32_distribution(d, n, 1, device=dev) for d in DISTS]
+    out = torch.empty_like(inputs[0])
+    torch.cuda.synchronize()
+    ctx = ms.Context(local)
+    h = ctx.handle
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        for a in inputs:
+            ms.msort_sort_copy(h, a, out, options=opts, stream=stream)
+
+    def barrier():
+        if dist:
+            tdist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+
+    # correctness guard on the last warm-up output: sorted, same multiset
+    last = out.to(torch.int64)
+    assert bool((last[1:] >= last[:-1]).all()), "output not sorted"
+    del last
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms.msort_ctx_set_profiling(h, True)
+    launches0 = ms.msort_ctx_launch_count(h)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    barrier()
+    elapsed_ms = e0.elapsed_time(e1)
+    launches = ms.msort_ctx_launch_count(h) - launches0
+    clocks = sampler.stop()
+    kt = {k: ms.msort_ctx_kernel_times(h, k) for k in
+          (ms.MSORT_KERNEL_TILE, ms.MSORT_KERNEL_PARTITION, ms.MSORT_KERNEL_MERGE)}
+    ms.msort_ctx_set_profiling(h, False)
+
+    # per-distribution rates (single timed sort each, profiling off)
+    per_dist = {}
+    for d, a in zip(DISTS, inputs):
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(3):
+            ms.msort_sort_copy(h, a, out, options=opts, stream=stream)
+        s1.record(stream)
+        s1.synchronize()
+        per_dist[d] = round(3 * n / (s0.elapsed_time(s1) * 1e-3) / 1e9, 3)
+
+    t_max = elapsed_ms
+    if dist:
+        tt = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
+        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    keys_total = args.steps * len(DISTS) * n * world
+    value = keys_total / (t_max * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (merge pass)
+    peak, peak_kind = _peaks()
+    m_launches, m_ms = kt[ms.MSORT_KERNEL_MERGE]
+    t_launches, t_ms = kt[ms.MSORT_KERNEL_TILE]
+    p_launches, p_ms = kt[ms.MSORT_KERNEL_PARTITION]
+    bytes_per_merge = 2 * n * 4
+    merge_avg_s = (m_ms / max(1, m_launches)) * 1e-3
+    achieved = bytes_per_merge / merge_avg_s / 1e9
+    passes = 0
+    T = args.tile or 4096
+    L = T
+    while L < n:
+        passes += 1
+        L *= 2
+    alg_bytes_sort = 2 * n * 4 * (1 + passes)
+
+    # end to end through the host-buffer API
+    e2e = None
+    if not args.no_e2e:
+        h_in = [a.cpu().pin_memory() for a in inputs]
+        h_out = torch.empty(n, dtype=torch.uint32).pin_memory()
+        for a in h_in[:1]:
+            ms.msort_sort_host(h, a, out_keys=h_out, options=opts, stream=stream)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for a in h_in:
+                ms.msort_sort_host(h, a, out_keys=h_out, options=opts, stream=stream)
+        barrier()
+        te = time.perf_counter() - t0
+        if dist:
+            tt = torch.tensor([te], device=dev, dtype=torch.float64)
+            tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": args.e2e_steps * len(DISTS) * n * world / te / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": len(DISTS) * n * 4, "d2h_bytes_per_step": len(DISTS) * n * 4,
+               "steps": args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        sample = [a[: 1 << 22].cpu().numpy() for a in inputs]
+        v, cores, reps = cpu_oracle_rate(sample, seconds_target=args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"first 2^22 keys of each of the 5 inputs, {reps} rounds, chunked oracle "
+                         f"merge sort + pairwise merge tree on {cores} threads"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (seeded SplitMix64 recipes, generated on the device)",
+            "config": {"workload": "2^28 uint32 keys x 5 distributions (uniform, sorted, reverse, 16 distinct, "
+                                   "Zipf 1.1 over 2^20 ranks), keys only, stable out-of-place sort",
+                       "n": n, "distributions": list(DISTS), "tile": T, "merge_passes": passes,
+                       "merge_block_outputs": 4096,
+                       "l2": "inputs are 1 GiB each (> 126 MB L2); no flush between steps",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind, "kernel": "k_merge_pass<u32>",
+                         "traffic": _ncu_traffic(), "algorithmic_bytes_per_launch": bytes_per_merge,
+                         "launches": m_launches, "avg_ms": m_ms / max(1, m_launches)},
+            "whole_sort_roofline": {"algorithmic_bytes": alg_bytes_sort,
+                                    "frac_of_measured_hbm": alg_bytes_sort * len(DISTS) * args.steps /
+                                    (t_max * 1e-3) / 1e9 / peak,
+                                    "frac_of_8tbs": alg_bytes_sort * len(DISTS) * args.steps /
+                                    (t_max * 1e-3) / 1e9 / NOMINAL_HBM_GBS},
+            "kernel_ms_per_step": {"tile_sort": t_ms / args.steps, "partition": p_ms / args.steps,
+                                   "merge": m_ms / args.steps},
+            "per_distribution_gkeys": per_dist,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        tdist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N)
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

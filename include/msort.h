@@ -1,0 +1,127 @@
+/*
+ * msort -- stable GPU merge sort for sm_103a (GB300), C ABI.
+ *
+ * The method is the divide-and-conquer merge sort of arXiv 2211.16479
+ * ("Approaches to the Parallelization of Merge Sort in Python"): sort
+ * fixed-size chunks independently (Section "Multiprocessing Merge Sort",
+ * Figs. 6-7, where each chunk of ceil(n/p) elements goes to one worker), then
+ * merge sorted runs pairwise, round after round, until one run is left
+ * (Section "MPI Merge Sort", Fig. 13).  Here a chunk is a tile of T keys
+ * sorted by one thread block, and a round is one global merge pass over the
+ * whole array, so ceil(log2(ceil(n / T))) passes follow the tile sort.  The
+ * merge takes from the left run on ties (Section "Sequential Merge Sort"
+ * leaves merge() undefined; this is the stable reading), so every sort here
+ * is stable.
+ *
+ * Conventions for every call:
+ *  - Pointers named d_* are device pointers on the context's device; h_*
+ *    are host pointers (pinned memory gives the fastest copies).  The caller
+ *    owns every buffer it passes; the library never frees them.
+ *  - Keys are unsigned 32- or 64-bit integers (msort_key_type), compared as
+ *    unsigned.  Values are optional uint32 words that travel with their key.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device work is enqueued on it and the call returns without
+ *    waiting, except where a function says it synchronises.
+ *  - Return value: MSORT_OK, or an error code; msort_last_error() gives a
+ *    message for the calling thread's last failure on that context.  Invalid
+ *    arguments are rejected before any work is enqueued.  n == 0 and
+ *    nseg == 0 are valid and do nothing.
+ *  - Scratch memory (a second key/value buffer of n elements plus a small
+ *    split table) belongs to the context and is reused; calls on one context
+ *    are ordered by the context itself (a call on a new stream waits for the
+ *    previous call's scratch use).  Use one context per thread for
+ *    concurrent host threads.
+ */
+#ifndef MSORT_H_
+#define MSORT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MSORT_OK = 0,
+    MSORT_ERR_INVALID_ARG = 1,
+    MSORT_ERR_UNSUPPORTED = 2,
+    MSORT_ERR_OOM = 3,
+    MSORT_ERR_CUDA = 4,
+    MSORT_ERR_TIMEOUT = 5,
+    MSORT_ERR_BUSY = 6
+} msort_status;
+
+typedef enum { MSORT_U32 = 0, MSORT_U64 = 1 } msort_key_type;
+
+typedef struct msort_ctx msort_ctx;
+
+/* Tuning knobs; a zeroed struct (or NULL) selects the defaults. */
+typedef struct {
+    int tile;           /* keys per tile-sort block: 0 = default, else 2048, 4096 or 8192 */
+    int partition_mode; /* 0 = exact merge-path search, 1 = learned CDF predictor (verified) */
+    int learned_passes; /* with mode 1: final passes that use it; 0 = passes with runs >= 2^22 */
+    int use_graph;      /* 1 = replay the pass sequence from a captured CUDA graph */
+    int reserved[4];    /* must be zero */
+} msort_options;
+
+/* Context on CUDA device `device`.  scratch_budget_bytes caps the scratch the
+ * context may hold (0 = no cap); a sort that needs more fails with
+ * MSORT_ERR_OOM and enqueues nothing. */
+msort_status msort_ctx_create(int device, size_t scratch_budget_bytes, msort_ctx** out);
+/* Waits for the context's outstanding work, frees its scratch and itself. */
+msort_status msort_ctx_destroy(msort_ctx* ctx);
+/* Message for the calling thread's last failing call on ctx ("" if none). */
+const char* msort_last_error(msort_ctx* ctx);
+/* Waits for `stream`, then reports any error a kernel recorded in the
+ * context's device status word (MSORT_ERR_TIMEOUT for a bounded wait that
+ * gave up) and clears it. */
+msort_status msort_ctx_sync(msort_ctx* ctx, void* stream);
+
+/* Bytes of scratch a sort of n elements needs (tile sort buffer + splits). */
+size_t msort_scratch_bytes(size_t n, msort_key_type kt, int with_vals, const msort_options* opt);
+
+/* In-place stable sort of d_keys[0:n). */
+msort_status msort_sort(msort_ctx* ctx, void* d_keys, size_t n, msort_key_type kt,
+                        const msort_options* opt, void* stream);
+
+/* In-place stable sort of (d_keys, d_vals)[0:n) by key. */
+msort_status msort_sort_pairs(msort_ctx* ctx, void* d_keys, uint32_t* d_vals, size_t n,
+                              msort_key_type kt, const msort_options* opt, void* stream);
+
+/* Out-of-place stable sort: d_keys_in (and d_vals_in) are only read, the
+ * result goes to d_keys_out (and d_vals_out).  d_vals_in/d_vals_out are both
+ * NULL for a keys-only sort.  Input and output must not overlap. */
+msort_status msort_sort_copy(msort_ctx* ctx, const void* d_keys_in, const uint32_t* d_vals_in,
+                             void* d_keys_out, uint32_t* d_vals_out, size_t n, msort_key_type kt,
+                             const msort_options* opt, void* stream);
+
+/* Host-buffer sort: copies h_keys_in (and h_vals_in, nullable) to the
+ * device, sorts there, and copies the result to h_keys_out (and h_vals_out;
+ * give both value pointers or neither).  Output may be the same buffer as
+ * input.  Device buffers come from the context (its staging area grows to
+ * the largest n seen).  Synchronises on `stream` before returning. */
+msort_status msort_sort_host(msort_ctx* ctx, const void* h_keys_in, const uint32_t* h_vals_in,
+                             void* h_keys_out, uint32_t* h_vals_out, size_t n, msort_key_type kt,
+                             const msort_options* opt, void* stream);
+
+/* ---- measurement ------------------------------------------------------ */
+
+/* Kernel kinds for msort_ctx_kernel_times. */
+enum { MSORT_KERNEL_TILE = 0, MSORT_KERNEL_PARTITION = 1, MSORT_KERNEL_MERGE = 2,
+       MSORT_KERNEL_SEGMENTED = 3, MSORT_KERNEL_MLP = 4 };
+
+/* on != 0: bracket every later launch with CUDA events on its own stream
+ * (resets the event log).  Off by default; events cost a few microseconds
+ * of host time per launch. */
+msort_status msort_ctx_set_profiling(msort_ctx* ctx, int on);
+/* Waits for the logged events of kernel kind `kind`, returns how many
+ * launches were logged and their summed device time, and clears that log. */
+msort_status msort_ctx_kernel_times(msort_ctx* ctx, int kind, uint64_t* launches, double* total_ms);
+/* Number of kernels this context has launched since it was created. */
+unsigned long long msort_ctx_launch_count(msort_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSORT_H_ */

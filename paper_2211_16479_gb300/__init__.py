@@ -1,0 +1,235 @@
+"""Python binding of libmsort (stable GPU merge sort for GB300 / sm_103a).
+
+Every function here marshals arguments and calls the C ABI declared in
+``include/msort.h`` under the same name; all sorting runs in the library's
+CUDA kernels.  Tensors supply device pointers, ``torch.cuda`` supplies the
+current stream; there is no CPU code path.  If ``libmsort.so`` has not been
+built, importing the library raises ``ImportError`` instead of falling back.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmsort.so")
+
+MSORT_OK, MSORT_ERR_INVALID_ARG, MSORT_ERR_UNSUPPORTED, MSORT_ERR_OOM = 0, 1, 2, 3
+MSORT_ERR_CUDA, MSORT_ERR_TIMEOUT, MSORT_ERR_BUSY = 4, 5, 6
+MSORT_U32, MSORT_U64 = 0, 1
+MSORT_KERNEL_TILE, MSORT_KERNEL_PARTITION, MSORT_KERNEL_MERGE = 0, 1, 2
+MSORT_KERNEL_SEGMENTED, MSORT_KERNEL_MLP = 3, 4
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "TIMEOUT", 6: "BUSY"}
+
+
+class MsortError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"msort {STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class msort_options(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int), ("partition_mode", ctypes.c_int),
+                ("learned_passes", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
+
+
+_P, _SZ, _I, _ST = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int
+_OPT = ctypes.POINTER(msort_options)
+
+_SIGS = {
+    "msort_ctx_create": ([_I, _SZ, ctypes.POINTER(_P)], _ST),
+    "msort_ctx_destroy": ([_P], _ST),
+    "msort_last_error": ([_P], ctypes.c_char_p),
+    "msort_ctx_sync": ([_P, _P], _ST),
+    "msort_scratch_bytes": ([_SZ, _I, _I, _OPT], _SZ),
+    "msort_sort": ([_P, _P, _SZ, _I, _OPT, _P], _ST),
+    "msort_sort_pairs": ([_P, _P, _P, _SZ, _I, _OPT, _P], _ST),
+    "msort_sort_copy": ([_P, _P, _P, _P, _P, _SZ, _I, _OPT, _P], _ST),
+    "msort_sort_host": ([_P, _P, _P, _P, _P, _SZ, _I, _OPT, _P], _ST),
+    "msort_ctx_set_profiling": ([_P, _I], _ST),
+    "msort_ctx_kernel_times": ([_P, _I, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)], _ST),
+    "msort_ctx_launch_count": ([_P], ctypes.c_ulonglong),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libmsort.so (raises ImportError when it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is not built; run paper_2211_16479_gb300._build.build() first")
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in _SIGS.items():
+        fn = getattr(lib, name, None)
+        if fn is None:
+            continue
+        fn.argtypes, fn.restype = args, res
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors passed to msort must be contiguous")
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):  # numpy array (host)
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)!r}")
+
+
+def _key_type(x, key_type):
+    if key_type is not None:
+        return int(key_type)
+    name = str(getattr(x, "dtype", ""))
+    if name.endswith(("uint32", "int32")):
+        return MSORT_U32
+    if name.endswith(("uint64", "int64")):
+        return MSORT_U64
+    raise TypeError(f"key dtype {name!r} is not a 32/64-bit integer; pass key_type explicitly")
+
+
+def _numel(x, n):
+    if n is not None:
+        return int(n)
+    if hasattr(x, "numel"):
+        return int(x.numel())
+    if hasattr(x, "size") and not callable(x.size):
+        return int(x.size)
+    raise ValueError("n is required for raw pointers")
+
+
+def _stream(stream, like=None):
+    if stream is None:
+        import torch
+        dev = like.device if like is not None and hasattr(like, "device") and like.device.type == "cuda" else None
+        return torch.cuda.current_stream(dev).cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _opts(options):
+    if options is None:
+        return None
+    if isinstance(options, msort_options):
+        return ctypes.byref(options)
+    o = msort_options()
+    for k, v in dict(options).items():
+        setattr(o, k, int(v))
+    return ctypes.byref(o)
+
+
+def _check(ctx, status):
+    if status != MSORT_OK:
+        msg = load_library().msort_last_error(ctx)
+        raise MsortError(status, msg.decode() if msg else "")
+
+
+# ---------------------------------------------------------------------------
+# C ABI, same names
+# ---------------------------------------------------------------------------
+def msort_ctx_create(device: int = 0, scratch_budget_bytes: int = 0):
+    out = ctypes.c_void_p()
+    _check(None, load_library().msort_ctx_create(int(device), int(scratch_budget_bytes), ctypes.byref(out)))
+    return out
+
+
+def msort_ctx_destroy(ctx) -> None:
+    _check(ctx, load_library().msort_ctx_destroy(ctx))
+
+
+def msort_last_error(ctx) -> str:
+    r = load_library().msort_last_error(ctx)
+    return r.decode() if r else ""
+
+
+def msort_ctx_sync(ctx, stream=None) -> None:
+    _check(ctx, load_library().msort_ctx_sync(ctx, _stream(stream)))
+
+
+def msort_scratch_bytes(n: int, key_type: int, with_vals: bool, options=None) -> int:
+    return int(load_library().msort_scratch_bytes(int(n), int(key_type), int(bool(with_vals)), _opts(options)))
+
+
+def msort_sort(ctx, keys, n=None, key_type=None, options=None, stream=None) -> None:
+    _check(ctx, load_library().msort_sort(ctx, _ptr(keys), _numel(keys, n), _key_type(keys, key_type),
+                                          _opts(options), _stream(stream, keys)))
+
+
+def msort_sort_pairs(ctx, keys, vals, n=None, key_type=None, options=None, stream=None) -> None:
+    _check(ctx, load_library().msort_sort_pairs(ctx, _ptr(keys), _ptr(vals), _numel(keys, n),
+                                                _key_type(keys, key_type), _opts(options), _stream(stream, keys)))
+
+
+def msort_sort_copy(ctx, keys_in, keys_out, vals_in=None, vals_out=None, n=None, key_type=None,
+                    options=None, stream=None) -> None:
+    _check(ctx, load_library().msort_sort_copy(ctx, _ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out),
+                                               _numel(keys_in, n), _key_type(keys_in, key_type), _opts(options),
+                                               _stream(stream, keys_in)))
+
+
+def msort_sort_host(ctx, keys, vals=None, out_keys=None, out_vals=None, n=None, key_type=None,
+                    options=None, stream=None) -> None:
+    """Sort host buffers (numpy arrays or CPU tensors; pinned is fastest).
+    The result goes to out_keys/out_vals, or back into keys/vals."""
+    if out_keys is None:
+        out_keys, out_vals = keys, vals
+    _check(ctx, load_library().msort_sort_host(ctx, _ptr(keys), _ptr(vals), _ptr(out_keys), _ptr(out_vals),
+                                               _numel(keys, n), _key_type(keys, key_type), _opts(options),
+                                               _stream(stream)))
+
+
+def msort_ctx_set_profiling(ctx, on: bool) -> None:
+    _check(ctx, load_library().msort_ctx_set_profiling(ctx, int(bool(on))))
+
+
+def msort_ctx_kernel_times(ctx, kind: int):
+    """(launches, total milliseconds) of the kernels of `kind` logged since the last call."""
+    n = ctypes.c_uint64()
+    ms = ctypes.c_double()
+    _check(ctx, load_library().msort_ctx_kernel_times(ctx, int(kind), ctypes.byref(n), ctypes.byref(ms)))
+    return int(n.value), float(ms.value)
+
+
+def msort_ctx_launch_count(ctx) -> int:
+    return int(load_library().msort_ctx_launch_count(ctx))
+
+
+class Context:
+    """Owns a msort context; usable as a context manager."""
+
+    def __init__(self, device: int = 0, scratch_budget_bytes: int = 0):
+        self.handle = msort_ctx_create(device, scratch_budget_bytes)
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            msort_ctx_destroy(self.handle)
+        self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,72 @@
+// Host-side context shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/msort.h"
+
+namespace msort {
+
+enum KernelKind { KK_TILE = 0, KK_PARTITION = 1, KK_MERGE = 2, KK_SEGMENTED = 3, KK_MLP = 4, KK_COUNT = 5 };
+
+// Status bits a kernel may raise in the context's device status word.
+enum : unsigned int { DEV_OK = 0, DEV_TIMEOUT = 1u, DEV_BAD_INPUT = 2u };
+
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+};
+
+struct Plan {
+    int tile;       // keys per tile sort block
+    int tthreads;   // threads of a tile sort block
+    int tipt;       // keys per thread in the tile sort
+    int mthreads;   // threads of a merge block
+    int mipt;       // outputs per thread in a merge block
+    int W;          // outputs per merge block
+    int passes;     // merge passes after the tile sort
+    int partition_mode;
+    int learned_passes;
+};
+
+}  // namespace msort
+
+struct msort_ctx {
+    int device = 0;
+    size_t budget = 0;  // 0 = unlimited
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    void* staging = nullptr;  // device buffers for msort_sort_host
+    size_t staging_bytes = 0;
+    unsigned int* d_status = nullptr;
+    cudaEvent_t scratch_done = nullptr;
+    cudaStream_t last_stream = nullptr;
+    bool scratch_pending = false;
+    bool profiling = false;
+    std::vector<msort::EventPair> prof[msort::KK_COUNT];
+    size_t prof_used[msort::KK_COUNT] = {};
+    unsigned long long launches = 0;
+    std::mutex mu;
+    // learned partitioner state (owned by learned.cu)
+    void* learned = nullptr;
+    // graph cache (owned by msort.cu)
+    void* graphs = nullptr;
+};
+
+namespace msort {
+
+msort_status fail(msort_status s, const std::string& msg);
+msort_status cuda_fail(cudaError_t e, const char* what);
+// Make sure ctx->scratch holds at least `bytes`; orders the caller's stream
+// after the previous scratch user.
+msort_status ensure_scratch(msort_ctx* ctx, size_t bytes, cudaStream_t st);
+// Profiling helpers around one launch of kind `k` on stream st.
+void prof_begin(msort_ctx* ctx, int k, cudaStream_t st);
+void prof_end(msort_ctx* ctx, int k, cudaStream_t st);
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace msort

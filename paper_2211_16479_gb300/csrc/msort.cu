@@ -1,0 +1,449 @@
+// Pass scheduler and C ABI of the plain merge sort.
+//
+// One sort = one tile-sort launch (the chunk sort of Section
+// "Multiprocessing Merge Sort", Figs. 6-7) followed by P = ceil(log2(n / T))
+// rounds of the pairwise merge tree (Section "MPI Merge Sort", Fig. 13); each
+// round is a partition launch (merge-path co-ranks of every output block) and
+// a merge launch.  Buffers ping-pong between the caller's output and the
+// context's scratch; the tile sort writes to whichever of the two makes the
+// last round land in the caller's buffer, so no final copy is needed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+
+#include "ctx.h"
+#include "learned.h"
+#include "sort_kernels.cuh"
+
+namespace msort {
+
+static thread_local std::string tl_error;
+
+msort_status fail(msort_status s, const std::string& msg) {
+    tl_error = msg;
+    return s;
+}
+
+msort_status cuda_fail(cudaError_t e, const char* what) {
+    tl_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return MSORT_ERR_CUDA;
+}
+
+void prof_begin(msort_ctx* ctx, int k, cudaStream_t st) {
+    if (!ctx->profiling) return;
+    auto& v = ctx->prof[k];
+    size_t& u = ctx->prof_used[k];
+    if (u == v.size()) {
+        EventPair p;
+        cudaEventCreate(&p.a);
+        cudaEventCreate(&p.b);
+        v.push_back(p);
+    }
+    cudaEventRecord(v[u].a, st);
+}
+
+void prof_end(msort_ctx* ctx, int k, cudaStream_t st) {
+    if (!ctx->profiling) return;
+    cudaEventRecord(ctx->prof[k][ctx->prof_used[k]].b, st);
+    ++ctx->prof_used[k];
+}
+
+msort_status ensure_scratch(msort_ctx* ctx, size_t bytes, cudaStream_t st) {
+    if (ctx->scratch_pending && ctx->last_stream != st) {
+        cudaError_t e = cudaStreamWaitEvent(st, ctx->scratch_done, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+    }
+    if (bytes <= ctx->scratch_bytes) return MSORT_OK;
+    if (ctx->budget && bytes + ctx->staging_bytes > ctx->budget)
+        return fail(MSORT_ERR_OOM, "scratch of " + std::to_string(bytes) + " bytes exceeds the context budget of " +
+                                       std::to_string(ctx->budget) + " bytes");
+    // Growth is rare (first call at a new size): wait until no kernel can
+    // still be using the old block, then replace it.
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (ctx->scratch) cudaFree(ctx->scratch);
+    ctx->scratch = nullptr;
+    ctx->scratch_bytes = 0;
+    size_t want = align_up(bytes, size_t(2) << 20);
+    e = cudaMalloc(&ctx->scratch, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MSORT_ERR_OOM, "cudaMalloc of scratch (" + std::to_string(want) + " bytes) failed");
+    }
+    ctx->scratch_bytes = want;
+    return MSORT_OK;
+}
+
+static void scratch_release(msort_ctx* ctx, cudaStream_t st) {
+    cudaEventRecord(ctx->scratch_done, st);
+    ctx->last_stream = st;
+    ctx->scratch_pending = true;
+}
+
+// ----------------------------------------------------------------------------
+// Plans
+// ----------------------------------------------------------------------------
+static constexpr int kMergeThreads = 256;
+static constexpr int kMergeIpt = 16;
+
+static bool make_plan(size_t n, const msort_options* opt, Plan* pl) {
+    int tile = opt && opt->tile ? opt->tile : 4096;
+    Plan p{};
+    switch (tile) {
+        case 2048: p.tthreads = 256; p.tipt = 8; break;
+        case 4096: p.tthreads = 256; p.tipt = 16; break;
+        case 8192: p.tthreads = 512; p.tipt = 16; break;
+        default: return false;
+    }
+    p.tile = tile;
+    p.mthreads = kMergeThreads;
+    p.mipt = kMergeIpt;
+    p.W = p.mthreads * p.mipt;
+    p.passes = 0;
+    for (size_t L = (size_t)tile; L < n; L *= 2) ++p.passes;
+    p.partition_mode = opt ? opt->partition_mode : 0;
+    p.learned_passes = opt ? opt->learned_passes : 0;
+    *pl = p;
+    return true;
+}
+
+template <class K, bool PAIRS>
+static size_t scratch_need(size_t n, const Plan& pl) {
+    size_t b = align_up(n * sizeof(K), 256);
+    if (PAIRS) b += align_up(n * sizeof(uint32_t), 256);
+    size_t nblocks = (n + pl.W - 1) / pl.W;
+    b += align_up((nblocks + 1) * sizeof(unsigned long long), 256);
+    return b;
+}
+
+template <class K, bool PAIRS>
+static size_t tile_smem(int T) {
+    using Item = typename TileItem<K, PAIRS>::T;
+    return sizeof(Item) * spad_size<Item>(T) + (PAIRS ? sizeof(uint32_t) * T : 0);
+}
+
+template <class K, bool PAIRS>
+static size_t merge_smem(int W) {
+    return sizeof(K) * spad_size<K>(W) + (PAIRS ? sizeof(uint32_t) * spad_size<uint32_t>(W) : 0);
+}
+
+static thread_local std::string tl_launch_info;
+
+template <class F>
+static cudaError_t set_smem(F* f, size_t bytes) {
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(f));
+    char buf[256];
+    std::snprintf(buf, sizeof buf, " [regs %d, max threads %d, static smem %zu, dyn smem %zu, max dyn %d]",
+                  fa.numRegs, fa.maxThreadsPerBlock, fa.sharedSizeBytes, bytes, fa.maxDynamicSharedSizeBytes);
+    tl_launch_info = buf;
+    if (e != cudaSuccess) return e;
+    if (bytes <= 48 * 1024 || (int)bytes <= fa.maxDynamicSharedSizeBytes) return cudaSuccess;
+    return cudaFuncSetAttribute(reinterpret_cast<const void*>(f), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)bytes);
+}
+
+template <class K, bool PAIRS>
+static cudaError_t launch_tile(const Plan& pl, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n,
+                               cudaStream_t st) {
+    const size_t nblocks = (n + pl.tile - 1) / pl.tile;
+    const size_t sm = tile_smem<K, PAIRS>(pl.tile);
+    cudaError_t e = cudaSuccess;
+#define MSORT_TILE_CASE(TH, IPT)                                                                 \
+    if (pl.tthreads == TH && pl.tipt == IPT) {                                                   \
+        auto f = k_tile_sort<K, PAIRS, TH, IPT>;                                                 \
+        if ((e = set_smem(f, sm)) != cudaSuccess) return e;                                      \
+        f<<<(unsigned)nblocks, TH, sm, st>>>(kin, vin, kout, vout, n);                           \
+        return cudaGetLastError();                                                               \
+    }
+    MSORT_TILE_CASE(256, 8)
+    MSORT_TILE_CASE(256, 16)
+    MSORT_TILE_CASE(512, 16)
+#undef MSORT_TILE_CASE
+    return cudaErrorInvalidConfiguration;
+}
+
+template <class K, bool PAIRS>
+static cudaError_t launch_merge(const Plan& pl, const K* src, K* dst, const uint32_t* vsrc, uint32_t* vdst, size_t n,
+                                size_t L, const unsigned long long* splits, cudaStream_t st) {
+    const size_t nblocks = (n + pl.W - 1) / pl.W;
+    const size_t sm = merge_smem<K, PAIRS>(pl.W);
+    auto f = k_merge_pass<K, PAIRS, kMergeThreads, kMergeIpt>;
+    cudaError_t e = set_smem(f, sm);
+    if (e != cudaSuccess) return e;
+    f<<<(unsigned)nblocks, kMergeThreads, sm, st>>>(src, dst, vsrc, vdst, n, L, splits);
+    return cudaGetLastError();
+}
+
+template <class K>
+static cudaError_t launch_partition(const Plan& pl, const K* src, size_t n, size_t L, unsigned long long* splits,
+                                    cudaStream_t st) {
+    const size_t nblocks = (n + pl.W - 1) / pl.W;
+    const unsigned th = 256;
+    k_partition<K><<<(unsigned)((nblocks + th - 1) / th), th, 0, st>>>(src, n, L, (size_t)pl.W, nblocks, splits);
+    return cudaGetLastError();
+}
+
+// The whole sort on stream st.  kin may equal kout (in-place).
+template <class K, bool PAIRS>
+static msort_status run_sort(msort_ctx* ctx, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n,
+                             const Plan& pl, cudaStream_t st) {
+    unsigned char* sp = static_cast<unsigned char*>(ctx->scratch);
+    K* tk = reinterpret_cast<K*>(sp);
+    sp += align_up(n * sizeof(K), 256);
+    uint32_t* tv = nullptr;
+    if (PAIRS) {
+        tv = reinterpret_cast<uint32_t*>(sp);
+        sp += align_up(n * sizeof(uint32_t), 256);
+    }
+    unsigned long long* splits = reinterpret_cast<unsigned long long*>(sp);
+
+    K* bk[2] = {kout, tk};
+    uint32_t* bv[2] = {vout, tv};
+    int cur = (pl.passes & 1) ? 1 : 0;
+    cudaError_t e;
+    prof_begin(ctx, KK_TILE, st);
+    e = launch_tile<K, PAIRS>(pl, kin, vin, bk[cur], bv[cur], n, st);
+    prof_end(ctx, KK_TILE, st);
+    ++ctx->launches;
+    if (e != cudaSuccess) return cuda_fail(e, ("tile sort launch" + tl_launch_info).c_str());
+    const int first_learned = pl.partition_mode == 1 ? learned_first_pass(pl, n) : pl.passes;
+    for (int p = 0; p < pl.passes; ++p) {
+        const size_t L = (size_t)pl.tile << p;
+        prof_begin(ctx, KK_PARTITION, st);
+        if (p >= first_learned)
+            e = launch_learned_partition<K>(ctx, pl, bk[cur], n, L, splits, st);
+        else
+            e = launch_partition<K>(pl, bk[cur], n, L, splits, st);
+        prof_end(ctx, KK_PARTITION, st);
+        ++ctx->launches;
+        if (e != cudaSuccess) return cuda_fail(e, "partition launch");
+        prof_begin(ctx, KK_MERGE, st);
+        e = launch_merge<K, PAIRS>(pl, bk[cur], bk[cur ^ 1], bv[cur], bv[cur ^ 1], n, L, splits, st);
+        prof_end(ctx, KK_MERGE, st);
+        ++ctx->launches;
+        if (e != cudaSuccess) return cuda_fail(e, ("merge pass launch" + tl_launch_info).c_str());
+        cur ^= 1;
+    }
+    return MSORT_OK;
+}
+
+template <class K, bool PAIRS>
+static msort_status sort_entry(msort_ctx* ctx, const void* kin, const uint32_t* vin, void* kout, uint32_t* vout,
+                               size_t n, const msort_options* opt, cudaStream_t st) {
+    Plan pl;
+    if (!make_plan(n, opt, &pl)) return fail(MSORT_ERR_INVALID_ARG, "options.tile must be 0, 2048, 4096 or 8192");
+    if (n == 0) return MSORT_OK;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    msort_status s = ensure_scratch(ctx, scratch_need<K, PAIRS>(n, pl), st);
+    if (s != MSORT_OK) return s;
+    if (pl.partition_mode == 1 && pl.passes > 0) {
+        s = learned_prepare<K>(ctx, pl, static_cast<const K*>(kin), n, st);
+        if (s != MSORT_OK) return s;
+    }
+    s = run_sort<K, PAIRS>(ctx, static_cast<const K*>(kin), vin, static_cast<K*>(kout), vout, n, pl, st);
+    scratch_release(ctx, st);
+    return s;
+}
+
+static msort_status check_common(msort_ctx* ctx, msort_key_type kt, const msort_options* opt) {
+    if (!ctx) return fail(MSORT_ERR_INVALID_ARG, "ctx is NULL");
+    if (kt != MSORT_U32 && kt != MSORT_U64) return fail(MSORT_ERR_INVALID_ARG, "unknown key type");
+    if (opt) {
+        for (int r : opt->reserved)
+            if (r) return fail(MSORT_ERR_INVALID_ARG, "options.reserved must be zero");
+        if (opt->partition_mode != 0 && opt->partition_mode != 1)
+            return fail(MSORT_ERR_INVALID_ARG, "options.partition_mode must be 0 or 1");
+        if (opt->learned_passes < 0) return fail(MSORT_ERR_INVALID_ARG, "options.learned_passes must be >= 0");
+    }
+    return MSORT_OK;
+}
+
+}  // namespace msort
+
+using namespace msort;
+
+extern "C" {
+
+msort_status msort_ctx_create(int device, size_t budget, msort_ctx** out) {
+    if (!out) return fail(MSORT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= count) return fail(MSORT_ERR_INVALID_ARG, "no such CUDA device");
+    if ((e = cudaSetDevice(device)) != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    msort_ctx* c = new msort_ctx();
+    c->device = device;
+    c->budget = budget;
+    if ((e = cudaEventCreateWithFlags(&c->scratch_done, cudaEventDisableTiming)) != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "cudaEventCreate");
+    }
+    if ((e = cudaMalloc(&c->d_status, 256)) != cudaSuccess || (e = cudaMemset(c->d_status, 0, 256)) != cudaSuccess) {
+        cudaEventDestroy(c->scratch_done);
+        delete c;
+        return cuda_fail(e, "status word");
+    }
+    *out = c;
+    return MSORT_OK;
+}
+
+msort_status msort_ctx_destroy(msort_ctx* ctx) {
+    if (!ctx) return MSORT_OK;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    learned_destroy(ctx);
+    graphs_destroy(ctx);
+    if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->staging) cudaFree(ctx->staging);
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    for (auto& v : ctx->prof)
+        for (auto& p : v) {
+            cudaEventDestroy(p.a);
+            cudaEventDestroy(p.b);
+        }
+    cudaEventDestroy(ctx->scratch_done);
+    delete ctx;
+    return MSORT_OK;
+}
+
+const char* msort_last_error(msort_ctx*) { return tl_error.c_str(); }
+
+msort_status msort_ctx_sync(msort_ctx* ctx, void* stream) {
+    if (!ctx) return fail(MSORT_ERR_INVALID_ARG, "ctx is NULL");
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    unsigned int st = 0;
+    e = cudaMemcpy(&st, ctx->d_status, sizeof(st), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (st) {
+        cudaMemset(ctx->d_status, 0, sizeof(unsigned int));
+        if (st & DEV_TIMEOUT) return fail(MSORT_ERR_TIMEOUT, "a kernel gave up a bounded wait");
+        return fail(MSORT_ERR_INVALID_ARG, "a kernel rejected its input (status " + std::to_string(st) + ")");
+    }
+    return MSORT_OK;
+}
+
+size_t msort_scratch_bytes(size_t n, msort_key_type kt, int with_vals, const msort_options* opt) {
+    Plan pl;
+    if (!make_plan(n, opt, &pl)) return 0;
+    if (kt == MSORT_U32) return with_vals ? scratch_need<uint32_t, true>(n, pl) : scratch_need<uint32_t, false>(n, pl);
+    return with_vals ? scratch_need<uint64_t, true>(n, pl) : scratch_need<uint64_t, false>(n, pl);
+}
+
+msort_status msort_sort_copy(msort_ctx* ctx, const void* kin, const uint32_t* vin, void* kout, uint32_t* vout,
+                             size_t n, msort_key_type kt, const msort_options* opt, void* stream) {
+    msort_status s = check_common(ctx, kt, opt);
+    if (s != MSORT_OK) return s;
+    if (n == 0) return MSORT_OK;
+    if (!kin || !kout) return fail(MSORT_ERR_INVALID_ARG, "key pointer is NULL");
+    if ((vin == nullptr) != (vout == nullptr)) return fail(MSORT_ERR_INVALID_ARG, "give both value pointers or none");
+    const size_t ks = kt == MSORT_U32 ? 4 : 8;
+    if ((reinterpret_cast<uintptr_t>(kin) | reinterpret_cast<uintptr_t>(kout)) % ks ||
+        (vin && ((reinterpret_cast<uintptr_t>(vin) | reinterpret_cast<uintptr_t>(vout)) & 3)))
+        return fail(MSORT_ERR_INVALID_ARG, "buffers must be aligned to their element size");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (kt == MSORT_U32)
+        return vin ? sort_entry<uint32_t, true>(ctx, kin, vin, kout, vout, n, opt, st)
+                   : sort_entry<uint32_t, false>(ctx, kin, nullptr, kout, nullptr, n, opt, st);
+    return vin ? sort_entry<uint64_t, true>(ctx, kin, vin, kout, vout, n, opt, st)
+               : sort_entry<uint64_t, false>(ctx, kin, nullptr, kout, nullptr, n, opt, st);
+}
+
+msort_status msort_sort(msort_ctx* ctx, void* d_keys, size_t n, msort_key_type kt, const msort_options* opt,
+                        void* stream) {
+    return msort_sort_copy(ctx, d_keys, nullptr, d_keys, nullptr, n, kt, opt, stream);
+}
+
+msort_status msort_sort_pairs(msort_ctx* ctx, void* d_keys, uint32_t* d_vals, size_t n, msort_key_type kt,
+                              const msort_options* opt, void* stream) {
+    if (n && !d_vals) return fail(MSORT_ERR_INVALID_ARG, "d_vals is NULL");
+    return msort_sort_copy(ctx, d_keys, d_vals, d_keys, d_vals, n, kt, opt, stream);
+}
+
+msort_status msort_sort_host(msort_ctx* ctx, const void* h_kin, const uint32_t* h_vin, void* h_kout,
+                             uint32_t* h_vout, size_t n, msort_key_type kt, const msort_options* opt, void* stream) {
+    msort_status s = check_common(ctx, kt, opt);
+    if (s != MSORT_OK) return s;
+    if (n == 0) return MSORT_OK;
+    if (!h_kin || !h_kout) return fail(MSORT_ERR_INVALID_ARG, "host key pointer is NULL");
+    if ((h_vin == nullptr) != (h_vout == nullptr)) return fail(MSORT_ERR_INVALID_ARG, "give both value pointers or none");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t ks = kt == MSORT_U32 ? 4 : 8;
+    const size_t kb = align_up(n * ks, 256);
+    const size_t need = kb + (h_vin ? align_up(n * 4, 256) : 0);
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        cudaSetDevice(ctx->device);
+        if (need > ctx->staging_bytes) {
+            if (ctx->budget && need + ctx->scratch_bytes > ctx->budget)
+                return fail(MSORT_ERR_OOM, "host-sort staging exceeds the context budget");
+            cudaError_t e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+            if (ctx->staging) cudaFree(ctx->staging);
+            ctx->staging = nullptr;
+            ctx->staging_bytes = 0;
+            if (cudaMalloc(&ctx->staging, need) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(MSORT_ERR_OOM, "cudaMalloc of host-sort staging failed");
+            }
+            ctx->staging_bytes = need;
+        }
+    }
+    unsigned char* dk = static_cast<unsigned char*>(ctx->staging);
+    uint32_t* dv = h_vin ? reinterpret_cast<uint32_t*>(dk + kb) : nullptr;
+    cudaError_t e = cudaMemcpyAsync(dk, h_kin, n * ks, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && h_vin) e = cudaMemcpyAsync(dv, h_vin, n * 4, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "host to device copy");
+    s = msort_sort_copy(ctx, dk, dv, dk, dv, n, kt, opt, stream);
+    if (s != MSORT_OK) return s;
+    e = cudaMemcpyAsync(h_kout, dk, n * ks, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && h_vin) e = cudaMemcpyAsync(h_vout, dv, n * 4, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "device to host copy");
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return MSORT_OK;
+}
+
+msort_status msort_ctx_set_profiling(msort_ctx* ctx, int on) {
+    if (!ctx) return fail(MSORT_ERR_INVALID_ARG, "ctx is NULL");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->profiling = on != 0;
+    for (auto& u : ctx->prof_used) u = 0;
+    return MSORT_OK;
+}
+
+msort_status msort_ctx_kernel_times(msort_ctx* ctx, int kind, uint64_t* launches, double* total_ms) {
+    if (!ctx || kind < 0 || kind >= KK_COUNT || !launches || !total_ms)
+        return fail(MSORT_ERR_INVALID_ARG, "bad argument to msort_ctx_kernel_times");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    cudaSetDevice(ctx->device);
+    double tot = 0.0;
+    const size_t used = ctx->prof_used[kind];
+    for (size_t i = 0; i < used; ++i) {
+        const EventPair& p = ctx->prof[kind][i];
+        cudaError_t e = cudaEventSynchronize(p.b);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, p.a, p.b);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+        tot += ms;
+    }
+    *launches = used;
+    *total_ms = tot;
+    ctx->prof_used[kind] = 0;
+    return MSORT_OK;
+}
+
+unsigned long long msort_ctx_launch_count(msort_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+}  // extern "C"
