@@ -208,7 +208,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     n = args.n
-    opts = {"tile": args.tile} if args.tile else None
+    opts = {"tile": args.tile, "merge_block": args.merge_block}
+    T, W, passes = ms.msort_plan_info(n, ms.MSORT_U32, False, opts)
 
     inputs = [torch_gen.u32_distribution(d, n, 1, device=dev) for d in DISTS]
     out = torch.empty_like(inputs[0])
@@ -282,12 +283,6 @@ def run_ours(args):
     bytes_per_merge = 2 * n * 4
     merge_avg_s = (m_ms / max(1, m_launches)) * 1e-3
     achieved = bytes_per_merge / merge_avg_s / 1e9
-    passes = 0
-    T = args.tile or 4096
-    L = T
-    while L < n:
-        passes += 1
-        L *= 2
     alg_bytes_sort = 2 * n * 4 * (1 + passes)
 
     # end to end through the host-buffer API
@@ -329,7 +324,7 @@ def run_ours(args):
             "config": {"workload": "2^28 uint32 keys x 5 distributions (uniform, sorted, reverse, 16 distinct, "
                                    "Zipf 1.1 over 2^20 ranks), keys only, stable out-of-place sort",
                        "n": n, "distributions": list(DISTS), "tile": T, "merge_passes": passes,
-                       "merge_block_outputs": 4096,
+                       "merge_block_outputs": W,
                        "l2": "inputs are 1 GiB each (> 126 MB L2); no flush between steps",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "gpu_launches": launches,
@@ -364,6 +359,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N)
     ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--merge-block", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

@@ -58,11 +58,15 @@ typedef struct msort_ctx msort_ctx;
 
 /* Tuning knobs; a zeroed struct (or NULL) selects the defaults. */
 typedef struct {
-    int tile;           /* keys per tile-sort block: 0 = default, else 2048, 4096 or 8192 */
+    int tile;           /* keys per tile-sort block: 0 = default, else 4352 (256 x 17),
+                           8448 (256 x 33), 8704 (512 x 17) or 16896 (512 x 33); 16896 is
+                           not available for 64-bit key-value sorts */
+    int merge_block;    /* outputs per merge block: 0, or the value the tile implies
+                           (4352 for tiles of 17 keys per thread, 8448 for 33) */
     int partition_mode; /* 0 = exact merge-path search, 1 = learned CDF predictor (verified) */
     int learned_passes; /* with mode 1: final passes that use it; 0 = passes with runs >= 2^22 */
     int use_graph;      /* 1 = replay the pass sequence from a captured CUDA graph */
-    int reserved[4];    /* must be zero */
+    int reserved[3];    /* must be zero */
 } msort_options;
 
 /* Context on CUDA device `device`.  scratch_budget_bytes caps the scratch the
@@ -78,8 +82,14 @@ const char* msort_last_error(msort_ctx* ctx);
  * gave up) and clears it. */
 msort_status msort_ctx_sync(msort_ctx* ctx, void* stream);
 
-/* Bytes of scratch a sort of n elements needs (tile sort buffer + splits). */
+/* Bytes of scratch a sort of n elements needs (tile sort buffer + splits);
+ * 0 if the options are invalid for this key/value type. */
 size_t msort_scratch_bytes(size_t n, msort_key_type kt, int with_vals, const msort_options* opt);
+
+/* The plan a sort of n elements would use: keys per tile, outputs per merge
+ * block and number of merge passes (any output pointer may be NULL). */
+msort_status msort_plan_info(size_t n, msort_key_type kt, int with_vals, const msort_options* opt, int* tile,
+                             int* merge_block, int* passes);
 
 /* In-place stable sort of d_keys[0:n). */
 msort_status msort_sort(msort_ctx* ctx, void* d_keys, size_t n, msort_key_type kt,

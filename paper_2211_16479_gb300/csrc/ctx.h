@@ -23,14 +23,11 @@ struct EventPair {
 
 struct Plan {
     int tile;       // keys per tile sort block
-    int tthreads;   // threads of a tile sort block
-    int tipt;       // keys per thread in the tile sort
-    int mthreads;   // threads of a merge block
-    int mipt;       // outputs per thread in a merge block
     int W;          // outputs per merge block
     int passes;     // merge passes after the tile sort
     int partition_mode;
     int learned_passes;
+    unsigned int* status;  // device status word of the context
 };
 
 }  // namespace msort

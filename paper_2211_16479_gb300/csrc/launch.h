@@ -1,0 +1,36 @@
+// Kernel launchers of the sort passes, instantiated per key type in
+// kern_u32.cu / kern_u64.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "ctx.h"
+
+namespace msort {
+
+// Shared memory bytes of one tile-sort / merge block.
+template <class K, bool PAIRS>
+size_t tile_smem_bytes(int tile);
+template <class K, bool PAIRS>
+size_t merge_smem_bytes(int W);
+// True when this (tile, key type, values) combination has a kernel.
+template <class K, bool PAIRS>
+bool tile_supported(int tile);
+
+template <class K, bool PAIRS>
+cudaError_t launch_tile(const Plan& pl, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n,
+                        cudaStream_t st);
+template <class K, bool PAIRS>
+cudaError_t launch_merge(const Plan& pl, const K* src, K* dst, const uint32_t* vsrc, uint32_t* vdst, size_t n,
+                         size_t L, const unsigned long long* splits, cudaStream_t st);
+template <class K>
+cudaError_t launch_partition(const Plan& pl, const K* src, size_t n, size_t L, unsigned long long* splits,
+                             cudaStream_t st);
+// Resource summary of the last kernel the calling thread prepared to launch.
+const std::string& last_launch_info();
+
+}  // namespace msort

@@ -1,0 +1,115 @@
+// Launcher definitions (included once per key type).
+#pragma once
+
+#include <cstdio>
+
+#include "launch.h"
+#include "sort_kernels.cuh"
+
+namespace msort {
+
+std::string& launch_info_ref();
+
+template <class F>
+static cudaError_t prepare(F* f, size_t smem) {
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(f));
+    char buf[200];
+    std::snprintf(buf, sizeof buf, " [regs %d, max threads %d, dyn smem %zu, max dyn %d]", fa.numRegs,
+                  fa.maxThreadsPerBlock, smem, fa.maxDynamicSharedSizeBytes);
+    launch_info_ref() = buf;
+    if (e != cudaSuccess) return e;
+    if ((int)smem <= fa.maxDynamicSharedSizeBytes) return cudaSuccess;
+    return cudaFuncSetAttribute(reinterpret_cast<const void*>(f), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+}
+
+template <class K, bool PAIRS>
+size_t tile_smem_bytes(int tile) {
+    using Item = typename TileItem<K, PAIRS>::T;
+    return sizeof(Item) * (tile + 1) + (PAIRS ? sizeof(uint32_t) * tile : 0);
+}
+
+// ipt = outputs per thread of the merge block (W = 256 * ipt).
+template <class K, bool PAIRS>
+size_t merge_smem_bytes(int W) {
+    const int ipt = W / 256;
+    return sizeof(K) * merge_slots(W, ipt, sizeof(K)) + (PAIRS ? 4 * merge_slots(W, ipt, 4) : 0);
+}
+
+template <class K, bool PAIRS>
+bool tile_supported(int tile) {
+    if (tile != 4352 && tile != 8448 && tile != 8704 && tile != 16896) return false;
+    return tile_smem_bytes<K, PAIRS>(tile) <= 227 * 1024;
+}
+
+// tile = threads * keys per thread (odd); merge blocks use 256 threads with
+// the same keys per thread, so W divides 2 * tile.
+#define MSORT_TILE_CFG(X) X(4352, 256, 17) X(8448, 256, 33) X(8704, 512, 17) X(16896, 512, 33)
+
+template <class K, bool PAIRS>
+cudaError_t launch_tile(const Plan& pl, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n,
+                        cudaStream_t st) {
+    const size_t nblocks = (n + pl.tile - 1) / pl.tile;
+    const size_t sm = tile_smem_bytes<K, PAIRS>(pl.tile);
+    if (!tile_supported<K, PAIRS>(pl.tile)) return cudaErrorInvalidConfiguration;
+    cudaError_t e;
+#define MSORT_TILE_CASE(TILE, TH, IPT)                                         \
+    if (pl.tile == TILE) {                                                     \
+        auto f = k_tile_sort<K, PAIRS, TH, IPT>;                               \
+        if ((e = prepare(f, sm)) != cudaSuccess) return e;                     \
+        f<<<(unsigned)nblocks, TH, sm, st>>>(kin, vin, kout, vout, n, pl.status); \
+        return cudaGetLastError();                                             \
+    }
+    MSORT_TILE_CFG(MSORT_TILE_CASE)
+#undef MSORT_TILE_CASE
+    return cudaErrorInvalidConfiguration;
+}
+
+template <class K, bool PAIRS>
+cudaError_t launch_merge(const Plan& pl, const K* src, K* dst, const uint32_t* vsrc, uint32_t* vdst, size_t n,
+                         size_t L, const unsigned long long* splits, cudaStream_t st) {
+    const size_t nblocks = (n + pl.W - 1) / pl.W;
+    const size_t sm = merge_smem_bytes<K, PAIRS>(pl.W);
+    cudaError_t e;
+#define MSORT_MERGE_CASE(WW, TH, IPT)                                          \
+    if (pl.W == WW) {                                                          \
+        auto f = k_merge_pass<K, PAIRS, TH, IPT>;                              \
+        if ((e = prepare(f, sm)) != cudaSuccess) return e;                     \
+        f<<<(unsigned)nblocks, TH, sm, st>>>(src, dst, vsrc, vdst, n, L, splits, pl.status); \
+        return cudaGetLastError();                                             \
+    }
+    MSORT_MERGE_CASE(4352, 256, 17)
+    MSORT_MERGE_CASE(8448, 256, 33)
+#undef MSORT_MERGE_CASE
+    return cudaErrorInvalidConfiguration;
+}
+
+template <class K>
+cudaError_t launch_partition(const Plan& pl, const K* src, size_t n, size_t L, unsigned long long* splits,
+                             cudaStream_t st) {
+    const size_t nblocks = (n + pl.W - 1) / pl.W;
+    const unsigned th = 128;
+    k_partition<K><<<(unsigned)((nblocks + th - 1) / th), th, 0, st>>>(src, n, L, (size_t)pl.W, nblocks, splits);
+    return cudaGetLastError();
+}
+
+#define MSORT_INSTANTIATE(K)                                                                                    \
+    template size_t tile_smem_bytes<K, false>(int);                                                             \
+    template size_t tile_smem_bytes<K, true>(int);                                                              \
+    template size_t merge_smem_bytes<K, false>(int);                                                            \
+    template size_t merge_smem_bytes<K, true>(int);                                                             \
+    template bool tile_supported<K, false>(int);                                                                \
+    template bool tile_supported<K, true>(int);                                                                 \
+    template cudaError_t launch_tile<K, false>(const Plan&, const K*, const uint32_t*, K*, uint32_t*, size_t,   \
+                                               cudaStream_t);                                                   \
+    template cudaError_t launch_tile<K, true>(const Plan&, const K*, const uint32_t*, K*, uint32_t*, size_t,    \
+                                              cudaStream_t);                                                    \
+    template cudaError_t launch_merge<K, false>(const Plan&, const K*, K*, const uint32_t*, uint32_t*, size_t,  \
+                                                size_t, const unsigned long long*, cudaStream_t);               \
+    template cudaError_t launch_merge<K, true>(const Plan&, const K*, K*, const uint32_t*, uint32_t*, size_t,   \
+                                               size_t, const unsigned long long*, cudaStream_t);                \
+    template cudaError_t launch_partition<K>(const Plan&, const K*, size_t, size_t, unsigned long long*,        \
+                                             cudaStream_t);
+
+}  // namespace msort

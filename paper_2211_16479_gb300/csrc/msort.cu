@@ -18,7 +18,7 @@
 
 #include "ctx.h"
 #include "learned.h"
-#include "sort_kernels.cuh"
+#include "launch.h"
 
 namespace msort {
 
@@ -88,26 +88,39 @@ static void scratch_release(msort_ctx* ctx, cudaStream_t st) {
 // ----------------------------------------------------------------------------
 // Plans
 // ----------------------------------------------------------------------------
-static constexpr int kMergeThreads = 256;
-static constexpr int kMergeIpt = 16;
+std::string& launch_info_ref() {
+    static thread_local std::string info;
+    return info;
+}
+const std::string& last_launch_info() { return launch_info_ref(); }
 
-static bool make_plan(size_t n, const msort_options* opt, Plan* pl) {
-    int tile = opt && opt->tile ? opt->tile : 4096;
+template <class K, bool PAIRS>
+static int default_tile() {
+    if (!PAIRS) return sizeof(K) == 4 ? 16896 : 8448;
+    return sizeof(K) == 4 ? 8448 : 8704;
+}
+
+template <class K, bool PAIRS>
+static bool make_plan(size_t n, const msort_options* opt, Plan* pl, std::string* why) {
     Plan p{};
-    switch (tile) {
-        case 2048: p.tthreads = 256; p.tipt = 8; break;
-        case 4096: p.tthreads = 256; p.tipt = 16; break;
-        case 8192: p.tthreads = 512; p.tipt = 16; break;
-        default: return false;
+    p.tile = opt && opt->tile ? opt->tile : default_tile<K, PAIRS>();
+    if (!tile_supported<K, PAIRS>(p.tile)) {
+        *why = "options.tile " + std::to_string(p.tile) +
+               " is not available for this key/value type (4352, 8448, 8704 or 16896)";
+        return false;
     }
-    p.tile = tile;
-    p.mthreads = kMergeThreads;
-    p.mipt = kMergeIpt;
-    p.W = p.mthreads * p.mipt;
+    // merge blocks use 256 threads and the tile's keys per thread
+    const int ipt = (p.tile == 4352 || p.tile == 8704) ? 17 : 33;
+    p.W = 256 * ipt;
+    if (opt && opt->merge_block && opt->merge_block != p.W) {
+        *why = "options.merge_block must be 0 or " + std::to_string(p.W) + " for tile " + std::to_string(p.tile);
+        return false;
+    }
     p.passes = 0;
-    for (size_t L = (size_t)tile; L < n; L *= 2) ++p.passes;
+    for (size_t L = (size_t)p.tile; L < n; L *= 2) ++p.passes;
     p.partition_mode = opt ? opt->partition_mode : 0;
     p.learned_passes = opt ? opt->learned_passes : 0;
+    p.status = nullptr;
     *pl = p;
     return true;
 }
@@ -119,74 +132,6 @@ static size_t scratch_need(size_t n, const Plan& pl) {
     size_t nblocks = (n + pl.W - 1) / pl.W;
     b += align_up((nblocks + 1) * sizeof(unsigned long long), 256);
     return b;
-}
-
-template <class K, bool PAIRS>
-static size_t tile_smem(int T) {
-    using Item = typename TileItem<K, PAIRS>::T;
-    return sizeof(Item) * spad_size<Item>(T) + (PAIRS ? sizeof(uint32_t) * T : 0);
-}
-
-template <class K, bool PAIRS>
-static size_t merge_smem(int W) {
-    return sizeof(K) * spad_size<K>(W) + (PAIRS ? sizeof(uint32_t) * spad_size<uint32_t>(W) : 0);
-}
-
-static thread_local std::string tl_launch_info;
-
-template <class F>
-static cudaError_t set_smem(F* f, size_t bytes) {
-    cudaFuncAttributes fa{};
-    cudaError_t e = cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(f));
-    char buf[256];
-    std::snprintf(buf, sizeof buf, " [regs %d, max threads %d, static smem %zu, dyn smem %zu, max dyn %d]",
-                  fa.numRegs, fa.maxThreadsPerBlock, fa.sharedSizeBytes, bytes, fa.maxDynamicSharedSizeBytes);
-    tl_launch_info = buf;
-    if (e != cudaSuccess) return e;
-    if (bytes <= 48 * 1024 || (int)bytes <= fa.maxDynamicSharedSizeBytes) return cudaSuccess;
-    return cudaFuncSetAttribute(reinterpret_cast<const void*>(f), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)bytes);
-}
-
-template <class K, bool PAIRS>
-static cudaError_t launch_tile(const Plan& pl, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n,
-                               cudaStream_t st) {
-    const size_t nblocks = (n + pl.tile - 1) / pl.tile;
-    const size_t sm = tile_smem<K, PAIRS>(pl.tile);
-    cudaError_t e = cudaSuccess;
-#define MSORT_TILE_CASE(TH, IPT)                                                                 \
-    if (pl.tthreads == TH && pl.tipt == IPT) {                                                   \
-        auto f = k_tile_sort<K, PAIRS, TH, IPT>;                                                 \
-        if ((e = set_smem(f, sm)) != cudaSuccess) return e;                                      \
-        f<<<(unsigned)nblocks, TH, sm, st>>>(kin, vin, kout, vout, n);                           \
-        return cudaGetLastError();                                                               \
-    }
-    MSORT_TILE_CASE(256, 8)
-    MSORT_TILE_CASE(256, 16)
-    MSORT_TILE_CASE(512, 16)
-#undef MSORT_TILE_CASE
-    return cudaErrorInvalidConfiguration;
-}
-
-template <class K, bool PAIRS>
-static cudaError_t launch_merge(const Plan& pl, const K* src, K* dst, const uint32_t* vsrc, uint32_t* vdst, size_t n,
-                                size_t L, const unsigned long long* splits, cudaStream_t st) {
-    const size_t nblocks = (n + pl.W - 1) / pl.W;
-    const size_t sm = merge_smem<K, PAIRS>(pl.W);
-    auto f = k_merge_pass<K, PAIRS, kMergeThreads, kMergeIpt>;
-    cudaError_t e = set_smem(f, sm);
-    if (e != cudaSuccess) return e;
-    f<<<(unsigned)nblocks, kMergeThreads, sm, st>>>(src, dst, vsrc, vdst, n, L, splits);
-    return cudaGetLastError();
-}
-
-template <class K>
-static cudaError_t launch_partition(const Plan& pl, const K* src, size_t n, size_t L, unsigned long long* splits,
-                                    cudaStream_t st) {
-    const size_t nblocks = (n + pl.W - 1) / pl.W;
-    const unsigned th = 256;
-    k_partition<K><<<(unsigned)((nblocks + th - 1) / th), th, 0, st>>>(src, n, L, (size_t)pl.W, nblocks, splits);
-    return cudaGetLastError();
 }
 
 // The whole sort on stream st.  kin may equal kout (in-place).
@@ -211,7 +156,7 @@ static msort_status run_sort(msort_ctx* ctx, const K* kin, const uint32_t* vin, 
     e = launch_tile<K, PAIRS>(pl, kin, vin, bk[cur], bv[cur], n, st);
     prof_end(ctx, KK_TILE, st);
     ++ctx->launches;
-    if (e != cudaSuccess) return cuda_fail(e, ("tile sort launch" + tl_launch_info).c_str());
+    if (e != cudaSuccess) return cuda_fail(e, ("tile sort launch" + last_launch_info()).c_str());
     const int first_learned = pl.partition_mode == 1 ? learned_first_pass(pl, n) : pl.passes;
     for (int p = 0; p < pl.passes; ++p) {
         const size_t L = (size_t)pl.tile << p;
@@ -227,7 +172,7 @@ static msort_status run_sort(msort_ctx* ctx, const K* kin, const uint32_t* vin, 
         e = launch_merge<K, PAIRS>(pl, bk[cur], bk[cur ^ 1], bv[cur], bv[cur ^ 1], n, L, splits, st);
         prof_end(ctx, KK_MERGE, st);
         ++ctx->launches;
-        if (e != cudaSuccess) return cuda_fail(e, ("merge pass launch" + tl_launch_info).c_str());
+        if (e != cudaSuccess) return cuda_fail(e, ("merge pass launch" + last_launch_info()).c_str());
         cur ^= 1;
     }
     return MSORT_OK;
@@ -237,11 +182,13 @@ template <class K, bool PAIRS>
 static msort_status sort_entry(msort_ctx* ctx, const void* kin, const uint32_t* vin, void* kout, uint32_t* vout,
                                size_t n, const msort_options* opt, cudaStream_t st) {
     Plan pl;
-    if (!make_plan(n, opt, &pl)) return fail(MSORT_ERR_INVALID_ARG, "options.tile must be 0, 2048, 4096 or 8192");
+    std::string why;
+    if (!make_plan<K, PAIRS>(n, opt, &pl, &why)) return fail(MSORT_ERR_INVALID_ARG, why);
     if (n == 0) return MSORT_OK;
     std::lock_guard<std::mutex> g(ctx->mu);
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    pl.status = ctx->d_status;
     msort_status s = ensure_scratch(ctx, scratch_need<K, PAIRS>(n, pl), st);
     if (s != MSORT_OK) return s;
     if (pl.partition_mode == 1 && pl.passes > 0) {
@@ -264,6 +211,25 @@ static msort_status check_common(msort_ctx* ctx, msort_key_type kt, const msort_
         if (opt->learned_passes < 0) return fail(MSORT_ERR_INVALID_ARG, "options.learned_passes must be >= 0");
     }
     return MSORT_OK;
+}
+
+template <class K, bool PAIRS>
+msort_status plan_info_for(size_t n, const msort_options* opt, int* tile, int* W, int* passes) {
+    Plan pl;
+    std::string why;
+    if (!make_plan<K, PAIRS>(n, opt, &pl, &why)) return fail(MSORT_ERR_INVALID_ARG, why);
+    if (tile) *tile = pl.tile;
+    if (W) *W = pl.W;
+    if (passes) *passes = pl.passes;
+    return MSORT_OK;
+}
+
+template <class K, bool PAIRS>
+size_t scratch_bytes_for(size_t n, const msort_options* opt) {
+    Plan pl;
+    std::string why;
+    if (!make_plan<K, PAIRS>(n, opt, &pl, &why)) return 0;
+    return scratch_need<K, PAIRS>(n, pl);
 }
 
 }  // namespace msort
@@ -334,10 +300,19 @@ msort_status msort_ctx_sync(msort_ctx* ctx, void* stream) {
 }
 
 size_t msort_scratch_bytes(size_t n, msort_key_type kt, int with_vals, const msort_options* opt) {
-    Plan pl;
-    if (!make_plan(n, opt, &pl)) return 0;
-    if (kt == MSORT_U32) return with_vals ? scratch_need<uint32_t, true>(n, pl) : scratch_need<uint32_t, false>(n, pl);
-    return with_vals ? scratch_need<uint64_t, true>(n, pl) : scratch_need<uint64_t, false>(n, pl);
+    if (kt == MSORT_U32) return with_vals ? scratch_bytes_for<uint32_t, true>(n, opt) : scratch_bytes_for<uint32_t, false>(n, opt);
+    return with_vals ? scratch_bytes_for<uint64_t, true>(n, opt) : scratch_bytes_for<uint64_t, false>(n, opt);
+}
+
+msort_status msort_plan_info(size_t n, msort_key_type kt, int with_vals, const msort_options* opt, int* tile,
+                             int* merge_block, int* passes) {
+    if (kt == MSORT_U32)
+        return with_vals ? plan_info_for<uint32_t, true>(n, opt, tile, merge_block, passes)
+                         : plan_info_for<uint32_t, false>(n, opt, tile, merge_block, passes);
+    if (kt == MSORT_U64)
+        return with_vals ? plan_info_for<uint64_t, true>(n, opt, tile, merge_block, passes)
+                         : plan_info_for<uint64_t, false>(n, opt, tile, merge_block, passes);
+    return fail(MSORT_ERR_INVALID_ARG, "unknown key type");
 }
 
 msort_status msort_sort_copy(msort_ctx* ctx, const void* kin, const uint32_t* vin, void* kout, uint32_t* vout,

@@ -9,29 +9,41 @@
 //
 // GPU mapping:
 //  * Tile sort (a "chunk" of the multiprocessing design): one thread block
-//    sorts T = THREADS * IPT keys.  Each thread holds IPT keys in registers;
-//    a bitonic network sorts each warp's 32 * IPT keys (in-thread stages are
-//    register compare-exchanges, cross-lane stages use __shfl_xor_sync), and
-//    log2(THREADS / 32) shared-memory merge rounds join the warp runs.
-//    Stability for key-value tiles comes from comparing (key, tile position):
-//    all such items are distinct, so any sorting network yields the stable
-//    order.
+//    sorts T = THREADS * IPT keys.  Each thread sorts IPT keys in registers
+//    with a Batcher odd-even merge network, then log2(THREADS) merge-path
+//    rounds in shared memory join the per-thread runs.  Key-value tiles
+//    compare (key, tile position), which makes the network stable.
 //  * Partition: the Merge Path co-rank (Odeh et al., cited in Section
 //    "Related Research").  For merged output position d of runs A and B, the
 //    split a(d) is the number of A elements among the first d outputs; with
 //    ties taken from A it is the first a in [max(0, d-|B|), min(d, |A|)]
 //    with B[d-1-a] < A[a], found by binary search.
 //  * Merge pass (one round of the merge tree): each block produces W
-//    consecutive outputs.  Its input windows A[a(d0):a(d1)) and
-//    B[d0-a(d0):d1-a(d1)) are staged in shared memory with coalesced loads,
-//    every thread merges IPT outputs from its own co-rank, and the block
-//    writes its W outputs back with coalesced stores.
+//    consecutive outputs.  Its windows A[a(d0):a(d1)) and
+//    B[d0-a(d0):d1-a(d1)) arrive in shared memory by 1-D bulk TMA copies;
+//    each thread merges IPT outputs from its own co-rank; the block's outputs
+//    leave by one bulk TMA store.
+//
+// IPT is odd (17 or 33): consecutive threads then start their merges at
+// shared-memory words that differ by an odd stride, which spreads a warp's
+// reads over the 32 banks without any index padding arithmetic.  Tiles and
+// merge blocks are therefore THREADS * IPT keys (e.g. 256 * 33 = 8448); all
+// run lengths are that times a power of two, so a merge block never
+// straddles two merge pairs.
 #pragma once
 
 #include <cstddef>
 #include <cstdint>
+#include <utility>
+
+#include "ptx.cuh"
 
 namespace msort {
+
+// Device status bits (a kernel that gives up a bounded wait sets one).
+constexpr unsigned int kStatusTimeout = 1u;
+// About one second at GB300 clocks.
+constexpr long long kWaitLimitCycles = 2000000000ll;
 
 // ---------------------------------------------------------------------------
 // Items of a tile: the key alone, or (key, position in tile) for pairs.
@@ -60,7 +72,6 @@ struct TileItem<K, false> {
     static __device__ __forceinline__ bool less(T a, T b) { return a < b; }
     static __device__ __forceinline__ T lo(T a, T b) { return a < b ? a : b; }
     static __device__ __forceinline__ T hi(T a, T b) { return a < b ? b : a; }
-    static __device__ __forceinline__ T shfl_xor(T v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
 };
 
 // 32-bit key and 32-bit tile position packed as (key << 32 | pos).
@@ -73,7 +84,6 @@ struct TileItem<uint32_t, true> {
     static __device__ __forceinline__ bool less(T a, T b) { return a < b; }
     static __device__ __forceinline__ T lo(T a, T b) { return a < b ? a : b; }
     static __device__ __forceinline__ T hi(T a, T b) { return a < b ? b : a; }
-    static __device__ __forceinline__ T shfl_xor(T v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
 };
 
 template <>
@@ -85,98 +95,97 @@ struct TileItem<uint64_t, true> {
     static __device__ __forceinline__ bool less(T a, T b) { return a.k < b.k || (a.k == b.k && a.p < b.p); }
     static __device__ __forceinline__ T lo(T a, T b) { return less(b, a) ? b : a; }
     static __device__ __forceinline__ T hi(T a, T b) { return less(b, a) ? a : b; }
-    static __device__ __forceinline__ T shfl_xor(T v, int m) {
-        return KeyPos64{__shfl_xor_sync(0xffffffffu, v.k, m), __shfl_xor_sync(0xffffffffu, v.p, m)};
-    }
 };
 
-// Shared-memory index with one pad element per 128-byte row, so that the
-// blocked (thread-major) and striped (element-major) access patterns of a
-// warp fall in distinct banks.
-template <class T>
-__device__ __forceinline__ int spad(int i) {
-    constexpr int ROW = 128 / (int)sizeof(T) > 0 ? 128 / (int)sizeof(T) : 1;
-    return i + i / ROW;
-}
-template <class T>
-__host__ __device__ constexpr int spad_size(int n) {
-    return n + n / (128 / (int)sizeof(T) > 0 ? 128 / (int)sizeof(T) : 1) + 1;
-}
-
 // ---------------------------------------------------------------------------
-// Warp-level bitonic sort of 32 * IPT items, blocked layout:
-// lane l holds positions l * IPT + i, i in [0, IPT).
+// In-register sort of one thread's N items: Batcher's odd-even merge sort
+// network (K. E. Batcher, "Sorting networks and their applications", 1968),
+// all comparators ascending.  For N not a power of two this is the network
+// of the next power of two with every comparator that touches an index >= N
+// removed (those positions would hold +infinity and never move).  The
+// comparator list is built at compile time and applied by a fold
+// expression, so every register index is a constant.
 // ---------------------------------------------------------------------------
-template <class TI, int IPT>
-__device__ __forceinline__ void warp_bitonic_sort(typename TI::T (&r)[IPT], int lane) {
-    using Item = typename TI::T;
-    static_assert((IPT & (IPT - 1)) == 0, "IPT must be a power of two");
-#pragma unroll
-    for (int k = 2; k <= 32 * IPT; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j >= IPT) {
-                // Partner lives in lane ^ (j / IPT), same register.
-                const int m = j / IPT;
-                const bool asc = ((lane * IPT) & k) == 0;
-                const bool lower = (lane & m) == 0;
-                const bool keep_lo = (asc == lower);
-#pragma unroll
-                for (int i = 0; i < IPT; ++i) {
-                    Item p = TI::shfl_xor(r[i], m);
-                    r[i] = keep_lo ? TI::lo(r[i], p) : TI::hi(r[i], p);
-                }
-            } else {
-                // Partner is register i ^ j of the same thread.
-#pragma unroll
-                for (int i = 0; i < IPT; ++i) {
-                    if ((i & j) == 0) {
-                        const bool asc = (((lane * IPT) + i) & k) == 0;
-                        Item x = r[i], y = r[i | j];
-                        Item l = TI::lo(x, y), h = TI::hi(x, y);
-                        r[i] = asc ? l : h;
-                        r[i | j] = asc ? h : l;
-                    }
-                }
-            }
-        }
+template <int N>
+struct OddEvenNet {
+    struct Pairs {
+        unsigned short a[N * N], b[N * N];
+        int count;
+    };
+    static constexpr Pairs build() {
+        Pairs r{};
+        r.count = 0;
+        for (int p = 1; p < N; p <<= 1)
+            for (int k = p; k >= 1; k >>= 1)
+                for (int j = k % p; j + k < N; j += 2 * k)
+                    for (int i = 0; i < k && i + j + k < N; ++i)
+                        if ((i + j) / (2 * p) == (i + j + k) / (2 * p)) {
+                            r.a[r.count] = (unsigned short)(i + j);
+                            r.b[r.count] = (unsigned short)(i + j + k);
+                            ++r.count;
+                        }
+        return r;
     }
+    static constexpr Pairs net = build();
+};
+
+template <class TI, int N, int C>
+__device__ __forceinline__ void net_cas(typename TI::T (&r)[N]) {
+    constexpr int a = OddEvenNet<N>::net.a[C];
+    constexpr int b = OddEvenNet<N>::net.b[C];
+    const typename TI::T x = r[a], y = r[b];
+    r[a] = TI::lo(x, y);
+    r[b] = TI::hi(x, y);
 }
 
-// One shared-memory merge round inside a tile: runs of length R (power of
-// two) at [2gR, 2gR+R) and [2gR+R, 2gR+2R) merge into 2R; thread t produces
-// outputs [t*IPT, t*IPT+IPT) into registers.
+template <class TI, int N, int... C>
+__device__ __forceinline__ void net_apply(typename TI::T (&r)[N], std::integer_sequence<int, C...>) {
+    (net_cas<TI, N, C>(r), ...);
+}
+
+template <class TI, int N>
+__device__ __forceinline__ void thread_sort(typename TI::T (&r)[N]) {
+    net_apply<TI, N>(r, std::make_integer_sequence<int, OddEvenNet<N>::net.count>{});
+}
+
+// Byte-offset shared-memory access (keeps the merge loops on 32-bit
+// offsets: one add per step, no index scaling).
+template <class T>
+__device__ __forceinline__ T sld(const unsigned char* base, int off) {
+    return *reinterpret_cast<const T*>(base + off);
+}
+
+// One shared-memory merge round inside a tile: the runs of length
+// R = IPT << lg at [2gR, 2gR + R) and [2gR + R, 2gR + 2R) merge into 2R;
+// thread t produces outputs [t*IPT, t*IPT + IPT) into registers.  Ties go to
+// the left run.  Reads may touch one item past the tile (slack item).
 template <class TI, int IPT>
-__device__ __forceinline__ void smem_merge_round(const typename TI::T* s, int R, int t,
-                                                 typename TI::T (&r)[IPT]) {
+__device__ __forceinline__ void smem_merge_round(const unsigned char* s, int lg, int t, typename TI::T (&r)[IPT]) {
     using Item = typename TI::T;
-    const int p0 = t * IPT;
-    const int pb = p0 & ~(2 * R - 1);
-    const int diag = p0 - pb;
+    constexpr int SZ = (int)sizeof(Item);
+    const int R = IPT << lg;
+    const int tpp = 2 << lg;  // threads per merge pair
+    const int pb = (t & ~(tpp - 1)) * IPT;
+    const int diag = (t & (tpp - 1)) * IPT;
+    const int A0 = pb * SZ, B0 = (pb + R) * SZ;
     int lo = diag > R ? diag - R : 0;
     int hi = diag < R ? diag : R;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (!TI::less(s[spad<Item>(pb + R + diag - 1 - mid)], s[spad<Item>(pb + mid)]))
+        if (!TI::less(sld<Item>(s, B0 + (diag - 1 - mid) * SZ), sld<Item>(s, A0 + mid * SZ)))
             lo = mid + 1;
         else
             hi = mid;
     }
-    int ai = pb + lo, bi = pb + R + diag - lo;
-    const int aend = pb + R, bend = pb + 2 * R;
-    Item av = s[spad<Item>(ai < aend ? ai : aend - 1)];
-    Item bv = s[spad<Item>(bi < bend ? bi : bend - 1)];
+    int ao = A0 + lo * SZ, bo = B0 + (diag - lo) * SZ;
+    const int ae = B0, be = B0 + R * SZ;
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
-        const bool take_a = (bi >= bend) || (ai < aend && !TI::less(bv, av));
-        r[i] = take_a ? av : bv;
-        if (take_a) {
-            ++ai;
-            if (ai < aend) av = s[spad<Item>(ai)];
-        } else {
-            ++bi;
-            if (bi < bend) bv = s[spad<Item>(bi)];
-        }
+        const Item av = sld<Item>(s, ao), bv = sld<Item>(s, bo);
+        const bool ta = ao < ae && (bo >= be || !TI::less(bv, av));
+        r[i] = ta ? av : bv;
+        ao += ta ? SZ : 0;
+        bo += ta ? 0 : SZ;
     }
 }
 
@@ -188,100 +197,100 @@ __device__ __forceinline__ bool aligned16(const K* p) {
 // ---------------------------------------------------------------------------
 // Tile sort: block b sorts kin[b*T, min((b+1)*T, n)) into kout at the same
 // place.  kin may equal kout (each block reads its whole tile first).
-// Dynamic shared memory: spad_size<Item>(T) items, then T uint32 values.
+// Dynamic shared memory: (T + 1) items, then T uint32 values for pairs.
 // ---------------------------------------------------------------------------
 template <class K, bool PAIRS, int THREADS, int IPT>
 __global__ void __launch_bounds__(THREADS)
-k_tile_sort(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n) {
+k_tile_sort(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n, unsigned int* status) {
     using TI = TileItem<K, PAIRS>;
     using Item = typename TI::T;
     constexpr int T = THREADS * IPT;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
     Item* s = reinterpret_cast<Item*>(smem_raw);
-    uint32_t* sv = reinterpret_cast<uint32_t*>(smem_raw + sizeof(Item) * spad_size<Item>(T));
+    uint32_t* sv = reinterpret_cast<uint32_t*>(smem_raw + sizeof(Item) * (T + 1));
 
     const size_t base = (size_t)blockIdx.x * T;
     const int valid = (int)((n - base) < (size_t)T ? (n - base) : (size_t)T);
-    const int t = threadIdx.x, lane = t & 31;
+    const int t = threadIdx.x;
     const K* src = kin + base;
+    K* dst = kout + base;
+
+    // Full, aligned keys-only tiles arrive by one bulk copy.
+    const bool bulk = !PAIRS && valid == T && aligned16(src);
+    if (bulk) {
+        if (t == 0) {
+            mbar_init(&bar, 1);
+            fence_mbar_init();
+            mbar_arrive_expect_tx(&bar, (uint32_t)(T * sizeof(K)));
+            tma_load_1d(s, src, (uint32_t)(T * sizeof(K)), &bar);
+        }
+        __syncthreads();
+        if (!mbar_wait_bounded(&bar, 0, kWaitLimitCycles)) {
+            if (t == 0) atomicOr(status, kStatusTimeout);
+            mbar_wait_bounded(&bar, 0, kWaitLimitCycles);
+            return;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) {
+            const int p = i * THREADS + t;
+            s[p] = TI::make(p < valid ? src[p] : key_max<K>(), (uint32_t)p);
+        }
+        if (PAIRS) {
+            for (int p = t; p < valid; p += THREADS) sv[p] = vin[base + p];
+        }
+        __syncthreads();
+    }
 
     Item r[IPT];
-    constexpr int PER = 16 / (int)sizeof(K);
-    if (valid == T && aligned16(src)) {
-        K k[IPT];
 #pragma unroll
-        for (int q = 0; q < IPT / PER; ++q) {
-            uint4 v = reinterpret_cast<const uint4*>(src + t * IPT)[q];
-            const K* pv = reinterpret_cast<const K*>(&v);
-#pragma unroll
-            for (int e = 0; e < PER; ++e) k[q * PER + e] = pv[e];
-        }
-#pragma unroll
-        for (int i = 0; i < IPT; ++i) r[i] = TI::make(k[i], (uint32_t)(t * IPT + i));
-    } else {
-#pragma unroll
-        for (int i = 0; i < IPT; ++i) {
-            const int p = t * IPT + i;
-            r[i] = TI::make(p < valid ? src[p] : key_max<K>(), (uint32_t)p);
-        }
-    }
-    if (PAIRS) {
-        for (int p = t; p < valid; p += THREADS) sv[p] = vin[base + p];
-    }
+    for (int i = 0; i < IPT; ++i) r[i] = s[t * IPT + i];
+    thread_sort<TI, IPT>(r);
 
-    warp_bitonic_sort<TI, IPT>(r, lane);
-
-    constexpr int R0 = 32 * IPT;
-    if (T > R0) {
-#pragma unroll
-        for (int i = 0; i < IPT; ++i) s[spad<Item>(t * IPT + i)] = r[i];
+    const unsigned char* sb = smem_raw;
+    int lg = 0;
+    for (int R = IPT; R < T; R *= 2, ++lg) {
         __syncthreads();
-        for (int R = R0; R < T; R *= 2) {
-            smem_merge_round<TI, IPT>(s, R, t, r);
-            if (2 * R < T) {
-                __syncthreads();
 #pragma unroll
-                for (int i = 0; i < IPT; ++i) s[spad<Item>(t * IPT + i)] = r[i];
-                __syncthreads();
-            }
-        }
+        for (int i = 0; i < IPT; ++i) s[t * IPT + i] = r[i];
+        __syncthreads();
+        smem_merge_round<TI, IPT>(sb, lg, t, r);
     }
-    if (PAIRS) __syncthreads();
+    __syncthreads();
 
-    K* dst = kout + base;
-    if (valid == T && aligned16(dst)) {
+    if (!PAIRS) {
+        K* sk = reinterpret_cast<K*>(smem_raw);
 #pragma unroll
-        for (int q = 0; q < IPT / PER; ++q) {
-            uint4 v;
-            K* pv = reinterpret_cast<K*>(&v);
-#pragma unroll
-            for (int e = 0; e < PER; ++e) pv[e] = TI::key(r[q * PER + e]);
-            reinterpret_cast<uint4*>(dst + t * IPT)[q] = v;
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < IPT; ++i) {
-            const int p = t * IPT + i;
-            if (p < valid) dst[p] = TI::key(r[i]);
-        }
-    }
-    if (PAIRS) {
-        uint32_t* vd = vout + base;
-        if (valid == T && aligned16(vd)) {
-#pragma unroll
-            for (int q = 0; q < IPT / 4; ++q) {
-                uint4 v;
-                v.x = sv[TI::pos(r[4 * q + 0])];
-                v.y = sv[TI::pos(r[4 * q + 1])];
-                v.z = sv[TI::pos(r[4 * q + 2])];
-                v.w = sv[TI::pos(r[4 * q + 3])];
-                reinterpret_cast<uint4*>(vd + t * IPT)[q] = v;
+        for (int i = 0; i < IPT; ++i) sk[t * IPT + i] = TI::key(r[i]);
+        if (valid == T && aligned16(dst)) {
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (t == 0) {
+                tma_store_1d(dst, sk, (uint32_t)(T * sizeof(K)));
+                tma_store_commit();
+                tma_store_wait_read();
             }
         } else {
+            __syncthreads();
 #pragma unroll
             for (int i = 0; i < IPT; ++i) {
-                const int p = t * IPT + i;
-                if (p < valid) vd[p] = sv[TI::pos(r[i])];
+                const int p = i * THREADS + t;
+                if (p < valid) dst[p] = sk[p];
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) s[t * IPT + i] = r[i];
+        __syncthreads();
+        uint32_t* vd = vout + base;
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) {
+            const int p = i * THREADS + t;
+            if (p < valid) {
+                const Item it = s[p];
+                dst[p] = TI::key(it);
+                vd[p] = sv[TI::pos(it)];
             }
         }
     }
@@ -334,21 +343,72 @@ __global__ void k_partition(const K* __restrict__ src, size_t n, size_t L, size_
     splits[c] = corank_search(A, g.alen, A + g.alen, g.blen, out0 - g.pb);
 }
 
+// Placement of one input window in shared memory: its first element sits at
+// element offset `off` of the region; elements [head, head + nbulk) move by a
+// bulk copy (16-byte aligned on both sides), the rest by scalar loads.
+struct Window {
+    int off;    // element offset of window element 0 in the shared array
+    int head;   // elements before the bulk part
+    int nbulk;  // elements in the bulk part (multiple of 16 / element size)
+    int end;    // first element offset after the window and its slack
+};
+
+template <class E>
+__device__ __forceinline__ Window place_window(const E* g, int n, int region, int slack) {
+    constexpr int EPC = 16 / (int)sizeof(E);
+    Window w;
+    int head = (int)(((16u - (reinterpret_cast<uintptr_t>(g) & 15u)) & 15u) / sizeof(E));
+    if (head > n) head = n;
+    w.head = head;
+    w.nbulk = ((n - head) / EPC) * EPC;
+    w.off = region + (EPC - head) % EPC;
+    const int e = w.off + n + slack;
+    w.end = (e + EPC - 1) / EPC * EPC;
+    return w;
+}
+
+// Scalar part of a window: the head and tail elements (fewer than 16 bytes
+// each) and `slack` copies of `fill` after the window.  Warp w0 moves the
+// head and tail, warp w0 + 1 writes the fill.
+template <class E>
+__device__ __forceinline__ void window_scalars(const E* g, int n, const Window& w, E* s, int warp, int lane, int w0,
+                                               int slack, E fill) {
+    if (warp == w0) {
+        if (lane < w.head) s[w.off + lane] = g[lane];
+        const int t0 = w.head + w.nbulk;
+        if (lane < n - t0) s[w.off + t0 + lane] = g[t0 + lane];
+    } else if (warp == w0 + 1) {
+        for (int i = lane; i < slack; i += 32) s[w.off + n + i] = fill;
+    }
+}
+
+// Shared slots of one merge-pass region (window A, window B, slack and
+// alignment), rounded to 16 elements so the next region stays 16-byte
+// aligned.
+__host__ __device__ constexpr int merge_slots(int W, int IPT, int esize) {
+    return (W + 2 * IPT + 6 * (16 / esize) + 8 + 15) / 16 * 16;
+}
+
 // ---------------------------------------------------------------------------
 // Merge pass: block c writes dst[c*W, min((c+1)*W, pair end)).
-// Dynamic shared memory: spad_size<K>(W) keys, then spad_size<uint32>(W)
-// values for pairs.
+// Dynamic shared memory: merge_slots(W, IPT, sizeof(K)) keys, then for pairs
+// merge_slots(W, IPT, 4) values.
 // ---------------------------------------------------------------------------
 template <class K, bool PAIRS, int THREADS, int IPT>
 __global__ void __launch_bounds__(THREADS)
 k_merge_pass(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __restrict__ vsrc,
-             uint32_t* __restrict__ vdst, size_t n, size_t L, const unsigned long long* __restrict__ splits) {
+             uint32_t* __restrict__ vdst, size_t n, size_t L, const unsigned long long* __restrict__ splits,
+             unsigned int* status) {
     constexpr int W = THREADS * IPT;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int KS = (int)sizeof(K);
+    constexpr int KSLOTS = merge_slots(W, IPT, KS);
+    constexpr int VSLOTS = merge_slots(W, IPT, 4);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
     K* sk = reinterpret_cast<K*>(smem_raw);
-    uint32_t* sv = reinterpret_cast<uint32_t*>(smem_raw + sizeof(K) * spad_size<K>(W));
+    uint32_t* sv = reinterpret_cast<uint32_t*>(smem_raw + KS * KSLOTS);
 
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const size_t c = blockIdx.x;
     const size_t out0 = c * W;
     const PassGeom g = pass_geom(out0, n, L);
@@ -359,68 +419,121 @@ k_merge_pass(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __r
     const size_t a1 = (d1 == dend) ? g.alen : (size_t)splits[c + 1];
     const int nA = (int)(a1 - a0);
     const int total = (int)(d1 - d0);
-    const K* A = src + g.pb + a0;
-    const K* B = src + g.pb + g.alen + (d0 - a0);
+    const int nB = total - nA;
+    const K* gA = src + g.pb + a0;
+    const K* gB = src + g.pb + g.alen + (d0 - a0);
 
-    for (int i = t; i < total; i += THREADS) sk[spad<K>(i)] = i < nA ? A[i] : B[i - nA];
+    const Window wA = place_window(gA, nA, 0, IPT);
+    const Window wB = place_window(gB, nB, wA.end, IPT);
+    Window vA{}, vB{};
+    const uint32_t* gvA = nullptr;
+    const uint32_t* gvB = nullptr;
     if (PAIRS) {
-        const uint32_t* VA = vsrc + g.pb + a0;
-        const uint32_t* VB = vsrc + g.pb + g.alen + (d0 - a0);
-        for (int i = t; i < total; i += THREADS) sv[spad<uint32_t>(i)] = i < nA ? VA[i] : VB[i - nA];
+        gvA = vsrc + g.pb + a0;
+        gvB = vsrc + g.pb + g.alen + (d0 - a0);
+        vA = place_window(gvA, nA, 0, 0);
+        vB = place_window(gvB, nB, vA.end, 0);
+    }
+
+    if (t == 0) {
+        uint32_t bytes = (uint32_t)((wA.nbulk + wB.nbulk) * KS);
+        if (PAIRS) bytes += (uint32_t)((vA.nbulk + vB.nbulk) * 4);
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        mbar_arrive_expect_tx(&bar, bytes);
+        if (wA.nbulk) tma_load_1d(sk + wA.off + wA.head, gA + wA.head, (uint32_t)(wA.nbulk * KS), &bar);
+        if (wB.nbulk) tma_load_1d(sk + wB.off + wB.head, gB + wB.head, (uint32_t)(wB.nbulk * KS), &bar);
+        if (PAIRS) {
+            if (vA.nbulk) tma_load_1d(sv + vA.off + vA.head, gvA + vA.head, (uint32_t)(vA.nbulk * 4), &bar);
+            if (vB.nbulk) tma_load_1d(sv + vB.off + vB.head, gvB + vB.head, (uint32_t)(vB.nbulk * 4), &bar);
+        }
+    }
+    window_scalars(gA, nA, wA, sk, warp, lane, 1, IPT, key_max<K>());
+    window_scalars(gB, nB, wB, sk, warp, lane, 3, IPT, key_max<K>());
+    if (PAIRS) {
+        window_scalars(gvA, nA, vA, sv, warp, lane, 5, 0, 0u);
+        window_scalars(gvB, nB, vB, sv, warp, lane, 6, 0, 0u);
     }
     __syncthreads();
+    if (!mbar_wait_bounded(&bar, 0, kWaitLimitCycles)) {
+        if (t == 0) atomicOr(status, kStatusTimeout);
+        mbar_wait_bounded(&bar, 0, kWaitLimitCycles);
+        return;
+    }
 
-    // Co-rank of this thread's first output inside the staged window.
+    // Co-rank of this thread's first output inside the staged windows.
+    const unsigned char* sb = smem_raw;
+    const int A0 = wA.off * KS, B0 = wB.off * KS;
     const int diag = t * IPT < total ? t * IPT : total;
-    const int nB = total - nA;
     int lo = diag > nB ? diag - nB : 0;
     int hi = diag < nA ? diag : nA;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (sk[spad<K>(mid)] <= sk[spad<K>(nA + diag - 1 - mid)])
+        if (sld<K>(sb, A0 + mid * KS) <= sld<K>(sb, B0 + (diag - 1 - mid) * KS))
             lo = mid + 1;
         else
             hi = mid;
     }
-    int ai = lo, bi = nA + diag - lo;
-    K av = sk[spad<K>(ai < nA ? ai : 0)];
-    K bv = sk[spad<K>(bi < total ? bi : 0)];
+    int ao = A0 + lo * KS, bo = B0 + (diag - lo) * KS;
     K ok[IPT];
     uint32_t ov[PAIRS ? IPT : 1];
+    if (!PAIRS) {
+        // Both windows are followed by IPT copies of the largest key, so no
+        // bounds checks are needed: once a run is exhausted its "next" key
+        // is the maximum, and whenever that maximum is taken the remaining
+        // keys of the other run are all the maximum too.
 #pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-        const bool take_a = (bi >= total) || (ai < nA && av <= bv);
-        ok[i] = take_a ? av : bv;
-        if (PAIRS) {
-            // past the block's last output both runs are exhausted; clamp the
-            // (unused) gather index into the staged window
-            const int from = take_a ? ai : bi;
-            ov[i] = sv[spad<uint32_t>(from < total ? from : total - 1)];
+        for (int i = 0; i < IPT; ++i) {
+            const K av = sld<K>(sb, ao), bv = sld<K>(sb, bo);
+            const bool ta = av <= bv;
+            ok[i] = ta ? av : bv;
+            ao += ta ? KS : 0;
+            bo += ta ? 0 : KS;
         }
-        if (take_a) {
-            ++ai;
-            if (ai < nA) av = sk[spad<K>(ai)];
-        } else {
-            ++bi;
-            if (bi < total) bv = sk[spad<K>(bi)];
+    } else {
+        const int ae = A0 + nA * KS, be = B0 + nB * KS;
+        const int vshiftA = vA.off - wA.off, vshiftB = vB.off - wB.off;
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) {
+            const K av = sld<K>(sb, ao), bv = sld<K>(sb, bo);
+            const bool ta = ao < ae && (bo >= be || av <= bv);
+            ok[i] = ta ? av : bv;
+            // value slot: the same element of the window in the value region
+            ov[i] = ta ? (uint32_t)(ao / KS + vshiftA) : (uint32_t)(bo / KS + vshiftB);
+            ao += ta ? KS : 0;
+            bo += ta ? 0 : KS;
         }
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) ov[i] = sv[ov[i] < (uint32_t)VSLOTS ? ov[i] : 0u];
     }
     __syncthreads();
+
+    // Outputs back to shared memory (thread t at [t*IPT, t*IPT + IPT)),
+    // then out with one bulk store per array.
+    const int mine = total - t * IPT;
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
-        const int p = t * IPT + i;
-        if (p < total) {
-            sk[spad<K>(p)] = ok[i];
-            if (PAIRS) sv[spad<uint32_t>(p)] = ov[i];
+        if (i < mine) {
+            sk[t * IPT + i] = ok[i];
+            if (PAIRS) sv[t * IPT + i] = ov[i];
         }
     }
-    __syncthreads();
     K* D = dst + out0;
-    for (int i = t; i < total; i += THREADS) D[i] = sk[spad<K>(i)];
-    if (PAIRS) {
-        uint32_t* VD = vdst + out0;
-        for (int i = t; i < total; i += THREADS) VD[i] = sv[spad<uint32_t>(i)];
+    uint32_t* VD = PAIRS ? vdst + out0 : nullptr;
+    const bool dst_ok = aligned16(D) && (!PAIRS || aligned16(VD));
+    const int nbk = dst_ok ? (total * KS / 16) * 16 / KS : 0;      // keys by bulk store
+    const int nbv = dst_ok && PAIRS ? (total * 4 / 16) * 16 / 4 : 0;  // values by bulk store
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (t == 0) {
+        if (nbk) tma_store_1d(D, sk, (uint32_t)(nbk * KS));
+        if (PAIRS && nbv) tma_store_1d(VD, sv, (uint32_t)(nbv * 4));
+        tma_store_commit();
     }
+    for (int i = nbk + t; i < total; i += THREADS) D[i] = sk[i];
+    if (PAIRS)
+        for (int i = nbv + t; i < total; i += THREADS) VD[i] = sv[i];
+    if (t == 0) tma_store_wait_read();
 }
 
 }  // namespace msort

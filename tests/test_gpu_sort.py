@@ -16,9 +16,9 @@ ms = pytest.importorskip("paper_2211_16479_gb300")
 
 pytestmark = pytest.mark.gpu
 
-SIZES = [0, 1, 2, 31, 32, 33, 511, 2047, 2048, 2049, 4095, 4096, 4097, 3 * 4096 + 5, 8191, 8193,
+SIZES = [0, 1, 2, 16, 17, 18, 33, 34, 511, 4351, 4352, 4353, 8447, 8448, 8449, 3 * 8448 + 5, 16896, 16897,
          65536, 65537, 3 * 65536 + 77, (1 << 20) + 12345]
-TILES = [2048, 4096, 8192]
+TILES = [4352, 8448, 8704, 16896]
 
 
 @pytest.fixture(scope="module")
@@ -48,7 +48,7 @@ def test_keys_u32_uniform(ctx, n, tile):
 
 
 @pytest.mark.parametrize("tile", TILES)
-@pytest.mark.parametrize("n", [1, 33, 4097, 3 * 4096 + 5, 65537, (1 << 20) + 12345])
+@pytest.mark.parametrize("n", [1, 33, 4353, 3 * 8448 + 5, 65537, (1 << 20) + 12345])
 @pytest.mark.parametrize("kt", ["u32", "u64"])
 def test_pairs_stable(ctx, n, tile, kt):
     if kt == "u32":
@@ -57,6 +57,10 @@ def test_pairs_stable(ctx, n, tile, kt):
         keys, _ = synth.dup_u64(n, 2, distinct=211)
     vals = np.arange(n, dtype=np.uint32)
     dk, dv = to_dev(keys), to_dev(vals)
+    if kt == "u64" and tile == 16896:
+        with pytest.raises(ms.MsortError):   # 16-byte items do not fit shared memory
+            ms.msort_sort_pairs(ctx, dk, dv, options={"tile": tile})
+        return
     ms.msort_sort_pairs(ctx, dk, dv, options={"tile": tile})
     ek, ev = oracle.sort(keys, vals)
     assert np.array_equal(to_host(dk), ek)
@@ -64,7 +68,7 @@ def test_pairs_stable(ctx, n, tile, kt):
 
 
 @pytest.mark.parametrize("tile", TILES)
-@pytest.mark.parametrize("n", [0, 5, 4096, 12345, (1 << 19) + 3])
+@pytest.mark.parametrize("n", [0, 5, 4352, 12345, (1 << 19) + 3])
 def test_keys_u64(ctx, n, tile):
     keys = synth.uniform_u64(n, 3)
     if n > 10:
@@ -129,6 +133,10 @@ def test_invalid_arguments(ctx):
     assert e.value.status == ms.MSORT_ERR_INVALID_ARG
     with pytest.raises(ms.MsortError):
         ms.msort_sort(ctx, d, options={"partition_mode": 7})
+    with pytest.raises(ms.MsortError):
+        ms.msort_sort(ctx, d, options={"merge_block": 1000})
+    with pytest.raises(ms.MsortError):
+        ms.msort_sort(ctx, d, options={"tile": 4096})
     with pytest.raises(ms.MsortError):
         ms.msort_sort_copy(ctx, d, d, d, None)
 
