@@ -115,6 +115,32 @@ msort_status msort_sort_host(msort_ctx* ctx, const void* h_keys_in, const uint32
                              void* h_keys_out, uint32_t* h_vals_out, size_t n, msort_key_type kt,
                              const msort_options* opt, void* stream);
 
+/* ---- sorting without device allocation -------------------------------- */
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that may not allocate device memory: code that owns the device's memory
+ * through its own pool, or a latency-critical path that cannot afford the
+ * device synchronisation an allocation can cause.  It runs the same stable
+ * sort as msort_sort_copy with the default plan, but takes its scratch from
+ * a fixed 48 MiB array compiled into the library (held on every GPU that
+ * loads the library until the process exits), and calls no allocator.
+ *  - Works on the calling thread's current device.  The first call on a
+ *    device looks up the array's device address (cudaGetSymbolAddress);
+ *    make that first call before any stream capture.
+ *  - n above msort_noalloc_max_keys(kt, with_vals) is rejected with
+ *    MSORT_ERR_INVALID_ARG before any work is enqueued.
+ *  - All calls on a device share the one array: calls whose work overlaps
+ *    on the GPU (unordered streams, concurrent host threads) race and give
+ *    wrong results.  Order them on one stream.
+ *  - d_keys_out may equal d_keys_in (in place); value pointers are both
+ *    NULL (keys only) or both set.  Errors a kernel detects on the device
+ *    are not reported here (there is no context to carry them). */
+msort_status msort_sort_noalloc(const void* d_keys_in, const uint32_t* d_vals_in, void* d_keys_out,
+                                uint32_t* d_vals_out, size_t n, msort_key_type kt, void* stream);
+/* Largest n msort_sort_noalloc accepts for this key type (with or without
+ * values). */
+size_t msort_noalloc_max_keys(msort_key_type kt, int with_vals);
+
 /* ---- measurement ------------------------------------------------------ */
 
 /* Kernel kinds for msort_ctx_kernel_times. */

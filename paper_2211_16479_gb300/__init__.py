@@ -48,6 +48,8 @@ _SIGS = {
     "msort_sort_pairs": ([_P, _P, _P, _SZ, _I, _OPT, _P], _ST),
     "msort_sort_copy": ([_P, _P, _P, _P, _P, _SZ, _I, _OPT, _P], _ST),
     "msort_sort_host": ([_P, _P, _P, _P, _P, _SZ, _I, _OPT, _P], _ST),
+    "msort_sort_noalloc": ([_P, _P, _P, _P, _SZ, _I, _P], _ST),
+    "msort_noalloc_max_keys": ([_I, _I], _SZ),
     "msort_ctx_set_profiling": ([_P, _I], _ST),
     "msort_ctx_kernel_times": ([_P, _I, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)], _ST),
     "msort_ctx_launch_count": ([_P], ctypes.c_ulonglong),
@@ -202,6 +204,20 @@ def msort_sort_host(ctx, keys, vals=None, out_keys=None, out_vals=None, n=None, 
     _check(ctx, load_library().msort_sort_host(ctx, _ptr(keys), _ptr(vals), _ptr(out_keys), _ptr(out_vals),
                                                _numel(keys, n), _key_type(keys, key_type), _opts(options),
                                                _stream(stream)))
+
+
+def msort_sort_noalloc(keys_in, keys_out, vals_in=None, vals_out=None, n=None, key_type=None,
+                       stream=None) -> None:
+    """Stable sort without any device allocation (scratch is a fixed array
+    inside the library; see msort_sort_noalloc in include/msort.h).  Calls
+    that overlap on the GPU race on that array: keep them on one stream."""
+    _check(None, load_library().msort_sort_noalloc(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out),
+                                                   _numel(keys_in, n), _key_type(keys_in, key_type),
+                                                   _stream(stream, keys_in)))
+
+
+def msort_noalloc_max_keys(key_type: int, with_vals: bool) -> int:
+    return int(load_library().msort_noalloc_max_keys(int(key_type), int(bool(with_vals))))
 
 
 def msort_ctx_set_profiling(ctx, on: bool) -> None:
