@@ -27,7 +27,8 @@ static cudaError_t prepare(F* f, size_t smem) {
 template <class K, bool PAIRS>
 size_t tile_smem_bytes(int tile) {
     using Item = typename TileItem<K, PAIRS>::T;
-    return sizeof(Item) * (tile + 1) + (PAIRS ? sizeof(uint32_t) * tile : 0);
+    const int threads = (tile == 8704 || tile == 16896) ? 512 : 256;
+    return sizeof(Item) * tile_slots(tile, threads) + (PAIRS ? sizeof(uint32_t) * tile : 0);
 }
 
 // ipt = outputs per thread of the merge block (W = 256 * ipt).

@@ -155,37 +155,69 @@ __device__ __forceinline__ T sld(const unsigned char* base, int off) {
     return *reinterpret_cast<const T*>(base + off);
 }
 
-// One shared-memory merge round inside a tile: the runs of length
-// R = IPT << lg at [2gR, 2gR + R) and [2gR + R, 2gR + 2R) merge into 2R;
-// thread t produces outputs [t*IPT, t*IPT + IPT) into registers.  Ties go to
-// the left run.  Reads may touch one item past the tile (slack item).
+// Store a thread's IPT sorted items (tile positions t*IPT ..) for a merge
+// round whose runs have length IPT << lg.  Runs are kept in "bitonic"
+// layout: the right-hand run of every merge pair (odd run index) is stored
+// reversed.  With the right run reversed, a merge that walks the left run
+// forwards and the right run backwards never needs a bounds check: past the
+// end of either run it meets the other run's largest element, which is at
+// least every element still to come (R. Sedgewick's merge without
+// sentinels, "Algorithms", 2nd ed., Ch. 12).  Each merge pair is followed by
+// one unused slot, so pairs start 2R + 1 words apart (an odd stride) and the
+// threads of different pairs hit different banks.
+template <class Item, int IPT>
+__device__ __forceinline__ void store_bitonic(Item* s, int t, int lg, const Item (&r)[IPT]) {
+    const int p0 = t * IPT;
+    const bool rev = (t >> lg) & 1;
+    const int run = IPT << lg;
+    const int qb = (t >> lg) * run;
+    const int start = (rev ? qb + run - 1 - (p0 - qb) : p0) + (t >> (lg + 1));
+    const int step = rev ? -1 : 1;
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) s[start + i * step] = r[i];
+}
+
+// Shared-memory items a tile sort of T items with THREADS threads needs.
+__host__ __device__ constexpr int tile_slots(int T, int THREADS) { return T + THREADS / 2 + 2; }
+
+// One shared-memory merge round inside a tile: pair g holds the run of
+// length R = IPT << lg at [g(2R+1), g(2R+1) + R) (ascending) followed by its
+// partner (stored descending); they merge into 2R outputs, of which thread t
+// produces [t*IPT, t*IPT + IPT) into registers.  Ties go to the left run.
+// One shared load per output: both run heads stay in registers and only the
+// consumed side is reloaded.
 template <class TI, int IPT>
 __device__ __forceinline__ void smem_merge_round(const unsigned char* s, int lg, int t, typename TI::T (&r)[IPT]) {
     using Item = typename TI::T;
     constexpr int SZ = (int)sizeof(Item);
     const int R = IPT << lg;
-    const int tpp = 2 << lg;  // threads per merge pair
-    const int pb = (t & ~(tpp - 1)) * IPT;
-    const int diag = (t & (tpp - 1)) * IPT;
-    const int A0 = pb * SZ, B0 = (pb + R) * SZ;
+    const int g = t >> (lg + 1);
+    const int base = g * (2 * R + 1);
+    const int diag = (t & ((2 << lg) - 1)) * IPT;
+    const int A0 = base * SZ;
+    const int BE = (base + 2 * R - 1) * SZ;  // B[k] lives at BE - k*SZ
     int lo = diag > R ? diag - R : 0;
     int hi = diag < R ? diag : R;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (!TI::less(sld<Item>(s, B0 + (diag - 1 - mid) * SZ), sld<Item>(s, A0 + mid * SZ)))
+        if (!TI::less(sld<Item>(s, BE - (diag - 1 - mid) * SZ), sld<Item>(s, A0 + mid * SZ)))
             lo = mid + 1;
         else
             hi = mid;
     }
-    int ao = A0 + lo * SZ, bo = B0 + (diag - lo) * SZ;
-    const int ae = B0, be = B0 + R * SZ;
+    int io = A0 + lo * SZ, jo = BE - (diag - lo) * SZ;
+    Item av = sld<Item>(s, io), bv = sld<Item>(s, jo);
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
-        const Item av = sld<Item>(s, ao), bv = sld<Item>(s, bo);
-        const bool ta = ao < ae && (bo >= be || !TI::less(bv, av));
-        r[i] = ta ? av : bv;
-        ao += ta ? SZ : 0;
-        bo += ta ? 0 : SZ;
+        const bool tb = TI::less(bv, av);
+        r[i] = tb ? bv : av;
+        io += tb ? 0 : SZ;
+        jo -= tb ? SZ : 0;
+        if (i + 1 < IPT) {
+            const Item nx = sld<Item>(s, tb ? jo : io);
+            av = tb ? av : nx;
+            bv = tb ? nx : bv;
+        }
     }
 }
 
@@ -197,7 +229,10 @@ __device__ __forceinline__ bool aligned16(const K* p) {
 // ---------------------------------------------------------------------------
 // Tile sort: block b sorts kin[b*T, min((b+1)*T, n)) into kout at the same
 // place.  kin may equal kout (each block reads its whole tile first).
-// Dynamic shared memory: (T + 1) items, then T uint32 values for pairs.
+// Dynamic shared memory: tile_slots(T, THREADS) items, then T uint32 values
+// for pairs.
+// Steps: bulk TMA load (or coalesced loads), per-thread network, merge
+// rounds in bitonic layout, bulk TMA store (or coalesced stores).
 // ---------------------------------------------------------------------------
 template <class K, bool PAIRS, int THREADS, int IPT>
 __global__ void __launch_bounds__(THREADS)
@@ -208,7 +243,7 @@ k_tile_sort(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     Item* s = reinterpret_cast<Item*>(smem_raw);
-    uint32_t* sv = reinterpret_cast<uint32_t*>(smem_raw + sizeof(Item) * (T + 1));
+    uint32_t* sv = reinterpret_cast<uint32_t*>(smem_raw + sizeof(Item) * tile_slots(T, THREADS));
 
     const size_t base = (size_t)blockIdx.x * T;
     const int valid = (int)((n - base) < (size_t)T ? (n - base) : (size_t)T);
@@ -252,8 +287,7 @@ k_tile_sort(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n
     int lg = 0;
     for (int R = IPT; R < T; R *= 2, ++lg) {
         __syncthreads();
-#pragma unroll
-        for (int i = 0; i < IPT; ++i) s[t * IPT + i] = r[i];
+        store_bitonic<Item, IPT>(s, t, lg, r);
         __syncthreads();
         smem_merge_round<TI, IPT>(sb, lg, t, r);
     }
@@ -316,7 +350,11 @@ __device__ __forceinline__ PassGeom pass_geom(size_t out0, size_t n, size_t L) {
     return g;
 }
 
-// Stable co-rank by binary search over global memory.
+// Stable co-rank by binary search over global memory: the first a in
+// [max(0, d-|B|), min(d, |A|)] with B[d-1-a] < A[a].  (An 8-ary variant with
+// seven independent probes per step measured slower on GB300: the pass's
+// searches are limited by scattered-load throughput, not by the length of
+// one search's dependent chain.)
 template <class K>
 __device__ __forceinline__ size_t corank_search(const K* A, size_t alen, const K* B, size_t blen, size_t d) {
     size_t lo = d > blen ? d - blen : 0;
