@@ -106,6 +106,22 @@ msort_status msort_sort_copy(msort_ctx* ctx, const void* d_keys_in, const uint32
                              void* d_keys_out, uint32_t* d_vals_out, size_t n, msort_key_type kt,
                              const msort_options* opt, void* stream);
 
+/* Batched segmented sort, in place: each segment [d_offsets[i],
+ * d_offsets[i+1]) of d_keys (and d_vals, nullable) is sorted on its own,
+ * stably.  d_offsets holds nseg + 1 nondecreasing uint64 offsets with
+ * d_offsets[0] = 0 and d_offsets[nseg] = n (the total key count).  The
+ * offsets are checked on the device: malformed offsets leave the keys
+ * untouched and make the next msort_ctx_sync return MSORT_ERR_INVALID_ARG.
+ * Segments are bucketed by length on the device and each bucket is sorted
+ * by one persistent launch, so the call never synchronises; with
+ * opt->use_graph the whole launch sequence is captured once per
+ * (buffers, sizes) and replayed from a CUDA graph afterwards.
+ * (Segmented sorting is the paper's method applied per array; the paper
+ * itself sorts one array.) */
+msort_status msort_segmented_sort(msort_ctx* ctx, void* d_keys, uint32_t* d_vals, const uint64_t* d_offsets,
+                                  size_t nseg, size_t n, msort_key_type kt, const msort_options* opt,
+                                  void* stream);
+
 /* Host-buffer sort: copies h_keys_in (and h_vals_in, nullable) to the
  * device, sorts there, and copies the result to h_keys_out (and h_vals_out;
  * give both value pointers or neither).  Output may be the same buffer as

@@ -48,6 +48,7 @@ _SIGS = {
     "msort_sort_pairs": ([_P, _P, _P, _SZ, _I, _OPT, _P], _ST),
     "msort_sort_copy": ([_P, _P, _P, _P, _P, _SZ, _I, _OPT, _P], _ST),
     "msort_sort_host": ([_P, _P, _P, _P, _P, _SZ, _I, _OPT, _P], _ST),
+    "msort_segmented_sort": ([_P, _P, _P, _P, _SZ, _SZ, _I, _OPT, _P], _ST),
     "msort_sort_noalloc": ([_P, _P, _P, _P, _SZ, _I, _P], _ST),
     "msort_noalloc_max_keys": ([_I, _I], _SZ),
     "msort_ctx_set_profiling": ([_P, _I], _ST),
@@ -193,6 +194,16 @@ def msort_sort_copy(ctx, keys_in, keys_out, vals_in=None, vals_out=None, n=None,
     _check(ctx, load_library().msort_sort_copy(ctx, _ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out),
                                                _numel(keys_in, n), _key_type(keys_in, key_type), _opts(options),
                                                _stream(stream, keys_in)))
+
+
+def msort_segmented_sort(ctx, keys, offsets, vals=None, nseg=None, n=None, key_type=None, options=None,
+                         stream=None) -> None:
+    """Sort every segment [offsets[i], offsets[i+1]) of keys (and vals) in
+    place; offsets is a device uint64/int64 tensor of nseg + 1 entries."""
+    nseg = int(offsets.numel()) - 1 if nseg is None else int(nseg)
+    _check(ctx, load_library().msort_segmented_sort(ctx, _ptr(keys), _ptr(vals), _ptr(offsets), nseg,
+                                                    _numel(keys, n), _key_type(keys, key_type), _opts(options),
+                                                    _stream(stream, keys)))
 
 
 def msort_sort_host(ctx, keys, vals=None, out_keys=None, out_vals=None, n=None, key_type=None,

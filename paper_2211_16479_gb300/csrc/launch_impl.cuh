@@ -26,9 +26,8 @@ static cudaError_t prepare(F* f, size_t smem) {
 
 template <class K, bool PAIRS>
 size_t tile_smem_bytes(int tile) {
-    using Item = typename TileItem<K, PAIRS>::T;
     const int threads = (tile == 8704 || tile == 16896) ? 512 : 256;
-    return sizeof(Item) * tile_slots(tile, threads) + (PAIRS ? sizeof(uint32_t) * tile : 0);
+    return threads == 512 ? tile_block_smem<K, PAIRS, 512>(tile) : tile_block_smem<K, PAIRS, 256>(tile);
 }
 
 // ipt = outputs per thread of the merge block (W = 256 * ipt).

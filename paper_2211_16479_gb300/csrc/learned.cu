@@ -24,6 +24,6 @@ template cudaError_t launch_learned_partition<uint64_t>(msort_ctx*, const Plan&,
                                                         unsigned long long*, cudaStream_t);
 
 void learned_destroy(msort_ctx*) {}
-void graphs_destroy(msort_ctx*) {}
+
 
 }  // namespace msort

@@ -1,0 +1,468 @@
+// Batched segmented sort: many independent arrays sorted in one call.
+//
+// The paper sorts one array; its chunk-then-merge structure (Sections
+// "Multiprocessing Merge Sort" and "MPI Merge Sort") applies unchanged to
+// each segment [off[i], off[i+1]) of a batch.  GPU plan, all enqueued on the
+// caller's stream with fixed launch shapes (so the sequence can be captured
+// in a CUDA graph and replayed):
+//   1. k_seg_classify: one thread per segment puts the segment's index on the
+//      work list of its length bucket (atomic append; order within a bucket
+//      does not affect the result because segments are independent).
+//   2. One persistent launch per small bucket: blocks of the bucket's shape
+//      (32 x 17 up to 1024 x 33 keys) take segments from the list with an
+//      atomic counter and sort each one entirely in shared memory with the
+//      tile-sort body (network + merge-path rounds).
+//   3. One persistent launch for the segments longer than the largest
+//      on-chip tile: a block sorts the segment's tiles, then runs the
+//      segment's merge passes itself (co-ranks of all its output blocks by
+//      binary search in parallel, then the bulk-TMA merge body per block),
+//      ping-ponging between the keys and the context scratch.
+#include <cuda_runtime.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+
+#include "ctx.h"
+#include "launch.h"
+#include "sort_kernels.cuh"
+
+namespace msort {
+
+constexpr int kSegMaxBuckets = 6;   // small buckets
+constexpr int kSegLarge = kSegMaxBuckets;  // index of the large-segment list
+constexpr int kSegLists = kSegMaxBuckets + 1;
+constexpr unsigned int kStatusBadInput = 2u;
+constexpr int kSegBadFlag = 63;  // counters[63]: this call's bad-input flag
+
+struct SegBuckets {
+    int n;                       // number of small buckets in use
+    int lim[kSegMaxBuckets];     // bucket b takes lengths in (lim[b-1], lim[b]]
+};
+
+// Device-side classification of segments into bucket work lists.
+__global__ void k_seg_classify(const unsigned long long* __restrict__ off, size_t nseg, size_t n, SegBuckets bk,
+                               unsigned int* __restrict__ lists, unsigned int* __restrict__ counts,
+                               unsigned int* status) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nseg) return;
+    const unsigned long long b = off[i], e = off[i + 1];
+    if (e < b || e > n || (i == 0 && b != 0) || (i == nseg - 1 && e != n)) {
+        atomicOr(status, kStatusBadInput);
+        atomicOr(&counts[kSegBadFlag], 1u);
+        return;
+    }
+    const unsigned long long len = e - b;
+    if (len <= 1) return;
+    int q = kSegLarge;
+    for (int k = 0; k < bk.n; ++k)
+        if (len <= (unsigned long long)bk.lim[k]) {
+            q = k;
+            break;
+        }
+    const unsigned int pos = atomicAdd(&counts[q], 1u);
+    lists[(size_t)q * nseg + pos] = (unsigned int)i;
+}
+
+// Next work item of list q for this block (all threads get the same value).
+__device__ __forceinline__ unsigned int seg_next(unsigned int* counters, int q, unsigned int* slot) {
+    __syncthreads();
+    if (threadIdx.x == 0) *slot = atomicAdd(&counters[kSegLists + q], 1u);
+    __syncthreads();
+    return *slot;
+}
+
+// Small bucket: every segment fits one block of THREADS x IPT keys.
+template <class K, bool PAIRS, int THREADS, int IPT>
+__global__ void __launch_bounds__(THREADS)
+k_seg_small(K* keys, uint32_t* vals, const unsigned long long* __restrict__ off, size_t nseg,
+            const unsigned int* __restrict__ lists, unsigned int* counters, int q, unsigned int* status) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ unsigned int slot;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    if (counters[kSegBadFlag]) return;  // malformed offsets: sort nothing
+    uint32_t phase = 0;
+    const unsigned int count = counters[q];
+    for (unsigned int w = seg_next(counters, q, &slot); w < count; w = seg_next(counters, q, &slot)) {
+        const unsigned int s = lists[(size_t)q * nseg + w];
+        const size_t b = off[s];
+        const int len = (int)(off[s + 1] - b);
+        if (!tile_sort_block<K, PAIRS, THREADS, IPT>(keys + b, PAIRS ? vals + b : nullptr, keys + b,
+                                                     PAIRS ? vals + b : nullptr, len, smem_raw, &bar, phase,
+                                                     status))
+            return;
+    }
+}
+
+// Make this block's global writes (bulk TMA stores and plain stores) visible
+// to its own later reads of either kind (plain loads and bulk TMA loads).
+__device__ __forceinline__ void block_pass_barrier() {
+    if (threadIdx.x == 0) tma_store_wait_all();
+    fence_proxy_async_global();
+    __threadfence_block();
+    __syncthreads();
+}
+
+// Large segments: tiles of THREADS x IPT keys, then merge passes with merge
+// blocks of the same size, all by one block per segment.
+template <class K, bool PAIRS, int THREADS, int IPT>
+__global__ void __launch_bounds__(THREADS)
+k_seg_large(K* keys, uint32_t* vals, K* tkeys, uint32_t* tvals, const unsigned long long* __restrict__ off,
+            size_t nseg, const unsigned int* __restrict__ lists, unsigned int* counters, unsigned int* status) {
+    constexpr int T = THREADS * IPT;
+    constexpr int W = T;
+    constexpr int kSplitChunk = THREADS;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ unsigned int slot;
+    __shared__ unsigned long long splits[kSplitChunk + 1];
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    if (counters[kSegBadFlag]) return;  // malformed offsets: sort nothing
+    uint32_t phase = 0;
+    const int t = threadIdx.x;
+    const unsigned int count = counters[kSegLarge];
+    for (unsigned int w = seg_next(counters, kSegLarge, &slot); w < count;
+         w = seg_next(counters, kSegLarge, &slot)) {
+        const unsigned int s = lists[(size_t)kSegLarge * nseg + w];
+        const size_t base = off[s];
+        const size_t len = off[s + 1] - base;
+        int passes = 0;
+        for (size_t L = T; L < len; L *= 2) ++passes;
+        K* bk[2] = {keys + base, tkeys + base};
+        uint32_t* bv[2] = {PAIRS ? vals + base : nullptr, PAIRS ? tvals + base : nullptr};
+        int cur = passes & 1;
+        for (size_t j = 0; j < len; j += T) {
+            const int valid = (int)(len - j < (size_t)T ? len - j : (size_t)T);
+            if (!tile_sort_block<K, PAIRS, THREADS, IPT>(keys + base + j, PAIRS ? vals + base + j : nullptr,
+                                                         bk[cur] + j, PAIRS ? bv[cur] + j : nullptr, valid,
+                                                         smem_raw, &bar, phase, status))
+                return;
+        }
+        block_pass_barrier();
+        for (int p = 0; p < passes; ++p) {
+            const size_t L = (size_t)T << p;
+            const K* src = bk[cur];
+            K* dst = bk[cur ^ 1];
+            const size_t nblocks = (len + W - 1) / W;
+            for (size_t c0 = 0; c0 < nblocks; c0 += kSplitChunk) {
+                const size_t cn = nblocks - c0 < (size_t)kSplitChunk ? nblocks - c0 : (size_t)kSplitChunk;
+                __syncthreads();
+                // the co-rank of every block start in this chunk, in parallel
+                if ((size_t)t < cn) {
+                    const size_t out0 = (c0 + t) * W;
+                    const PassGeom g = pass_geom(out0, len, L);
+                    splits[t] = corank_search(src + g.pb, g.alen, src + g.pb + g.alen, g.blen, out0 - g.pb);
+                }
+                if (t == 0) {
+                    // split at the start of the block after the chunk (or unused)
+                    const size_t out0 = (c0 + cn) * W;
+                    if (c0 + cn < nblocks) {
+                        const PassGeom g = pass_geom(out0, len, L);
+                        splits[cn] = corank_search(src + g.pb, g.alen, src + g.pb + g.alen, g.blen, out0 - g.pb);
+                    }
+                }
+                __syncthreads();
+                for (size_t ci = 0; ci < cn; ++ci) {
+                    const size_t out0 = (c0 + ci) * W;
+                    const PassGeom g = pass_geom(out0, len, L);
+                    const size_t d0 = out0 - g.pb;
+                    const size_t dend = g.alen + g.blen;
+                    const size_t d1 = (d0 + W < dend) ? d0 + W : dend;
+                    const size_t a0 = splits[ci];
+                    const size_t a1 = (d1 == dend) ? g.alen : (size_t)splits[ci + 1];
+                    const int nA = (int)(a1 - a0);
+                    const int nB = (int)(d1 - d0) - nA;
+                    const size_t oA = g.pb + a0, oB = g.pb + g.alen + (d0 - a0);
+                    if (!merge_block<K, PAIRS, THREADS, IPT>(
+                            src + oA, nA, src + oB, nB, PAIRS ? bv[cur] + oA : nullptr,
+                            PAIRS ? bv[cur] + oB : nullptr, dst + out0, PAIRS ? bv[cur ^ 1] + out0 : nullptr,
+                            smem_raw, &bar, phase, status))
+                        return;
+                }
+            }
+            block_pass_barrier();
+            cur ^= 1;
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Host side
+// ----------------------------------------------------------------------------
+namespace {
+
+template <class F>
+int persistent_blocks(F* f, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, int, size_t, int>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(reinterpret_cast<const void*>(f), threads, smem, dev);
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, f, threads, smem);
+    const int blocks = sms * (per > 0 ? per : 1);
+    cache[key] = blocks;
+    return blocks;
+}
+
+template <class F>
+cudaError_t allow_smem(F* f, size_t smem) {
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(f));
+    if (e != cudaSuccess) return e;
+    if ((int)smem <= fa.maxDynamicSharedSizeBytes) return cudaSuccess;
+    return cudaFuncSetAttribute(reinterpret_cast<const void*>(f), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+}
+
+template <class K, bool PAIRS, int TH, int IPT>
+cudaError_t launch_small(K* keys, uint32_t* vals, const unsigned long long* off, size_t nseg,
+                         const unsigned int* lists, unsigned int* counters, int q, unsigned int* status,
+                         cudaStream_t st) {
+    auto f = k_seg_small<K, PAIRS, TH, IPT>;
+    const size_t sm = tile_block_smem<K, PAIRS, TH>(TH * IPT);
+    cudaError_t e = allow_smem(f, sm);
+    if (e != cudaSuccess) return e;
+    const int blocks = persistent_blocks(f, TH, sm);
+    f<<<blocks, TH, sm, st>>>(keys, vals, off, nseg, lists, counters, q, status);
+    return cudaGetLastError();
+}
+
+template <class K, bool PAIRS, int TH, int IPT>
+cudaError_t launch_large(K* keys, uint32_t* vals, K* tk, uint32_t* tv, const unsigned long long* off, size_t nseg,
+                         const unsigned int* lists, unsigned int* counters, unsigned int* status,
+                         cudaStream_t st) {
+    auto f = k_seg_large<K, PAIRS, TH, IPT>;
+    const size_t a = tile_block_smem<K, PAIRS, TH>(TH * IPT), b = merge_block_smem<K, PAIRS, TH, IPT>();
+    const size_t sm = a > b ? a : b;
+    cudaError_t e = allow_smem(f, sm);
+    if (e != cudaSuccess) return e;
+    const int blocks = persistent_blocks(f, TH, sm);
+    f<<<blocks, TH, sm, st>>>(keys, vals, tk, tv, off, nseg, lists, counters, status);
+    return cudaGetLastError();
+}
+
+// Bucket plans per key/value type: small buckets (threads x keys per thread)
+// and the tile of the large-segment kernel.
+template <class K, bool PAIRS>
+struct SegPlan;
+
+#define MSORT_SMALL_LAUNCHES(K, PAIRS)                                                                          \
+    if ((e = launch_small<K, PAIRS, 32, 17>(keys, vals, off, nseg, lists, counters, 0, status, st))) return e;  \
+    if ((e = launch_small<K, PAIRS, 128, 17>(keys, vals, off, nseg, lists, counters, 1, status, st))) return e; \
+    if ((e = launch_small<K, PAIRS, 256, 33>(keys, vals, off, nseg, lists, counters, 2, status, st))) return e;
+
+template <>
+struct SegPlan<uint32_t, false> {
+    static SegBuckets buckets() { return SegBuckets{5, {544, 2176, 8448, 16896, 33792, 0}}; }
+    static cudaError_t run(uint32_t* keys, uint32_t* vals, uint32_t* tk, uint32_t* tv, const unsigned long long* off,
+                           size_t nseg, const unsigned int* lists, unsigned int* counters, unsigned int* status,
+                           cudaStream_t st) {
+        cudaError_t e;
+        MSORT_SMALL_LAUNCHES(uint32_t, false)
+        if ((e = launch_small<uint32_t, false, 512, 33>(keys, vals, off, nseg, lists, counters, 3, status, st)))
+            return e;
+        if ((e = launch_small<uint32_t, false, 1024, 33>(keys, vals, off, nseg, lists, counters, 4, status, st)))
+            return e;
+        return launch_large<uint32_t, false, 512, 33>(keys, vals, tk, tv, off, nseg, lists, counters, status, st);
+    }
+};
+
+template <>
+struct SegPlan<uint32_t, true> {
+    static SegBuckets buckets() { return SegBuckets{4, {544, 2176, 8448, 16896, 0, 0}}; }
+    static cudaError_t run(uint32_t* keys, uint32_t* vals, uint32_t* tk, uint32_t* tv, const unsigned long long* off,
+                           size_t nseg, const unsigned int* lists, unsigned int* counters, unsigned int* status,
+                           cudaStream_t st) {
+        cudaError_t e;
+        MSORT_SMALL_LAUNCHES(uint32_t, true)
+        if ((e = launch_small<uint32_t, true, 512, 33>(keys, vals, off, nseg, lists, counters, 3, status, st)))
+            return e;
+        return launch_large<uint32_t, true, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, status, st);
+    }
+};
+
+template <>
+struct SegPlan<uint64_t, false> {
+    static SegBuckets buckets() { return SegBuckets{4, {544, 2176, 8448, 16896, 0, 0}}; }
+    static cudaError_t run(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv, const unsigned long long* off,
+                           size_t nseg, const unsigned int* lists, unsigned int* counters, unsigned int* status,
+                           cudaStream_t st) {
+        cudaError_t e;
+        MSORT_SMALL_LAUNCHES(uint64_t, false)
+        if ((e = launch_small<uint64_t, false, 512, 33>(keys, vals, off, nseg, lists, counters, 3, status, st)))
+            return e;
+        return launch_large<uint64_t, false, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, status, st);
+    }
+};
+
+template <>
+struct SegPlan<uint64_t, true> {
+    static SegBuckets buckets() { return SegBuckets{3, {544, 2176, 8448, 0, 0, 0}}; }
+    static cudaError_t run(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv, const unsigned long long* off,
+                           size_t nseg, const unsigned int* lists, unsigned int* counters, unsigned int* status,
+                           cudaStream_t st) {
+        cudaError_t e;
+        MSORT_SMALL_LAUNCHES(uint64_t, true)
+        return launch_large<uint64_t, true, 256, 17>(keys, vals, tk, tv, off, nseg, lists, counters, status, st);
+    }
+};
+
+struct SegLayout {
+    size_t keys, vals, lists, counters, end;
+};
+
+template <class K, bool PAIRS>
+SegLayout seg_layout(size_t n, size_t nseg) {
+    SegLayout l{};
+    l.keys = 0;
+    l.vals = align_up(n * sizeof(K), 256);
+    l.lists = l.vals + (PAIRS ? align_up(n * 4, 256) : 0);
+    l.counters = l.lists + align_up((size_t)kSegLists * nseg * 4, 256);
+    l.end = l.counters + 256;
+    return l;
+}
+
+template <class K, bool PAIRS>
+msort_status seg_enqueue(msort_ctx* ctx, K* keys, uint32_t* vals, const unsigned long long* off, size_t nseg,
+                         size_t n, cudaStream_t st) {
+    const SegLayout l = seg_layout<K, PAIRS>(n, nseg);
+    unsigned char* sp = static_cast<unsigned char*>(ctx->scratch);
+    K* tk = reinterpret_cast<K*>(sp + l.keys);
+    uint32_t* tv = PAIRS ? reinterpret_cast<uint32_t*>(sp + l.vals) : nullptr;
+    unsigned int* lists = reinterpret_cast<unsigned int*>(sp + l.lists);
+    unsigned int* counters = reinterpret_cast<unsigned int*>(sp + l.counters);
+    cudaError_t e = cudaMemsetAsync(counters, 0, 256, st);
+    if (e != cudaSuccess) return cuda_fail(e, "clearing segment counters");
+    prof_begin(ctx, KK_SEGMENTED, st);
+    k_seg_classify<<<(unsigned)((nseg + 255) / 256), 256, 0, st>>>(off, nseg, n, SegPlan<K, PAIRS>::buckets(), lists,
+                                                                   counters, ctx->d_status);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = SegPlan<K, PAIRS>::run(keys, vals, tk, tv, off, nseg, lists, counters, ctx->d_status, st);
+    prof_end(ctx, KK_SEGMENTED, st);
+    ctx->launches += 1 + SegPlan<K, PAIRS>::buckets().n + 1;
+    if (e != cudaSuccess) return cuda_fail(e, "segmented sort launch");
+    return MSORT_OK;
+}
+
+struct SegGraphKey {
+    const void* keys;
+    const void* vals;
+    const void* off;
+    size_t nseg, n;
+    int kt;
+    const void* scratch;
+    cudaStream_t st;
+    bool operator<(const SegGraphKey& o) const {
+        return std::tie(keys, vals, off, nseg, n, kt, scratch, st) <
+               std::tie(o.keys, o.vals, o.off, o.nseg, o.n, o.kt, o.scratch, o.st);
+    }
+};
+
+struct GraphCache {
+    std::map<SegGraphKey, cudaGraphExec_t> seg;
+};
+
+}  // namespace
+
+GraphCache* graph_cache(msort_ctx* ctx) {
+    if (!ctx->graphs) ctx->graphs = new GraphCache();
+    return static_cast<GraphCache*>(ctx->graphs);
+}
+
+void graphs_destroy(msort_ctx* ctx) {
+    if (!ctx->graphs) return;
+    GraphCache* gc = static_cast<GraphCache*>(ctx->graphs);
+    for (auto& kv : gc->seg) cudaGraphExecDestroy(kv.second);
+    delete gc;
+    ctx->graphs = nullptr;
+}
+
+template <class K, bool PAIRS>
+msort_status seg_sort(msort_ctx* ctx, K* keys, uint32_t* vals, const unsigned long long* off, size_t nseg, size_t n,
+                      const msort_options* opt, cudaStream_t st) {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    msort_status s = ensure_scratch(ctx, seg_layout<K, PAIRS>(n, nseg).end, st);
+    if (s != MSORT_OK) return s;
+    const bool use_graph = opt && opt->use_graph;
+    if (!use_graph || ctx->profiling) {
+        s = seg_enqueue<K, PAIRS>(ctx, keys, vals, off, nseg, n, st);
+    } else {
+        GraphCache* gc = graph_cache(ctx);
+        const SegGraphKey key{keys, vals, off, nseg, n, (int)sizeof(K) * 2 + PAIRS, ctx->scratch, st};
+        auto it = gc->seg.find(key);
+        if (it == gc->seg.end()) {
+            cudaStream_t cap;
+            e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                const unsigned long long before = ctx->launches;
+                s = seg_enqueue<K, PAIRS>(ctx, keys, vals, off, nseg, n, cap);
+                ctx->launches = before;
+                cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+                if (s == MSORT_OK && e2 != cudaSuccess) s = cuda_fail(e2, "cudaStreamEndCapture");
+            } else {
+                s = cuda_fail(e, "cudaStreamBeginCapture");
+            }
+            cudaStreamDestroy(cap);
+            if (s != MSORT_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return s;
+            }
+            cudaGraphExec_t exec = nullptr;
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+            it = gc->seg.emplace(key, exec).first;
+        }
+        e = cudaGraphLaunch(it->second, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+        ctx->launches += 1 + SegPlan<K, PAIRS>::buckets().n + 1;
+    }
+    cudaEventRecord(ctx->scratch_done, st);
+    ctx->last_stream = st;
+    ctx->scratch_pending = true;
+    return s;
+}
+
+}  // namespace msort
+
+using namespace msort;
+
+extern "C" msort_status msort_segmented_sort(msort_ctx* ctx, void* d_keys, uint32_t* d_vals,
+                                             const uint64_t* d_offsets, size_t nseg, size_t n, msort_key_type kt,
+                                             const msort_options* opt, void* stream) {
+    if (!ctx) return fail(MSORT_ERR_INVALID_ARG, "ctx is NULL");
+    if (kt != MSORT_U32 && kt != MSORT_U64) return fail(MSORT_ERR_INVALID_ARG, "unknown key type");
+    if (nseg == 0) return MSORT_OK;
+    if (!d_offsets) return fail(MSORT_ERR_INVALID_ARG, "d_offsets is NULL");
+    if (n && !d_keys) return fail(MSORT_ERR_INVALID_ARG, "d_keys is NULL");
+    if (nseg > 0xFFFFFFFFull) return fail(MSORT_ERR_UNSUPPORTED, "more than 2^32 - 1 segments");
+    const size_t ks = kt == MSORT_U32 ? 4 : 8;
+    if (reinterpret_cast<uintptr_t>(d_keys) % ks || reinterpret_cast<uintptr_t>(d_vals) % 4 ||
+        reinterpret_cast<uintptr_t>(d_offsets) % 8)
+        return fail(MSORT_ERR_INVALID_ARG, "buffers must be aligned to their element size");
+    cudaStream_t st = (cudaStream_t)stream;
+    const unsigned long long* off = reinterpret_cast<const unsigned long long*>(d_offsets);
+    if (kt == MSORT_U32)
+        return d_vals ? seg_sort<uint32_t, true>(ctx, static_cast<uint32_t*>(d_keys), d_vals, off, nseg, n, opt, st)
+                      : seg_sort<uint32_t, false>(ctx, static_cast<uint32_t*>(d_keys), nullptr, off, nseg, n, opt, st);
+    return d_vals ? seg_sort<uint64_t, true>(ctx, static_cast<uint64_t*>(d_keys), d_vals, off, nseg, n, opt, st)
+                  : seg_sort<uint64_t, false>(ctx, static_cast<uint64_t*>(d_keys), nullptr, off, nseg, n, opt, st);
+}

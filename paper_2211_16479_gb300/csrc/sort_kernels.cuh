@@ -227,44 +227,40 @@ __device__ __forceinline__ bool aligned16(const K* p) {
 }
 
 // ---------------------------------------------------------------------------
-// Tile sort: block b sorts kin[b*T, min((b+1)*T, n)) into kout at the same
-// place.  kin may equal kout (each block reads its whole tile first).
-// Dynamic shared memory: tile_slots(T, THREADS) items, then T uint32 values
-// for pairs.
-// Steps: bulk TMA load (or coalesced loads), per-thread network, merge
-// rounds in bitonic layout, bulk TMA store (or coalesced stores).
+// Tile sort of one block: sorts src[0, valid) (valid <= T = THREADS * IPT)
+// into dst[0, valid); src may equal dst.  `bar` is an initialised mbarrier
+// of this block and `phase` its next parity (flipped on every bulk load).
+// Returns false if a bounded wait gave up (status records it).
+// Shared memory: tile_slots(T, THREADS) items, then T uint32 values for
+// pairs.  Steps: bulk TMA load (or coalesced loads), per-thread network,
+// merge rounds in bitonic layout, bulk TMA store (or coalesced stores).
 // ---------------------------------------------------------------------------
 template <class K, bool PAIRS, int THREADS, int IPT>
-__global__ void __launch_bounds__(THREADS)
-k_tile_sort(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n, unsigned int* status) {
+__device__ __forceinline__ bool tile_sort_block(const K* src, const uint32_t* vin, K* dst, uint32_t* vout, int valid,
+                                                unsigned char* smem_raw, uint64_t* bar, uint32_t& phase,
+                                                unsigned int* status) {
     using TI = TileItem<K, PAIRS>;
     using Item = typename TI::T;
     constexpr int T = THREADS * IPT;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar;
     Item* s = reinterpret_cast<Item*>(smem_raw);
     uint32_t* sv = reinterpret_cast<uint32_t*>(smem_raw + sizeof(Item) * tile_slots(T, THREADS));
-
-    const size_t base = (size_t)blockIdx.x * T;
-    const int valid = (int)((n - base) < (size_t)T ? (n - base) : (size_t)T);
     const int t = threadIdx.x;
-    const K* src = kin + base;
-    K* dst = kout + base;
+    __syncthreads();  // the previous user of this shared memory is done
 
     // Full, aligned keys-only tiles arrive by one bulk copy.
     const bool bulk = !PAIRS && valid == T && aligned16(src);
     if (bulk) {
         if (t == 0) {
-            mbar_init(&bar, 1);
-            fence_mbar_init();
-            mbar_arrive_expect_tx(&bar, (uint32_t)(T * sizeof(K)));
-            tma_load_1d(s, src, (uint32_t)(T * sizeof(K)), &bar);
+            mbar_arrive_expect_tx(bar, (uint32_t)(T * sizeof(K)));
+            tma_load_1d(s, src, (uint32_t)(T * sizeof(K)), bar);
         }
         __syncthreads();
-        if (!mbar_wait_bounded(&bar, 0, kWaitLimitCycles)) {
+        const bool ok = mbar_wait_bounded(bar, phase, kWaitLimitCycles);
+        phase ^= 1u;
+        if (!ok) {
             if (t == 0) atomicOr(status, kStatusTimeout);
-            mbar_wait_bounded(&bar, 0, kWaitLimitCycles);
-            return;
+            mbar_wait_bounded(bar, phase ^ 1u, kWaitLimitCycles);
+            return false;
         }
     } else {
 #pragma unroll
@@ -273,7 +269,7 @@ k_tile_sort(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n
             s[p] = TI::make(p < valid ? src[p] : key_max<K>(), (uint32_t)p);
         }
         if (PAIRS) {
-            for (int p = t; p < valid; p += THREADS) sv[p] = vin[base + p];
+            for (int p = t; p < valid; p += THREADS) sv[p] = vin[p];
         }
         __syncthreads();
     }
@@ -317,17 +313,41 @@ k_tile_sort(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n
 #pragma unroll
         for (int i = 0; i < IPT; ++i) s[t * IPT + i] = r[i];
         __syncthreads();
-        uint32_t* vd = vout + base;
 #pragma unroll
         for (int i = 0; i < IPT; ++i) {
             const int p = i * THREADS + t;
             if (p < valid) {
                 const Item it = s[p];
                 dst[p] = TI::key(it);
-                vd[p] = sv[TI::pos(it)];
+                vout[p] = sv[TI::pos(it)];
             }
         }
     }
+    return true;
+}
+
+template <class K, bool PAIRS, int THREADS>
+__host__ __device__ constexpr size_t tile_block_smem(int T) {
+    return sizeof(typename TileItem<K, PAIRS>::T) * (size_t)tile_slots(T, THREADS) + (PAIRS ? 4u * T : 0u);
+}
+
+// Tile sort kernel: block b sorts kin[b*T, min((b+1)*T, n)) in place into
+// kout.  kin may equal kout (each block reads its whole tile first).
+template <class K, bool PAIRS, int THREADS, int IPT>
+__global__ void __launch_bounds__(THREADS)
+k_tile_sort(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n, unsigned int* status) {
+    constexpr int T = THREADS * IPT;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    const size_t base = (size_t)blockIdx.x * T;
+    const int valid = (int)((n - base) < (size_t)T ? (n - base) : (size_t)T);
+    uint32_t phase = 0;
+    tile_sort_block<K, PAIRS, THREADS, IPT>(kin + base, PAIRS ? vin + base : nullptr, kout + base,
+                                            PAIRS ? vout + base : nullptr, valid, smem_raw, &bar, phase, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -428,47 +448,30 @@ __host__ __device__ constexpr int merge_slots(int W, int IPT, int esize) {
 }
 
 // ---------------------------------------------------------------------------
-// Merge pass: block c writes dst[c*W, min((c+1)*W, pair end)).
-// Dynamic shared memory: merge_slots(W, IPT, sizeof(K)) keys, then for pairs
-// merge_slots(W, IPT, 4) values.
+// Merge of one output block: D[0, nA + nB) = stable merge of gA[0, nA) and
+// gB[0, nB) (nA + nB <= W = THREADS * IPT), values alongside for pairs.
+// `bar` is an initialised mbarrier of this block, `phase` its next parity.
+// Shared memory: merge_slots(W, IPT, sizeof(K)) keys, then for pairs
+// merge_slots(W, IPT, 4) values.  Returns false if a bounded wait gave up.
 // ---------------------------------------------------------------------------
 template <class K, bool PAIRS, int THREADS, int IPT>
-__global__ void __launch_bounds__(THREADS)
-k_merge_pass(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __restrict__ vsrc,
-             uint32_t* __restrict__ vdst, size_t n, size_t L, const unsigned long long* __restrict__ splits,
-             unsigned int* status) {
+__device__ __forceinline__ bool merge_block(const K* gA, int nA, const K* gB, int nB, const uint32_t* gvA,
+                                            const uint32_t* gvB, K* D, uint32_t* VD, unsigned char* smem_raw,
+                                            uint64_t* bar, uint32_t& phase, unsigned int* status) {
     constexpr int W = THREADS * IPT;
     constexpr int KS = (int)sizeof(K);
     constexpr int KSLOTS = merge_slots(W, IPT, KS);
     constexpr int VSLOTS = merge_slots(W, IPT, 4);
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar;
     K* sk = reinterpret_cast<K*>(smem_raw);
     uint32_t* sv = reinterpret_cast<uint32_t*>(smem_raw + KS * KSLOTS);
-
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const size_t c = blockIdx.x;
-    const size_t out0 = c * W;
-    const PassGeom g = pass_geom(out0, n, L);
-    const size_t d0 = out0 - g.pb;
-    const size_t dend = g.alen + g.blen;
-    const size_t d1 = (d0 + W < dend) ? d0 + W : dend;
-    const size_t a0 = splits[c];
-    const size_t a1 = (d1 == dend) ? g.alen : (size_t)splits[c + 1];
-    const int nA = (int)(a1 - a0);
-    const int total = (int)(d1 - d0);
-    const int nB = total - nA;
-    const K* gA = src + g.pb + a0;
-    const K* gB = src + g.pb + g.alen + (d0 - a0);
+    const int total = nA + nB;
+    __syncthreads();  // the previous user of this shared memory is done
 
     const Window wA = place_window(gA, nA, 0, IPT);
     const Window wB = place_window(gB, nB, wA.end, IPT);
     Window vA{}, vB{};
-    const uint32_t* gvA = nullptr;
-    const uint32_t* gvB = nullptr;
     if (PAIRS) {
-        gvA = vsrc + g.pb + a0;
-        gvB = vsrc + g.pb + g.alen + (d0 - a0);
         vA = place_window(gvA, nA, 0, 0);
         vB = place_window(gvB, nB, vA.end, 0);
     }
@@ -476,14 +479,12 @@ k_merge_pass(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __r
     if (t == 0) {
         uint32_t bytes = (uint32_t)((wA.nbulk + wB.nbulk) * KS);
         if (PAIRS) bytes += (uint32_t)((vA.nbulk + vB.nbulk) * 4);
-        mbar_init(&bar, 1);
-        fence_mbar_init();
-        mbar_arrive_expect_tx(&bar, bytes);
-        if (wA.nbulk) tma_load_1d(sk + wA.off + wA.head, gA + wA.head, (uint32_t)(wA.nbulk * KS), &bar);
-        if (wB.nbulk) tma_load_1d(sk + wB.off + wB.head, gB + wB.head, (uint32_t)(wB.nbulk * KS), &bar);
+        mbar_arrive_expect_tx(bar, bytes);
+        if (wA.nbulk) tma_load_1d(sk + wA.off + wA.head, gA + wA.head, (uint32_t)(wA.nbulk * KS), bar);
+        if (wB.nbulk) tma_load_1d(sk + wB.off + wB.head, gB + wB.head, (uint32_t)(wB.nbulk * KS), bar);
         if (PAIRS) {
-            if (vA.nbulk) tma_load_1d(sv + vA.off + vA.head, gvA + vA.head, (uint32_t)(vA.nbulk * 4), &bar);
-            if (vB.nbulk) tma_load_1d(sv + vB.off + vB.head, gvB + vB.head, (uint32_t)(vB.nbulk * 4), &bar);
+            if (vA.nbulk) tma_load_1d(sv + vA.off + vA.head, gvA + vA.head, (uint32_t)(vA.nbulk * 4), bar);
+            if (vB.nbulk) tma_load_1d(sv + vB.off + vB.head, gvB + vB.head, (uint32_t)(vB.nbulk * 4), bar);
         }
     }
     window_scalars(gA, nA, wA, sk, warp, lane, 1, IPT, key_max<K>());
@@ -493,10 +494,12 @@ k_merge_pass(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __r
         window_scalars(gvB, nB, vB, sv, warp, lane, 6, 0, 0u);
     }
     __syncthreads();
-    if (!mbar_wait_bounded(&bar, 0, kWaitLimitCycles)) {
+    const bool ok_wait = mbar_wait_bounded(bar, phase, kWaitLimitCycles);
+    phase ^= 1u;
+    if (!ok_wait) {
         if (t == 0) atomicOr(status, kStatusTimeout);
-        mbar_wait_bounded(&bar, 0, kWaitLimitCycles);
-        return;
+        mbar_wait_bounded(bar, phase ^ 1u, kWaitLimitCycles);
+        return false;
     }
 
     // Co-rank of this thread's first output inside the staged windows.
@@ -556,8 +559,6 @@ k_merge_pass(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __r
             if (PAIRS) sv[t * IPT + i] = ov[i];
         }
     }
-    K* D = dst + out0;
-    uint32_t* VD = PAIRS ? vdst + out0 : nullptr;
     const bool dst_ok = aligned16(D) && (!PAIRS || aligned16(VD));
     const int nbk = dst_ok ? (total * KS / 16) * 16 / KS : 0;      // keys by bulk store
     const int nbv = dst_ok && PAIRS ? (total * 4 / 16) * 16 / 4 : 0;  // values by bulk store
@@ -572,6 +573,43 @@ k_merge_pass(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __r
     if (PAIRS)
         for (int i = nbv + t; i < total; i += THREADS) VD[i] = sv[i];
     if (t == 0) tma_store_wait_read();
+    return true;
+}
+
+template <class K, bool PAIRS, int THREADS, int IPT>
+__host__ __device__ constexpr size_t merge_block_smem() {
+    return sizeof(K) * (size_t)merge_slots(THREADS * IPT, IPT, sizeof(K)) +
+           (PAIRS ? 4u * merge_slots(THREADS * IPT, IPT, 4) : 0u);
+}
+
+// Merge pass kernel: block c writes dst[c*W, min((c+1)*W, pair end)).
+template <class K, bool PAIRS, int THREADS, int IPT>
+__global__ void __launch_bounds__(THREADS)
+k_merge_pass(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __restrict__ vsrc,
+             uint32_t* __restrict__ vdst, size_t n, size_t L, const unsigned long long* __restrict__ splits,
+             unsigned int* status) {
+    constexpr int W = THREADS * IPT;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    const size_t c = blockIdx.x;
+    const size_t out0 = c * W;
+    const PassGeom g = pass_geom(out0, n, L);
+    const size_t d0 = out0 - g.pb;
+    const size_t dend = g.alen + g.blen;
+    const size_t d1 = (d0 + W < dend) ? d0 + W : dend;
+    const size_t a0 = splits[c];
+    const size_t a1 = (d1 == dend) ? g.alen : (size_t)splits[c + 1];
+    const int nA = (int)(a1 - a0);
+    const int nB = (int)(d1 - d0) - nA;
+    const size_t oA = g.pb + a0, oB = g.pb + g.alen + (d0 - a0);
+    uint32_t phase = 0;
+    merge_block<K, PAIRS, THREADS, IPT>(src + oA, nA, src + oB, nB, PAIRS ? vsrc + oA : nullptr,
+                                        PAIRS ? vsrc + oB : nullptr, dst + out0, PAIRS ? vdst + out0 : nullptr,
+                                        smem_raw, &bar, phase, status);
 }
 
 }  // namespace msort

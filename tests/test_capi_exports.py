@@ -28,7 +28,7 @@ def lib_path():
 
 def test_header_declares_the_boundary():
     names = _declared()
-    for required in ("msort_sort", "msort_sort_pairs", "msort_ctx_create",
+    for required in ("msort_sort", "msort_sort_pairs", "msort_segmented_sort", "msort_ctx_create",
                      "msort_ctx_destroy", "msort_last_error"):
         assert required in names
 

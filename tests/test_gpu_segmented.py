@@ -1,0 +1,106 @@
+"""GPU parity of the batched segmented sort against the CPU oracle.
+
+Every segment must equal the oracle's stable sort of that segment alone
+(bit-exact; values are original indices, so stability is checked exactly).
+Lengths straddle every bucket boundary of the device plan, including empty
+and one-element segments and segments longer than the largest on-chip tile.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_util import need_gpu, to_dev, to_host, torch
+
+ms = pytest.importorskip("paper_2211_16479_gb300")
+
+pytestmark = pytest.mark.gpu
+
+BOUNDARY_LENS = [0, 1, 2, 3, 17, 33, 543, 544, 545, 2175, 2176, 2177, 4352, 8447, 8448, 8449, 16895, 16896, 16897,
+                 33791, 33792, 33793, 65536, 100003]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    need_gpu()
+    c = ms.Context(0)
+    yield c.handle
+    c.close()
+
+
+def _keys(kt, n, seed, alphabet):
+    if kt == "u32":
+        return synth.uniform_u32(n, seed) % np.uint32(alphabet)
+    k, _ = synth.dup_u64(n, seed, distinct=alphabet)
+    return k
+
+
+@pytest.mark.parametrize("kt", ["u32", "u64"])
+@pytest.mark.parametrize("pairs", [False, True])
+def test_bucket_boundaries(ctx, kt, pairs):
+    rng = np.random.default_rng(1)
+    lens = np.asarray(BOUNDARY_LENS + list(rng.permutation(BOUNDARY_LENS)), dtype=np.int64)
+    off = synth.segment_offsets(lens)
+    n = int(off[-1])
+    keys = _keys(kt, n, 2, 1000)
+    vals = np.arange(n, dtype=np.uint32) if pairs else None
+    dk = to_dev(keys)
+    dv = to_dev(vals) if pairs else None
+    doff = to_dev(off)
+    ms.msort_segmented_sort(ctx, dk, doff, vals=dv)
+    ms.msort_ctx_sync(ctx)
+    ek, ev = oracle.segmented_sort(keys, off, vals)
+    assert np.array_equal(to_host(dk), ek)
+    if pairs:
+        assert np.array_equal(to_host(dv), ev)
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_log_uniform_batch(ctx, use_graph):
+    lens = synth.segment_lengths(3000, 5)
+    off = synth.segment_offsets(lens)
+    n = int(off[-1])
+    keys = synth.uniform_u32(n, 6)
+    doff = to_dev(off)
+    exp, _ = oracle.segmented_sort(keys, off)
+    dk = to_dev(keys)
+    for rep in range(3):   # graph: capture on the first call, replay afterwards
+        dk.copy_(to_dev(keys))
+        ms.msort_segmented_sort(ctx, dk, doff, options={"use_graph": int(use_graph)})
+        ms.msort_ctx_sync(ctx)
+        assert np.array_equal(to_host(dk), exp), f"rep {rep}"
+
+
+def test_malformed_offsets_rejected_on_device(ctx):
+    lens = np.asarray([5, 7, 9], dtype=np.int64)
+    off = synth.segment_offsets(lens)
+    off[2] = off[1] - 1          # decreasing
+    n = int(lens.sum())
+    keys = synth.uniform_u32(n, 7)
+    dk = to_dev(keys)
+    ms.msort_segmented_sort(ctx, dk, to_dev(off))
+    with pytest.raises(ms.MsortError) as e:
+        ms.msort_ctx_sync(ctx)
+    assert e.value.status == ms.MSORT_ERR_INVALID_ARG
+    assert np.array_equal(to_host(dk), keys)
+    ms.msort_ctx_sync(ctx)       # the status word was cleared
+
+
+def test_empty_batch(ctx):
+    d = torch.empty(0, dtype=torch.uint32, device="cuda")
+    ms.msort_segmented_sort(ctx, d, to_dev(np.zeros(1, dtype=np.uint64)), nseg=0)
+
+
+def test_full_workload_50000_segments(ctx):
+    """The batched workload itself: 50,000 segments, lengths log-uniform in
+    [1, 65536] (about 3e8 keys), uniform uint32 keys, graph replay."""
+    from synth import torch_gen
+    lens = synth.segment_lengths(50000, 1)
+    off = synth.segment_offsets(lens)
+    n = int(off[-1])
+    d = torch_gen.uniform_u32(n, 1, device="cuda")
+    keys = to_host(d)
+    ms.msort_segmented_sort(ctx, d, to_dev(off), options={"use_graph": 1})
+    ms.msort_ctx_sync(ctx)
+    exp, _ = oracle.segmented_sort(keys, off)
+    assert np.array_equal(to_host(d), exp)
