@@ -63,8 +63,14 @@ typedef struct {
                            not available for 64-bit key-value sorts */
     int merge_block;    /* outputs per merge block: 0, or the value the tile implies
                            (4352 for tiles of 17 keys per thread, 8448 for 33) */
-    int partition_mode; /* 0 = exact merge-path search, 1 = learned CDF predictor (verified) */
-    int learned_passes; /* with mode 1: final passes that use it; 0 = passes with runs >= 2^22 */
+    int partition_mode; /* 0 = exact merge-path binary search; 1 = learned CDF predictor
+                           (window verified, exact search inside, so the result is the same);
+                           2 = ratio guess d*|A|/(|A|+|B|) with the same verification
+                           (the learned mode without its model, for comparison);
+                           3 = exact binary search in the guided kernel (diagnostics: its
+                           probes are counted like modes 1 and 2) */
+    int learned_passes; /* with modes 1/2: how many final passes use the guided search;
+                           0 = the passes whose runs hold >= 2^22 keys */
     int use_graph;      /* 1 = replay the pass sequence from a captured CUDA graph */
     int reserved[3];    /* must be zero */
 } msort_options;
@@ -156,6 +162,41 @@ msort_status msort_sort_noalloc(const void* d_keys_in, const uint32_t* d_vals_in
 /* Largest n msort_sort_noalloc accepts for this key type (with or without
  * values). */
 size_t msort_noalloc_max_keys(msort_key_type kt, int with_vals);
+
+/* ---- learned partitioner: model access and checks ---------------------- */
+
+/* The network of partition_mode 1 (1 -> 32 -> 1, ReLU; 97 fp32 parameters
+ * ordered w1[32], b1[32], w2[32], b2) is fitted by mean squared error to the
+ * empirical CDF of a sorted key sample: target of the r-th of m samples is
+ * (r + 1/2) / m.  These calls run the library's own training kernels on
+ * caller data (m <= 65536), so that gradients and training can be checked
+ * against a reference. */
+/* d_grad[97] = gradient of the loss at d_params over d_x[0:m). */
+msort_status msort_mlp_grad(msort_ctx* ctx, const float* d_x, size_t m, const float* d_params, float* d_grad,
+                            void* stream);
+/* `steps` safeguarded Adam steps (betas 0.9/0.999, eps 1e-8, starting rate
+ * lr) on d_params in place: before each update the loss of the current
+ * parameters is compared with the best so far; if it is higher, the best
+ * parameters are restored, the rate halves and the Adam moments restart.
+ * A final check keeps the best parameters seen.  knot_init != 0 first sets
+ * d_params to the piecewise-linear interpolant through 32 quantiles of the
+ * sorted d_x. */
+msort_status msort_mlp_train(msort_ctx* ctx, const float* d_x, size_t m, float* d_params, int knot_init,
+                             int steps, float lr, void* stream);
+/* Copies the last model trained by a partition_mode 1 sort (97 floats) and
+ * its maximum error on its sample (nullable) to host memory; synchronises. */
+msort_status msort_learned_model(msort_ctx* ctx, float* h_params, float* h_err);
+/* Installs h_params (97 floats) and its error bound as the model of later
+ * partition_mode 1 sorts on ctx, which then skip sampling and training
+ * (a model trained once can serve many sorts of similar data).  Any model
+ * is safe: the prediction is verified and exact search completes it, so a
+ * poor model costs probes, never correctness.  h_params == NULL returns to
+ * training a fresh model per sort.  Synchronises the device. */
+msort_status msort_learned_set_model(msort_ctx* ctx, const float* h_params, float err);
+/* Probes (tests of A[a] <= B[d-1-a]) and searches made by guided partition
+ * launches (modes 1-3) while profiling was on; resets the counts.
+ * Synchronises the device. */
+msort_status msort_ctx_partition_stats(msort_ctx* ctx, uint64_t* probes, uint64_t* searches);
 
 /* ---- measurement ------------------------------------------------------ */
 

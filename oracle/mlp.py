@@ -80,6 +80,36 @@ def adam_step(p, g, m1, m2, step: int, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8
     return p - lr * mh / (np.sqrt(vh) + eps), m1, m2
 
 
+def train_guarded(p0, x, t, steps: int, lr: float = 1e-3):
+    """Safeguarded Adam, the training algorithm of the learned partitioner:
+    before each update the loss of the current parameters is compared with
+    the best so far; a higher loss restores the best parameters, halves the
+    rate and restarts the Adam moments (step counter back to 0).  A final
+    check keeps the best parameters.  Returns (parameters, loss history)."""
+    p = np.asarray(p0, dtype=np.float64).copy()
+    m1 = np.zeros_like(p)
+    m2 = np.zeros_like(p)
+    best, saved, k, seen = None, p.copy(), 0, False
+    hist = []
+    for _ in range(steps + 1):
+        cur = loss(p, x, t)
+        hist.append(cur)
+        final = len(hist) == steps + 1
+        if not seen or cur <= best:
+            best, saved, seen = cur, p.copy(), True
+            if not final:
+                g, _ = grad(p, x, t)
+                k += 1
+                p, m1, m2 = adam_step(p, g, m1, m2, k, lr=lr)
+        else:
+            p = saved.copy()
+            m1[:] = 0.0
+            m2[:] = 0.0
+            k = 0
+            lr *= 0.5
+    return p, hist
+
+
 def cdf(p, x):
     """The network read as a CDF: forward pass clamped to [0, 1]."""
     y, _, _ = forward(p, x)

@@ -51,6 +51,11 @@ _SIGS = {
     "msort_segmented_sort": ([_P, _P, _P, _P, _SZ, _SZ, _I, _OPT, _P], _ST),
     "msort_sort_noalloc": ([_P, _P, _P, _P, _SZ, _I, _P], _ST),
     "msort_noalloc_max_keys": ([_I, _I], _SZ),
+    "msort_mlp_grad": ([_P, _P, _SZ, _P, _P, _P], _ST),
+    "msort_mlp_train": ([_P, _P, _SZ, _P, _I, _I, ctypes.c_float, _P], _ST),
+    "msort_learned_model": ([_P, _P, _P], _ST),
+    "msort_learned_set_model": ([_P, _P, ctypes.c_float], _ST),
+    "msort_ctx_partition_stats": ([_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)], _ST),
     "msort_ctx_set_profiling": ([_P, _I], _ST),
     "msort_ctx_kernel_times": ([_P, _I, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)], _ST),
     "msort_ctx_launch_count": ([_P], ctypes.c_ulonglong),
@@ -229,6 +234,42 @@ def msort_sort_noalloc(keys_in, keys_out, vals_in=None, vals_out=None, n=None, k
 
 def msort_noalloc_max_keys(key_type: int, with_vals: bool) -> int:
     return int(load_library().msort_noalloc_max_keys(int(key_type), int(bool(with_vals))))
+
+
+def msort_mlp_grad(ctx, x, params, grad, m=None, stream=None) -> None:
+    _check(ctx, load_library().msort_mlp_grad(ctx, _ptr(x), _numel(x, m), _ptr(params), _ptr(grad),
+                                              _stream(stream, x)))
+
+
+def msort_mlp_train(ctx, x, params, steps: int, lr: float = 1e-3, knot_init: bool = False, m=None,
+                    stream=None) -> None:
+    _check(ctx, load_library().msort_mlp_train(ctx, _ptr(x), _numel(x, m), _ptr(params), int(bool(knot_init)),
+                                               int(steps), float(lr), _stream(stream, x)))
+
+
+def msort_learned_model(ctx):
+    """(97 parameters as a list, max sample error) of the last trained model."""
+    p = (ctypes.c_float * 97)()
+    e = ctypes.c_float()
+    _check(ctx, load_library().msort_learned_model(ctx, p, ctypes.byref(e)))
+    return list(p), float(e.value)
+
+
+def msort_learned_set_model(ctx, params, err: float = 0.0) -> None:
+    """Install a fixed model (sequence of 97 floats) for partition_mode 1, or
+    None to go back to training per sort."""
+    if params is None:
+        _check(ctx, load_library().msort_learned_set_model(ctx, None, 0.0))
+        return
+    arr = (ctypes.c_float * 97)(*[float(v) for v in params])
+    _check(ctx, load_library().msort_learned_set_model(ctx, arr, float(err)))
+
+
+def msort_ctx_partition_stats(ctx):
+    """(probes, searches) counted by guided partitions while profiling."""
+    a, b = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(ctx, load_library().msort_ctx_partition_stats(ctx, ctypes.byref(a), ctypes.byref(b)))
+    return int(a.value), int(b.value)
 
 
 def msort_ctx_set_profiling(ctx, on: bool) -> None:

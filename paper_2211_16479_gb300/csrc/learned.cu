@@ -1,29 +1,629 @@
-// Learned-CDF partitioner: placeholder until the training kernels land.
+// Learned-CDF partitioner for the final merge passes.
+//
+// The paper has no learned component: its merge tree hands each pair of
+// runs to one process (Section "MPI Merge Sort", Fig. 13) and only cites
+// Merge Path partitioning (Section "Related Research").  Here the co-rank
+// search that splits every merge pass into equal output blocks starts from
+// a prediction made by a small network, F: key -> [0, 1], an estimate of the
+// keys' cumulative distribution:
+//
+//   network   h_j = max(0, w1_j x + b1_j) (32 units), F(x) = clamp(w2 . h + b2)
+//   input     x = key / 2^32 (32-bit keys) or key / 2^64 (64-bit), in fp32
+//   data      2^16 keys drawn at seeded random positions of the input, sorted
+//             by this library's own sort; target of the r-th smallest is
+//             (r + 1/2) / 2^16
+//   init      piecewise-linear interpolant through 32 sample quantiles
+//   training  full-batch mean squared error, Adam (0.9, 0.999, 1e-8) from
+//             lr 1e-3 with a safeguard: a step whose loss is above the best
+//             so far is undone and the rate halved, so the model never ends
+//             worse than its initialisation; forward / backward / update
+//             kernels below reduce in a fixed order, so training is
+//             reproducible
+//
+// Prediction for runs A, B and output position d: start from the length
+// ratio a0 = d |A| / (|A| + |B|), then take two secant steps in F-space:
+// the model's values at the two probed keys, scaled by each run's density
+// in F-space (from the model's values at the run's first and last keys);
+// each probe also narrows the bracket by its exact comparison.
+// Verification: an exponential search outward from the prediction (probes
+// at distance 1, 2, 4, ... until the split is bracketed; J. L. Bentley and
+// A. C. Yao, "An almost optimal algorithm for unbounded searching", 1976),
+// then binary search inside the bracket.  A prediction off by e costs about
+// 2 log2(e) + 1 probes; the split returned is always the exact co-rank, so
+// the sort's output never changes, whatever the model.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <string>
+
 #include "learned.h"
+#include "launch.h"
+#include "sort_kernels.cuh"
 
 namespace msort {
 
-int learned_first_pass(const Plan& pl, size_t) { return pl.passes; }
+constexpr int kH = 32;
+constexpr int kNP = 3 * kH + 1;  // w1[32], b1[32], w2[32], b2
+constexpr int kSample = 1 << 16;
+constexpr int kTrainSteps = 32;
+constexpr int kTrainStride = 4;  // train on every 4th sorted sample (2^14 points)
+constexpr float kLr = 1e-3f;
+
+struct LearnedState {
+    unsigned char* block = nullptr;
+    uint64_t* sample = nullptr;
+    uint64_t* sorted = nullptr;
+    void* sort_scratch = nullptr;
+    float* x = nullptr;
+    float* dy = nullptr;
+    float* params = nullptr;
+    float* m1 = nullptr;
+    float* m2 = nullptr;
+    float* grad = nullptr;
+    float* err = nullptr;
+    unsigned long long* probes = nullptr;  // [0] probes, [1] searches
+    cudaStream_t side = nullptr;
+    cudaEvent_t input_ready = nullptr, model_ready = nullptr;
+    bool pending = false;
+    bool trained = false;
+    bool frozen = false;  // a caller-installed model: skip sampling and training
+    int key_bits = 32;
+};
+
+// ---------------------------------------------------------------------------
+// Device side
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float mlp_f(const float* p, float x) {
+    float y = p[3 * kH];
+#pragma unroll
+    for (int j = 0; j < kH; ++j) {
+        const float h = fmaxf(fmaf(p[j], x, p[kH + j]), 0.f);
+        y = fmaf(p[2 * kH + j], h, y);
+    }
+    return y;
+}
+
+__device__ __forceinline__ float clamp01(float v) { return fminf(fmaxf(v, 0.f), 1.f); }
 
 template <class K>
-msort_status learned_prepare(msort_ctx*, const Plan&, const K*, size_t, cudaStream_t) {
-    return fail(MSORT_ERR_UNSUPPORTED, "learned partitioning is not built yet");
+__device__ __forceinline__ float key_to_x(K k);
+template <>
+__device__ __forceinline__ float key_to_x<uint32_t>(uint32_t k) {
+    return __uint2float_rn(k) * 2.3283064365386963e-10f;  // k / 2^32, rounded to fp32
+}
+template <>
+__device__ __forceinline__ float key_to_x<uint64_t>(uint64_t k) {
+    return __ull2float_rn(k) * 5.421010862427522e-20f;  // k / 2^64, rounded to fp32
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Sample r = key at position floor(mix(seed, r) * n / 2^64).
+template <class K>
+__global__ void k_sample(const K* __restrict__ keys, size_t n, uint64_t seed, K* __restrict__ out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= kSample) return;
+    const uint64_t h = mix64(seed + (uint64_t)(r + 1) * 0x9E3779B97F4A7C15ull);
+    out[r] = keys[__umul64hi(h, (uint64_t)n)];
+}
+
+// x[r] = key_to_x(sorted[r * stride]) for r < m / stride.
+template <class K>
+__global__ void k_keys_to_x(const K* __restrict__ sorted, int m, int stride, float* __restrict__ x) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < m / stride) x[r] = key_to_x<K>(sorted[(size_t)r * stride + stride / 2]);
+}
+
+// Knot initialisation from sorted x (one block of kH threads): unit j is
+// relu(x - q_j) with q_j the sample quantile at (j + 1/2) / H; output
+// weights are the slope changes between consecutive knots.
+__global__ void k_knot_init(const float* __restrict__ x, int m, float* __restrict__ p, float* m1, float* m2) {
+    __shared__ float q[kH], slope[kH];
+    const int j = threadIdx.x;
+    const float rank_j = (j + 0.5f) / kH;
+    int idx = (int)(rank_j * m);
+    q[j] = x[idx < m ? idx : m - 1];
+    __syncthreads();
+    if (j < kH - 1) {
+        const float dx = q[j + 1] - q[j];
+        slope[j] = dx > 0.f ? (1.0f / kH) / dx : 0.f;
+    } else {
+        slope[j] = 0.f;
+    }
+    __syncthreads();
+    p[j] = 1.f;
+    p[kH + j] = -q[j];
+    p[2 * kH + j] = slope[j] - (j > 0 ? slope[j - 1] : 0.f);
+    if (j == 0) p[3 * kH] = 0.5f / kH;
+    for (int i = j; i < kNP; i += kH) {
+        m1[i] = 0.f;
+        m2[i] = 0.f;
+    }
+}
+
+// The whole safeguarded training in one block of 512 threads (one launch,
+// one SM, so it runs beside the sort without taking the GPU from it).
+// Per round: forward over all samples (dy to `dy`, loss by a fixed tree),
+// the guard (accept: save and update; reject: restore, halve the rate,
+// restart the moments), and on accept the backward pass with each warp
+// owning two hidden units (lane-strided sums, then a fixed xor-shuffle tree;
+// the warp of unit 0 also sums dy for b2) followed by Adam.  grad_only != 0: one forward and
+// backward at the given parameters, gradient to grad_out, no update.
+constexpr int kTrainThreads = 512;
+constexpr int kUnitsPerWarp = kH / (kTrainThreads / 32);
+__global__ void __launch_bounds__(kTrainThreads)
+k_mlp_train_fused(const float* __restrict__ x, int m, float* __restrict__ params, int steps, float lr0,
+                  float* __restrict__ dy, float* __restrict__ grad_out, int grad_only) {
+    __shared__ float p[kNP], g[kNP], m1[kNP], m2[kNP], saved[kNP];
+    __shared__ float red[kTrainThreads];
+    __shared__ float lr, best, pw1, pw2;  // pw1 = 0.9^k, pw2 = 0.999^k for the bias corrections
+    __shared__ int seen, accept;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int i = tid; i < kNP; i += kTrainThreads) {
+        p[i] = params[i];
+        m1[i] = 0.f;
+        m2[i] = 0.f;
+    }
+    if (tid == 0) {
+        lr = lr0;
+        best = 0.f;
+        pw1 = 1.f;
+        pw2 = 1.f;
+        seen = 0;
+    }
+    __syncthreads();
+    const float inv_m = 1.f / (float)m;
+    for (int round = 0;; ++round) {
+        float e2 = 0.f;
+        for (int r = tid; r < m; r += kTrainThreads) {
+            const float res = mlp_f(p, x[r]) - (r + 0.5f) * inv_m;
+            dy[r] = 2.f * res * inv_m;
+            e2 += res * res;
+        }
+        red[tid] = e2;
+        __syncthreads();
+        for (int w = kTrainThreads / 2; w > 0; w >>= 1) {
+            if (tid < w) red[tid] += red[tid + w];
+            __syncthreads();
+        }
+        const bool last = grad_only || round >= steps;  // a rejected final round re-checks once more
+        if (tid == 0) {
+            const float loss = red[0] * inv_m;
+            accept = grad_only || !seen || loss <= best;
+            if (accept) {
+                best = loss;
+                seen = 1;
+            } else {
+                lr *= 0.5f;
+                pw1 = 1.f;
+                pw2 = 1.f;
+            }
+        }
+        __syncthreads();
+        if (!accept) {
+            for (int i = tid; i < kNP; i += kTrainThreads) {
+                p[i] = saved[i];
+                m1[i] = 0.f;
+                m2[i] = 0.f;
+            }
+            __syncthreads();
+            continue;
+        }
+        if (!grad_only)
+            for (int i = tid; i < kNP; i += kTrainThreads) saved[i] = p[i];
+        if (last && !grad_only) break;
+        // backward: warp w -> units w * kUnitsPerWarp + u
+#pragma unroll
+        for (int u = 0; u < kUnitsPerWarp; ++u) {
+            const int j = warp * kUnitsPerWarp + u;
+            const float w1 = p[j], b1 = p[kH + j], w2 = p[2 * kH + j];
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, ab = 0.f;
+            for (int r = lane; r < m; r += 32) {
+                const float xr = x[r], d = dy[r];
+                const float pre = fmaf(w1, xr, b1);
+                const bool act = pre > 0.f;
+                const float h = act ? pre : 0.f;
+                const float gp = act ? d * w2 : 0.f;
+                a0 = fmaf(gp, xr, a0);
+                a1 += gp;
+                a2 = fmaf(d, h, a2);
+                if (j == 0) ab += d;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+                a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+                a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+                ab += __shfl_xor_sync(0xffffffffu, ab, o);
+            }
+            if (lane == 0) {
+                g[j] = a0;
+                g[kH + j] = a1;
+                g[2 * kH + j] = a2;
+                if (j == 0) g[3 * kH] = ab;
+            }
+        }
+        __syncthreads();
+        if (grad_only) {
+            for (int i = tid; i < kNP; i += kTrainThreads) grad_out[i] = g[i];
+            return;
+        }
+        if (tid < kNP) {
+            const float b1c = 0.9f, b2c = 0.999f, eps = 1e-8f;
+            const float c1 = 1.f - pw1 * b1c, c2 = 1.f - pw2 * b2c;  // 1 - beta^(k+1)
+            const float gi = g[tid];
+            const float a = b1c * m1[tid] + (1.f - b1c) * gi;
+            const float v = b2c * m2[tid] + (1.f - b2c) * gi * gi;
+            m1[tid] = a;
+            m2[tid] = v;
+            p[tid] -= lr * (a / c1) / (sqrtf(v / c2) + eps);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            pw1 *= 0.9f;
+            pw2 *= 0.999f;
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    for (int i = tid; i < kNP; i += kTrainThreads) params[i] = saved[i];
+}
+
+// err[0] = max_r |clamp(F(x_r)) - t_r| (one block, fixed reduction).
+__global__ void k_model_error(const float* __restrict__ x, int m, const float* __restrict__ params,
+                              float* __restrict__ err) {
+    constexpr int TH = 256;
+    __shared__ float p[kNP];
+    __shared__ float s[TH];
+    for (int i = threadIdx.x; i < kNP; i += TH) p[i] = params[i];
+    __syncthreads();
+    float e = 0.f;
+    for (int r = threadIdx.x; r < m; r += TH) e = fmaxf(e, fabsf(clamp01(mlp_f(p, x[r])) - (r + 0.5f) / m));
+    s[threadIdx.x] = e;
+    __syncthreads();
+    for (int w = TH / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s[threadIdx.x] = fmaxf(s[threadIdx.x], s[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) err[0] = s[0];
+}
+
+// Co-rank with a guided start.  params == nullptr: ratio guess (mode 2);
+// exact_only: no guess at all (plain binary search, mode 3, used to count
+// its probes).  Counts probes (one probe = one test of A[a] <= B[d-1-a]).
+template <class K>
+__global__ void k_partition_guided(const K* __restrict__ src, size_t n, size_t L, size_t W, size_t nblocks,
+                                   unsigned long long* __restrict__ splits, const float* __restrict__ params,
+                                   int exact_only,
+                                   unsigned long long* probes) {
+    __shared__ float p[kNP];
+    if (params)
+        for (int i = threadIdx.x; i < kNP; i += blockDim.x) p[i] = params[i];
+    __syncthreads();
+    const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nblocks) return;
+    const size_t out0 = c * W;
+    const PassGeom g = pass_geom(out0, n, L);
+    const K* A = src + g.pb;
+    const K* B = A + g.alen;
+    const size_t alen = g.alen, blen = g.blen, d = out0 - g.pb;
+    size_t lo = d > blen ? d - blen : 0;
+    size_t hi = d < alen ? d : alen;
+    unsigned long long np = 0;
+    if (lo < hi && !exact_only) {
+        size_t ahat = (size_t)((double)d * (double)alen / (double)(alen + blen));
+        ahat = ahat < lo ? lo : (ahat > hi ? hi : ahat);
+        if (params) {
+            // Secant steps in F-space.  A run's keys cover [F(first), F(last)]
+            // (the whole CDF for random-order runs, a sliver for presorted
+            // ones), so moving a by D shifts F(A[a]) by about D * sA and
+            // F(B[d-1-a]) by -D * sB, sR = (F(R_last) - F(R_first)) / |R|.
+            // At a probe a the two keys sit near the split, so the model's
+            // error largely cancels in F(B[d-1-a]) - F(A[a]).  Every probe
+            // also narrows the bracket by its exact comparison.
+            const float fa0 = mlp_f(p, key_to_x<K>(A[0])), fa1 = mlp_f(p, key_to_x<K>(A[alen - 1]));
+            const float fb0 = mlp_f(p, key_to_x<K>(B[0])), fb1 = mlp_f(p, key_to_x<K>(B[blen - 1]));
+            np += 2;
+            const float sA = fmaxf(fa1 - fa0, 1e-12f) / (float)alen;
+            const float sB = fmaxf(fb1 - fb0, 1e-12f) / (float)blen;
+            const float inv = 1.f / (sA + sB);
+            for (int it = 0; it < 2 && lo < hi && ahat < hi; ++it) {
+                const K ka = A[ahat], kb = B[d - 1 - ahat];
+                ++np;
+                if (ka <= kb)
+                    lo = ahat + 1;
+                else
+                    hi = ahat;
+                if (lo >= hi) break;
+                const float delta = (mlp_f(p, key_to_x<K>(kb)) - mlp_f(p, key_to_x<K>(ka))) * inv;
+                const float cand = (float)ahat + rintf(delta);
+                ahat = cand <= (float)lo ? lo : (cand >= (float)hi ? hi : (size_t)cand);
+            }
+        }
+        // Exponential search outward from the prediction; f(a) = A[a] <=
+        // B[d-1-a] is true below the split and false from it on.
+        if (ahat < hi && (++np, A[ahat] <= B[d - 1 - ahat])) {
+            size_t last_true = ahat, step = 1;
+            for (;;) {
+                const size_t probe = last_true + step;
+                if (probe >= hi) {
+                    lo = last_true + 1;
+                    break;
+                }
+                ++np;
+                if (A[probe] <= B[d - 1 - probe]) {
+                    last_true = probe;
+                    step *= 2;
+                } else {
+                    lo = last_true + 1;
+                    hi = probe;
+                    break;
+                }
+            }
+        } else {
+            size_t first_false = ahat, step = 1;  // the split is at or below ahat
+            while (first_false >= lo + step) {
+                const size_t probe = first_false - step;
+                ++np;
+                if (A[probe] <= B[d - 1 - probe]) {
+                    lo = probe + 1;
+                    break;
+                }
+                first_false = probe;
+                step *= 2;
+            }
+            hi = first_false;
+        }
+    }
+    while (lo < hi) {
+        const size_t mid = (lo + hi) >> 1;
+        ++np;
+        if (A[mid] <= B[d - 1 - mid])
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    splits[c] = lo;
+    if (probes) {
+        atomicAdd(&probes[0], np);
+        atomicAdd(&probes[1], 1ull);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+static LearnedState* state(msort_ctx* ctx) { return static_cast<LearnedState*>(ctx->learned); }
+
+static msort_status ensure_state(msort_ctx* ctx) {
+    if (ctx->learned) return MSORT_OK;
+    LearnedState* s = new LearnedState();
+    const size_t ssz = align_up(sort_keys_scratch<uint64_t>(kSample), 256);
+    const size_t bytes = 2 * (size_t)kSample * 8 + ssz + 2 * (size_t)kSample * 4 + 8 * 512 + 1024 + 256;
+    if (cudaMalloc(&s->block, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return fail(MSORT_ERR_OOM, "cudaMalloc of the learned-partitioner state failed");
+    }
+    unsigned char* q = s->block;
+    s->sample = reinterpret_cast<uint64_t*>(q);
+    q += (size_t)kSample * 8;
+    s->sorted = reinterpret_cast<uint64_t*>(q);
+    q += (size_t)kSample * 8;
+    s->sort_scratch = q;
+    q += ssz;
+    s->x = reinterpret_cast<float*>(q);
+    q += (size_t)kSample * 4;
+    s->dy = reinterpret_cast<float*>(q);
+    q += (size_t)kSample * 4;
+    s->params = reinterpret_cast<float*>(q);
+    q += 512;
+    s->m1 = reinterpret_cast<float*>(q);
+    q += 512;
+    s->m2 = reinterpret_cast<float*>(q);
+    q += 512;
+    s->grad = reinterpret_cast<float*>(q);
+    q += 512;
+    s->err = reinterpret_cast<float*>(q);
+    q += 512;
+    s->probes = reinterpret_cast<unsigned long long*>(q);
+    cudaMemset(s->probes, 0, 16);
+    cudaMemset(s->err, 0, 4);
+    int lo_prio = 0, hi_prio = 0;
+    cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+    // highest priority: the few blocks of the sample sort and training get
+    // scheduled ahead of the sort's own blocks as SMs free up
+    cudaStreamCreateWithPriority(&s->side, cudaStreamNonBlocking, hi_prio);
+    cudaEventCreateWithFlags(&s->input_ready, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&s->model_ready, cudaEventDisableTiming);
+    ctx->learned = s;
+    return MSORT_OK;
+}
+
+void learned_destroy(msort_ctx* ctx) {
+    LearnedState* s = state(ctx);
+    if (!s) return;
+    if (s->side) {
+        cudaStreamSynchronize(s->side);
+        cudaStreamDestroy(s->side);
+    }
+    if (s->input_ready) cudaEventDestroy(s->input_ready);
+    if (s->model_ready) cudaEventDestroy(s->model_ready);
+    cudaFree(s->block);
+    delete s;
+    ctx->learned = nullptr;
+}
+
+int learned_first_pass(const Plan& pl, size_t) {
+    if (pl.learned_passes > 0) return pl.passes > pl.learned_passes ? pl.passes - pl.learned_passes : 0;
+    int p = 0;
+    while (p < pl.passes && ((size_t)pl.tile << p) < ((size_t)1 << 22)) ++p;
+    return p;
+}
+
+static cudaError_t train_on(msort_ctx* ctx, LearnedState* s, const float* x, int m, float* params, int steps,
+                            float lr, cudaStream_t st) {
+    k_mlp_train_fused<<<1, kTrainThreads, 0, st>>>(x, m, params, steps, lr, s->dy, nullptr, 0);
+    ++ctx->launches;
+    return cudaGetLastError();
 }
 
 template <class K>
-cudaError_t launch_learned_partition(msort_ctx*, const Plan&, const K*, size_t, size_t, unsigned long long*,
-                                     cudaStream_t) {
-    return cudaErrorNotSupported;
+msort_status learned_prepare(msort_ctx* ctx, const Plan& pl, const K* keys, size_t n, cudaStream_t st) {
+    msort_status rs = ensure_state(ctx);
+    if (rs != MSORT_OK) return rs;
+    LearnedState* s = state(ctx);
+    if (s->frozen) return MSORT_OK;
+    cudaError_t e = cudaEventRecord(s->input_ready, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->side, s->input_ready, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "learned partitioner stream order");
+    K* sample = reinterpret_cast<K*>(s->sample);
+    K* sorted = reinterpret_cast<K*>(s->sorted);
+    k_sample<K><<<kSample / 256, 256, 0, s->side>>>(keys, n, 0x5EEDull + n, sample);
+    ++ctx->launches;
+    rs = sort_keys_internal<K>(ctx, sample, sorted, kSample, s->sort_scratch, s->side);
+    if (rs != MSORT_OK) return rs;
+    const int mt = kSample / kTrainStride;
+    k_keys_to_x<K><<<mt / 256, 256, 0, s->side>>>(sorted, kSample, kTrainStride, s->x);
+    k_knot_init<<<1, kH, 0, s->side>>>(s->x, mt, s->params, s->m1, s->m2);
+    ctx->launches += 2;
+    e = train_on(ctx, s, s->x, mt, s->params, kTrainSteps, kLr, s->side);
+    if (e == cudaSuccess) {
+        k_model_error<<<1, 256, 0, s->side>>>(s->x, mt, s->params, s->err);
+        ++ctx->launches;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(s->model_ready, s->side);
+    if (e != cudaSuccess) return cuda_fail(e, "learned partitioner training launch");
+    s->pending = true;
+    s->trained = true;
+    s->key_bits = 8 * (int)sizeof(K);
+    return MSORT_OK;
+}
+
+template <class K>
+cudaError_t launch_guided_partition(msort_ctx* ctx, const Plan& pl, const K* src, size_t n, size_t L,
+                                    unsigned long long* splits, cudaStream_t st) {
+    if (ensure_state(ctx) != MSORT_OK) return cudaErrorMemoryAllocation;
+    LearnedState* s = state(ctx);
+    const bool model = pl.partition_mode == 1;
+    const int exact_only = pl.partition_mode == 3;
+    if (model && s->pending) {
+        cudaError_t e = cudaStreamWaitEvent(st, s->model_ready, 0);
+        if (e != cudaSuccess) return e;
+        s->pending = false;
+    }
+    const size_t nblocks = (n + pl.W - 1) / pl.W;
+    const unsigned th = 128;
+    k_partition_guided<K><<<(unsigned)((nblocks + th - 1) / th), th, 0, st>>>(
+        src, n, L, (size_t)pl.W, nblocks, splits, model ? s->params : nullptr, exact_only,
+        ctx->profiling ? s->probes : nullptr);
+    return cudaGetLastError();
 }
 
 template msort_status learned_prepare<uint32_t>(msort_ctx*, const Plan&, const uint32_t*, size_t, cudaStream_t);
 template msort_status learned_prepare<uint64_t>(msort_ctx*, const Plan&, const uint64_t*, size_t, cudaStream_t);
-template cudaError_t launch_learned_partition<uint32_t>(msort_ctx*, const Plan&, const uint32_t*, size_t, size_t,
-                                                        unsigned long long*, cudaStream_t);
-template cudaError_t launch_learned_partition<uint64_t>(msort_ctx*, const Plan&, const uint64_t*, size_t, size_t,
-                                                        unsigned long long*, cudaStream_t);
-
-void learned_destroy(msort_ctx*) {}
-
+template cudaError_t launch_guided_partition<uint32_t>(msort_ctx*, const Plan&, const uint32_t*, size_t, size_t,
+                                                       unsigned long long*, cudaStream_t);
+template cudaError_t launch_guided_partition<uint64_t>(msort_ctx*, const Plan&, const uint64_t*, size_t, size_t,
+                                                       unsigned long long*, cudaStream_t);
 
 }  // namespace msort
+
+using namespace msort;
+
+extern "C" {
+
+msort_status msort_mlp_grad(msort_ctx* ctx, const float* d_x, size_t m, const float* d_params, float* d_grad,
+                            void* stream) {
+    if (!ctx || !d_x || !d_params || !d_grad) return fail(MSORT_ERR_INVALID_ARG, "NULL argument");
+    if (m == 0 || m > (size_t)kSample) return fail(MSORT_ERR_INVALID_ARG, "m must be in [1, 65536]");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    cudaSetDevice(ctx->device);
+    msort_status rs = ensure_state(ctx);
+    if (rs != MSORT_OK) return rs;
+    LearnedState* s = state(ctx);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStreamSynchronize(s->side);
+    k_mlp_train_fused<<<1, kTrainThreads, 0, st>>>(d_x, (int)m, const_cast<float*>(d_params), 0, 0.f, s->dy, d_grad,
+                                                   1);
+    ++ctx->launches;
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MSORT_OK : cuda_fail(e, "gradient launch");
+}
+
+msort_status msort_mlp_train(msort_ctx* ctx, const float* d_x, size_t m, float* d_params, int knot_init, int steps,
+                             float lr, void* stream) {
+    if (!ctx || !d_x || !d_params) return fail(MSORT_ERR_INVALID_ARG, "NULL argument");
+    if (m == 0 || m > (size_t)kSample) return fail(MSORT_ERR_INVALID_ARG, "m must be in [1, 65536]");
+    if (steps < 0) return fail(MSORT_ERR_INVALID_ARG, "steps must be >= 0");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    cudaSetDevice(ctx->device);
+    msort_status rs = ensure_state(ctx);
+    if (rs != MSORT_OK) return rs;
+    LearnedState* s = state(ctx);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStreamSynchronize(s->side);
+    if (knot_init) {
+        k_knot_init<<<1, kH, 0, st>>>(d_x, (int)m, d_params, s->m1, s->m2);
+        ++ctx->launches;
+    }
+    cudaError_t e = train_on(ctx, s, d_x, (int)m, d_params, steps, lr, st);
+    return e == cudaSuccess ? MSORT_OK : cuda_fail(e, "training launch");
+}
+
+msort_status msort_learned_model(msort_ctx* ctx, float* h_params, float* h_err) {
+    if (!ctx || !h_params) return fail(MSORT_ERR_INVALID_ARG, "NULL argument");
+    LearnedState* s = state(ctx);
+    if (!s || !s->trained) return fail(MSORT_ERR_INVALID_ARG, "no model trained on this context yet");
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(s->side);
+    cudaError_t e = cudaMemcpy(h_params, s->params, kNP * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && h_err) e = cudaMemcpy(h_err, s->err, sizeof(float), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? MSORT_OK : cuda_fail(e, "model read");
+}
+
+msort_status msort_learned_set_model(msort_ctx* ctx, const float* h_params, float err) {
+    if (!ctx) return fail(MSORT_ERR_INVALID_ARG, "ctx is NULL");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    cudaSetDevice(ctx->device);
+    msort_status rs = ensure_state(ctx);
+    if (rs != MSORT_OK) return rs;
+    LearnedState* s = state(ctx);
+    cudaStreamSynchronize(s->side);
+    cudaDeviceSynchronize();
+    if (!h_params) {
+        s->frozen = false;
+        return MSORT_OK;
+    }
+    cudaError_t e = cudaMemcpy(s->params, h_params, kNP * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->err, &err, sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "model upload");
+    s->frozen = true;
+    s->trained = true;
+    s->pending = false;
+    return MSORT_OK;
+}
+
+msort_status msort_ctx_partition_stats(msort_ctx* ctx, uint64_t* probes, uint64_t* searches) {
+    if (!ctx || !probes || !searches) return fail(MSORT_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    cudaSetDevice(ctx->device);
+    msort_status rs = ensure_state(ctx);
+    if (rs != MSORT_OK) return rs;
+    LearnedState* s = state(ctx);
+    cudaDeviceSynchronize();
+    unsigned long long h[2] = {0, 0};
+    cudaError_t e = cudaMemcpy(h, s->probes, 16, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(s->probes, 0, 16);
+    if (e != cudaSuccess) return cuda_fail(e, "partition stats");
+    *probes = h[0];
+    *searches = h[1];
+    return MSORT_OK;
+}
+
+}  // extern "C"

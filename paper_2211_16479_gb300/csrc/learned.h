@@ -7,18 +7,26 @@
 
 namespace msort {
 
-// First merge pass (0-based) whose partition uses the learned predictor.
+// First merge pass (0-based) whose partition uses the guided search.
 int learned_first_pass(const Plan& pl, size_t n);
 // Draw the key sample from the unsorted input, sort it and train the network
-// on the device, all enqueued on st before the sort's tile pass.
+// on the device.  Runs on a side stream that waits for `st`; the first
+// guided partition launch on `st` waits for the training to finish.
 template <class K>
 msort_status learned_prepare(msort_ctx* ctx, const Plan& pl, const K* keys, size_t n, cudaStream_t st);
-// Partition launch that starts each co-rank search from the network's
-// prediction and verifies it (exact search remains the fallback).
+// Partition launch that starts each co-rank search from a prediction (the
+// network's in mode 1, the length ratio in mode 2) and verifies it; exact
+// binary search finishes inside the verified bracket.
 template <class K>
-cudaError_t launch_learned_partition(msort_ctx* ctx, const Plan& pl, const K* src, size_t n, size_t L,
-                                     unsigned long long* splits, cudaStream_t st);
+cudaError_t launch_guided_partition(msort_ctx* ctx, const Plan& pl, const K* src, size_t n, size_t L,
+                                    unsigned long long* splits, cudaStream_t st);
 void learned_destroy(msort_ctx* ctx);
 void graphs_destroy(msort_ctx* ctx);
+
+// Plain keys-only sort with caller-provided scratch (used for the sample).
+template <class K>
+size_t sort_keys_scratch(size_t n);
+template <class K>
+msort_status sort_keys_internal(msort_ctx* ctx, const K* in, K* out, size_t n, void* scratch, cudaStream_t st);
 
 }  // namespace msort

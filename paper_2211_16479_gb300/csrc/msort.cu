@@ -134,11 +134,13 @@ static size_t scratch_need(size_t n, const Plan& pl) {
     return b;
 }
 
-// The whole sort on stream st.  kin may equal kout (in-place).
+// The whole sort on stream st.  kin may equal kout (in-place).  `scratch`
+// holds the ping-pong buffer and the split table (scratch_need bytes);
+// `log` brackets launches with the profiling events.
 template <class K, bool PAIRS>
 static msort_status run_sort(msort_ctx* ctx, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n,
-                             const Plan& pl, cudaStream_t st) {
-    unsigned char* sp = static_cast<unsigned char*>(ctx->scratch);
+                             const Plan& pl, void* scratch, bool log, cudaStream_t st) {
+    unsigned char* sp = static_cast<unsigned char*>(scratch);
     K* tk = reinterpret_cast<K*>(sp);
     sp += align_up(n * sizeof(K), 256);
     uint32_t* tv = nullptr;
@@ -152,31 +154,55 @@ static msort_status run_sort(msort_ctx* ctx, const K* kin, const uint32_t* vin, 
     uint32_t* bv[2] = {vout, tv};
     int cur = (pl.passes & 1) ? 1 : 0;
     cudaError_t e;
-    prof_begin(ctx, KK_TILE, st);
+    if (log) prof_begin(ctx, KK_TILE, st);
     e = launch_tile<K, PAIRS>(pl, kin, vin, bk[cur], bv[cur], n, st);
-    prof_end(ctx, KK_TILE, st);
+    if (log) prof_end(ctx, KK_TILE, st);
     ++ctx->launches;
     if (e != cudaSuccess) return cuda_fail(e, ("tile sort launch" + last_launch_info()).c_str());
-    const int first_learned = pl.partition_mode == 1 ? learned_first_pass(pl, n) : pl.passes;
+    const int first_guided = pl.partition_mode != 0 ? learned_first_pass(pl, n) : pl.passes;
     for (int p = 0; p < pl.passes; ++p) {
         const size_t L = (size_t)pl.tile << p;
-        prof_begin(ctx, KK_PARTITION, st);
-        if (p >= first_learned)
-            e = launch_learned_partition<K>(ctx, pl, bk[cur], n, L, splits, st);
+        if (log) prof_begin(ctx, KK_PARTITION, st);
+        if (p >= first_guided)
+            e = launch_guided_partition<K>(ctx, pl, bk[cur], n, L, splits, st);
         else
             e = launch_partition<K>(pl, bk[cur], n, L, splits, st);
-        prof_end(ctx, KK_PARTITION, st);
+        if (log) prof_end(ctx, KK_PARTITION, st);
         ++ctx->launches;
         if (e != cudaSuccess) return cuda_fail(e, "partition launch");
-        prof_begin(ctx, KK_MERGE, st);
+        if (log) prof_begin(ctx, KK_MERGE, st);
         e = launch_merge<K, PAIRS>(pl, bk[cur], bk[cur ^ 1], bv[cur], bv[cur ^ 1], n, L, splits, st);
-        prof_end(ctx, KK_MERGE, st);
+        if (log) prof_end(ctx, KK_MERGE, st);
         ++ctx->launches;
         if (e != cudaSuccess) return cuda_fail(e, ("merge pass launch" + last_launch_info()).c_str());
         cur ^= 1;
     }
     return MSORT_OK;
 }
+
+template <class K>
+size_t sort_keys_scratch(size_t n) {
+    Plan pl;
+    std::string why;
+    make_plan<K, false>(n, nullptr, &pl, &why);
+    return scratch_need<K, false>(n, pl);
+}
+
+template <class K>
+msort_status sort_keys_internal(msort_ctx* ctx, const K* in, K* out, size_t n, void* scratch, cudaStream_t st) {
+    Plan pl;
+    std::string why;
+    if (!make_plan<K, false>(n, nullptr, &pl, &why)) return fail(MSORT_ERR_INVALID_ARG, why);
+    pl.status = ctx->d_status;
+    return run_sort<K, false>(ctx, in, nullptr, out, nullptr, n, pl, scratch, false, st);
+}
+
+template size_t sort_keys_scratch<uint32_t>(size_t);
+template size_t sort_keys_scratch<uint64_t>(size_t);
+template msort_status sort_keys_internal<uint32_t>(msort_ctx*, const uint32_t*, uint32_t*, size_t, void*,
+                                                   cudaStream_t);
+template msort_status sort_keys_internal<uint64_t>(msort_ctx*, const uint64_t*, uint64_t*, size_t, void*,
+                                                   cudaStream_t);
 
 template <class K, bool PAIRS>
 static msort_status sort_entry(msort_ctx* ctx, const void* kin, const uint32_t* vin, void* kout, uint32_t* vout,
@@ -195,7 +221,8 @@ static msort_status sort_entry(msort_ctx* ctx, const void* kin, const uint32_t* 
         s = learned_prepare<K>(ctx, pl, static_cast<const K*>(kin), n, st);
         if (s != MSORT_OK) return s;
     }
-    s = run_sort<K, PAIRS>(ctx, static_cast<const K*>(kin), vin, static_cast<K*>(kout), vout, n, pl, st);
+    s = run_sort<K, PAIRS>(ctx, static_cast<const K*>(kin), vin, static_cast<K*>(kout), vout, n, pl, ctx->scratch,
+                           true, st);
     scratch_release(ctx, st);
     return s;
 }
@@ -206,8 +233,8 @@ static msort_status check_common(msort_ctx* ctx, msort_key_type kt, const msort_
     if (opt) {
         for (int r : opt->reserved)
             if (r) return fail(MSORT_ERR_INVALID_ARG, "options.reserved must be zero");
-        if (opt->partition_mode != 0 && opt->partition_mode != 1)
-            return fail(MSORT_ERR_INVALID_ARG, "options.partition_mode must be 0 or 1");
+        if (opt->partition_mode < 0 || opt->partition_mode > 3)
+            return fail(MSORT_ERR_INVALID_ARG, "options.partition_mode must be 0, 1, 2 or 3");
         if (opt->learned_passes < 0) return fail(MSORT_ERR_INVALID_ARG, "options.learned_passes must be >= 0");
     }
     return MSORT_OK;

@@ -89,3 +89,34 @@ def test_training_lowers_loss():
         g, _ = mlp.grad(p, xs, t)
         p, m1, m2 = mlp.adam_step(p, g, m1, m2, step, lr=1e-3)
     assert mlp.loss(p, xs, t) < l0
+
+
+def _skewed_sample(m=4096):
+    rng = np.random.default_rng(11)
+    x = np.sort(np.concatenate([rng.lognormal(-9, 1.0, m // 2), rng.lognormal(-5, 0.5, m // 2)]))
+    return np.clip(x, 0, 1), (np.arange(m) + 0.5) / m
+
+
+def test_guarded_training_never_ends_worse():
+    # plain Adam at lr 1e-3 diverges from the knot fit on skewed keys; the
+    # safeguard must undo those steps and still end at or below the start
+    x, t = _skewed_sample()
+    p0 = mlp.knot_init(x)
+    p, hist = mlp.train_guarded(p0, x, t, steps=60, lr=1e-3)
+    assert mlp.loss(p, x, t) <= hist[0]
+    assert any(b > a for a, b in zip(hist, hist[1:])), "expected at least one rejected step"
+
+
+def test_guarded_training_is_adam_while_loss_falls():
+    rng = np.random.default_rng(12)
+    x = np.sort(rng.uniform(0, 1, 2048))
+    t = (np.arange(len(x)) + 0.5) / len(x)
+    p0 = mlp.knot_init(x)
+    steps = 5
+    p, hist = mlp.train_guarded(p0, x, t, steps=steps, lr=1e-5)
+    assert all(b <= a for a, b in zip(hist, hist[1:])), "loss rose; choose a smaller rate for this pin"
+    q, a, b = p0.copy(), np.zeros_like(p0), np.zeros_like(p0)
+    for k in range(1, steps + 1):
+        g, _ = mlp.grad(q, x, t)
+        q, a, b = mlp.adam_step(q, g, a, b, k, lr=1e-5)
+    assert np.allclose(p, q, rtol=0, atol=1e-15)
