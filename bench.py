@@ -351,6 +351,235 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Additional workloads (one JSON line each; the default run is the 2^28 sort)
+# ---------------------------------------------------------------------------
+def _events_ms(fn, reps, stream=None):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _base_line(metric, value, unit, args, ms_per_step, config, **extra):
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "data": "synthetic (seeded SplitMix64 recipes, generated on the device)",
+            "config": config}
+    line.update(extra)
+    return line
+
+
+def run_pairs(args):
+    """Stable key-value sort of 2^27 pairs: uint64 keys from 2^20 distinct
+    values, uint32 values = original index."""
+    import torch
+
+    import paper_2211_16479_gb300 as ms
+    from synth import torch_gen
+    n = 1 << 27
+    keys, vals = torch_gen.dup_u64(n, 1, device="cuda")
+    ok, ov = torch.empty_like(keys), torch.empty_like(vals)
+    ctx = ms.Context(0)
+    h = ctx.handle
+    step = lambda: ms.msort_sort_copy(h, keys, ok, vals, ov)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # stability guard: equal keys keep increasing original indices
+    k64 = ok.view(torch.int64) ^ torch.iinfo(torch.int64).min
+    v64 = ov.to(torch.int64)
+    same = k64[1:] == k64[:-1]
+    assert bool((k64[1:] >= k64[:-1]).all()) and bool((v64[1:][same] > v64[:-1][same]).all())
+    t = _events_ms(step, args.steps)
+    T, W, P = ms.msort_plan_info(n, ms.MSORT_U64, True)
+    alg = 2 * n * 12 * (1 + P)
+    peak, kind = _peaks()
+    line = _base_line("Gpairs/s sorted (stable, 2^27 uint64 keys + uint32 values)", n / t / 1e6, "Gpairs/s", args, t,
+                      {"workload": "2^27 (uint64 key, uint32 original index) pairs, keys from 2^20 distinct values",
+                       "n": n, "tile": T, "merge_block_outputs": W, "merge_passes": P},
+                      dtype="u64+u32",
+                      whole_sort_roofline={"algorithmic_bytes": alg,
+                                           "frac_of_measured_hbm": alg / (t * 1e-3) / 1e9 / peak,
+                                           "frac_of_8tbs": alg / (t * 1e-3) / 1e9 / NOMINAL_HBM_GBS})
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_segmented(args):
+    """50,000 uint32 arrays with lengths log-uniform in [1, 65536]."""
+    import numpy as np
+    import torch
+
+    import paper_2211_16479_gb300 as ms
+    import synth
+    from synth import torch_gen
+    lens = synth.segment_lengths(50000, 1)
+    off = synth.segment_offsets(lens)
+    n = int(off[-1])
+    src = torch_gen.uniform_u32(n, 1, device="cuda")
+    work = torch.empty_like(src)
+    doff = torch.from_numpy(off).cuda()
+    ctx = ms.Context(0)
+    h = ctx.handle
+    copy_ms = _events_ms(lambda: work.copy_(src), 5)
+
+    def seg(graph):
+        work.copy_(src)
+        ms.msort_segmented_sort(h, work, doff, options={"use_graph": graph})
+    res = {}
+    for graph in (0, 1):
+        for _ in range(args.warmup):
+            seg(graph)
+        res[graph] = _events_ms(lambda: seg(graph), args.steps) - copy_ms
+    ms.msort_ctx_sync(h)
+    # plain sort alternative with identical output: one global sort of
+    # (segment index << 32 | key) as 64-bit keys
+    seg_id = torch.repeat_interleave(torch.arange(len(lens), device="cuda", dtype=torch.int64),
+                                     torch.from_numpy(lens).cuda())
+    comp = ((seg_id << 32) | src.to(torch.int64)).view(torch.uint64)
+    out = torch.empty_like(comp)
+    for _ in range(args.warmup):
+        ms.msort_sort_copy(h, comp, out)
+    plain = _events_ms(lambda: ms.msort_sort_copy(h, comp, out), args.steps)
+    same = bool(torch.equal((out.view(torch.int64) & 0xFFFFFFFF).to(torch.uint32).view(torch.int32),
+                            work.view(torch.int32)))
+    # plain sort per segment, looped, on the 500 longest segments (extrapolated by keys)
+    big = np.argsort(-lens)[:500]
+    def loop():
+        for s in big:
+            ms.msort_sort(h, work[int(off[s]):int(off[s + 1])])
+    loop_ms = _events_ms(loop, 1)
+    loop_keys = int(lens[big].sum())
+    best = min(res.values())
+    line = _base_line("Gkeys/s sorted (batched segmented sort, 50,000 uint32 arrays)", n / best / 1e6, "Gkeys/s",
+                      args, best,
+                      {"workload": "50,000 uint32 arrays, lengths log-uniform in [1, 65536], uniform keys", "n": n,
+                       "segments": 50000},
+                      dtype="u32",
+                      eager_ms=res[0], graph_ms=res[1],
+                      plain_composite_sort={"ms": plain, "gkeys_per_s": n / plain / 1e6,
+                                            "identical_output": same},
+                      plain_per_segment_loop={"segments": 500, "keys": loop_keys, "ms": loop_ms,
+                                              "gkeys_per_s": loop_keys / loop_ms / 1e6},
+                      speedup_vs_plain=plain / best)
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_learned(args):
+    """2^30 uint32 keys from the lognormal mixture: exact vs learned partition."""
+    import torch
+
+    import paper_2211_16479_gb300 as ms
+    from synth import torch_gen
+    n = 1 << 30
+    src = torch_gen.lognormal3_u32(n, 1, device="cuda")
+    out = torch.empty_like(src)
+    ctx = ms.Context(0)
+    h = ctx.handle
+    modes = {"exact": {}, "learned_final_passes": {"partition_mode": 1},
+             "learned_all_passes": {"partition_mode": 1, "learned_passes": 64},
+             "ratio_guess_all_passes": {"partition_mode": 2, "learned_passes": 64}}
+    times, same = {}, {}
+    ref = None
+    for name, o in modes.items():
+        for _ in range(args.warmup):
+            ms.msort_sort_copy(h, src, out, options=o)
+        times[name] = _events_ms(lambda: ms.msort_sort_copy(h, src, out, options=o), args.steps)
+        if ref is None:
+            ref = out.clone()
+        same[name] = bool(torch.equal(out.view(torch.int32), ref.view(torch.int32)))
+    probes = {}
+    for name, o in list(modes.items()) + [("exact_counted_all_passes", {"partition_mode": 3, "learned_passes": 64})]:
+        ms.msort_ctx_set_profiling(h, True)
+        ms.msort_sort_copy(h, src, out, options=o)
+        torch.cuda.synchronize()
+        pl, pt = ms.msort_ctx_kernel_times(h, ms.MSORT_KERNEL_PARTITION)
+        pr, se = ms.msort_ctx_partition_stats(h)
+        ms.msort_ctx_set_profiling(h, False)
+        probes[name] = {"partition_ms": pt, "probes_per_search": (pr / se) if se else None}
+    _, err = ms.msort_learned_model(h)
+    best = times["learned_all_passes"]
+    line = _base_line("Gkeys/s sorted (2^30 uint32 lognormal mixture, learned co-rank partition)", n / best / 1e6,
+                      "Gkeys/s", args, best,
+                      {"workload": "2^30 uint32 keys, lognormal mixture (0.5/0.3/0.2; mu 14/18/21; sigma 1/0.5/0.3)",
+                       "n": n},
+                      dtype="u32",
+                      modes_ms=times, gkeys_per_s={k: n / v / 1e6 for k, v in times.items()},
+                      speedup_vs_exact=times["exact"] / best,
+                      identical_output_to_exact=same,
+                      partition=probes, model_max_sample_error=err)
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_serving(args):
+    """Poisson arrivals of sort requests, sizes log-uniform in [2^10, 2^24],
+    8 GB budget: continuous batching (8 slots) vs a FIFO queue alone (1 slot)."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    import paper_2211_16479_gb300 as ms
+    import synth
+    from synth import torch_gen
+    count = 2000
+    _, sizes = synth.poisson_requests(count, 1, rate_per_s=1.0)
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    total = int(offs[-1])
+    buf = torch.empty(total, dtype=torch.uint32, device="cuda")
+
+    def refill():
+        buf.copy_(torch_gen.uniform_u32(total, 7, device="cuda"))
+        torch.cuda.synchronize()
+
+    def run(slots, rate):
+        refill()
+        t_arr, _ = synth.poisson_requests(count, 1, rate_per_s=rate) if rate else (np.zeros(count), None)
+        with ms.Server(0, mem_budget_bytes=8 << 30, max_slots=slots) as srv:
+            ids = []
+            t0 = time.perf_counter()
+            for i in range(count):
+                if rate:
+                    while time.perf_counter() - t0 < t_arr[i]:
+                        pass
+                ids.append(srv.submit(buf[int(offs[i]):int(offs[i + 1])]))
+            for rid in ids:
+                srv.wait(rid, 600000.0)
+            wall = time.perf_counter() - t0
+            st = srv.stats()
+        return {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+                "gkeys_per_s": total / wall / 1e9, "max_inflight": st["max_inflight"],
+                "arena_high_water_gb": st["arena_high_water"] / 1e9}
+
+    # saturation: everything submitted at once
+    sat1 = run(1, 0.0)
+    sat8 = run(8, 0.0)
+    mean_keys = float(np.mean(sizes))
+    mu = sat1["gkeys_per_s"] * 1e9 / mean_keys        # plain service rate, requests/s
+    loads = {}
+    for rho in (0.3, 0.6, 0.9):
+        loads[str(rho)] = {"fifo_1_slot": run(1, rho * mu), "continuous_8_slots": run(8, rho * mu),
+                           "rate_per_s": rho * mu}
+    line = _base_line("Gkeys/s served (continuous batching of sort requests, saturation)", sat8["gkeys_per_s"],
+                      "Gkeys/s", args, 1e3 * total / (sat8["gkeys_per_s"] * 1e9),
+                      {"workload": "2000 uint32 sort requests, sizes log-uniform in [2^10, 2^24], Poisson arrivals, "
+                                   "8 GB budget", "requests": count, "keys": total},
+                      dtype="u32",
+                      saturation={"fifo_1_slot": sat1, "continuous_8_slots": sat8},
+                      speedup_vs_fifo=sat8["gkeys_per_s"] / sat1["gkeys_per_s"],
+                      poisson_load=loads, p50_ms=loads["0.6"]["continuous_8_slots"]["p50_ms"],
+                      p99_ms=loads["0.6"]["continuous_8_slots"]["p99_ms"])
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -364,11 +593,16 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", default="sort", choices=["sort", "pairs", "segmented", "learned", "serving"])
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "sort":
+        fn = {"pairs": run_pairs, "segmented": run_segmented, "learned": run_learned, "serving": run_serving}
+        fn[args.workload](args)
+        return 0
     return run_ours(args)
 
 

@@ -137,6 +137,45 @@ msort_status msort_sort_host(msort_ctx* ctx, const void* h_keys_in, const uint32
                              void* h_keys_out, uint32_t* h_vals_out, size_t n, msort_key_type kt,
                              const msort_options* opt, void* stream);
 
+/* ---- serving: continuous batching of sort requests ---------------------- */
+
+/* A server owns one GPU-side loop (a host thread), max_slots CUDA streams
+ * and a device arena of mem_budget_bytes from which every admitted
+ * request's scratch is carved.  Requests are admitted in FIFO order as soon
+ * as a slot is free and their scratch fits in the arena; admitted requests
+ * run concurrently on their slots' streams, and each completion immediately
+ * frees its slot and memory for the next queued request.  The budget is a
+ * hard cap: no device memory is allocated while serving.  (Serving is not
+ * in the paper; each request is the paper's sort of one array.) */
+typedef struct msort_server msort_server;
+
+typedef struct {
+    uint64_t completed;        /* requests finished since the last reset */
+    uint64_t queued;           /* waiting for a slot or memory */
+    uint64_t inflight;         /* on the GPU now */
+    uint64_t max_inflight;     /* most requests on the GPU at once */
+    double p50_ms, p99_ms, max_ms; /* submit-to-completion latency */
+    double keys_per_s;         /* keys completed / (last completion - first submit) */
+    uint64_t arena_high_water; /* most scratch bytes in use at once (<= budget) */
+    uint64_t budget;           /* arena size in bytes */
+} msort_server_stats;
+
+msort_status msort_server_create(int device, size_t mem_budget_bytes, int max_slots, msort_server** out);
+/* Queues an in-place stable sort of d_keys[0:n) (and d_vals, nullable); the
+ * buffers must stay valid and untouched until the request is done.  Never
+ * blocks.  MSORT_ERR_OOM if the request's scratch alone exceeds the budget. */
+msort_status msort_server_submit(msort_server* s, void* d_keys, uint32_t* d_vals, size_t n, msort_key_type kt,
+                                 uint64_t* req_id);
+/* *done = 1 once the request finished (its latency in *latency_ms, nullable);
+ * returns the request's own status when done. */
+msort_status msort_server_poll(msort_server* s, uint64_t req_id, int* done, double* latency_ms);
+/* Blocks until the request finishes or timeout_ms passes (MSORT_ERR_TIMEOUT). */
+msort_status msort_server_wait(msort_server* s, uint64_t req_id, double timeout_ms, double* latency_ms);
+msort_status msort_server_get_stats(msort_server* s, msort_server_stats* out);
+msort_status msort_server_reset_stats(msort_server* s);
+/* Finishes every queued and running request, then frees the server. */
+msort_status msort_server_destroy(msort_server* s);
+
 /* ---- sorting without device allocation -------------------------------- */
 
 /* The paper has no counterpart to this entry point; it exists for callers

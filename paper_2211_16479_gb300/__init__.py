@@ -37,6 +37,13 @@ class msort_options(ctypes.Structure):
 _P, _SZ, _I, _ST = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int
 _OPT = ctypes.POINTER(msort_options)
 
+
+class msort_server_stats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("queued", ctypes.c_uint64), ("inflight", ctypes.c_uint64),
+                ("max_inflight", ctypes.c_uint64), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("keys_per_s", ctypes.c_double),
+                ("arena_high_water", ctypes.c_uint64), ("budget", ctypes.c_uint64)]
+
 _SIGS = {
     "msort_ctx_create": ([_I, _SZ, ctypes.POINTER(_P)], _ST),
     "msort_ctx_destroy": ([_P], _ST),
@@ -56,6 +63,13 @@ _SIGS = {
     "msort_learned_model": ([_P, _P, _P], _ST),
     "msort_learned_set_model": ([_P, _P, ctypes.c_float], _ST),
     "msort_ctx_partition_stats": ([_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)], _ST),
+    "msort_server_create": ([_I, _SZ, _I, ctypes.POINTER(_P)], _ST),
+    "msort_server_submit": ([_P, _P, _P, _SZ, _I, ctypes.POINTER(ctypes.c_uint64)], _ST),
+    "msort_server_poll": ([_P, ctypes.c_uint64, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)], _ST),
+    "msort_server_wait": ([_P, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)], _ST),
+    "msort_server_get_stats": ([_P, ctypes.POINTER(msort_server_stats)], _ST),
+    "msort_server_reset_stats": ([_P], _ST),
+    "msort_server_destroy": ([_P], _ST),
     "msort_ctx_set_profiling": ([_P, _I], _ST),
     "msort_ctx_kernel_times": ([_P, _I, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)], _ST),
     "msort_ctx_launch_count": ([_P], ctypes.c_ulonglong),
@@ -286,6 +300,75 @@ def msort_ctx_kernel_times(ctx, kind: int):
 
 def msort_ctx_launch_count(ctx) -> int:
     return int(load_library().msort_ctx_launch_count(ctx))
+
+
+def msort_server_create(device: int = 0, mem_budget_bytes: int = 8 << 30, max_slots: int = 8):
+    out = ctypes.c_void_p()
+    _check(None, load_library().msort_server_create(int(device), int(mem_budget_bytes), int(max_slots),
+                                                    ctypes.byref(out)))
+    return out
+
+
+def msort_server_submit(server, keys, vals=None, n=None, key_type=None) -> int:
+    rid = ctypes.c_uint64()
+    _check(None, load_library().msort_server_submit(server, _ptr(keys), _ptr(vals), _numel(keys, n),
+                                                    _key_type(keys, key_type), ctypes.byref(rid)))
+    return int(rid.value)
+
+
+def msort_server_poll(server, req_id: int):
+    """(done, latency_ms)."""
+    done = ctypes.c_int()
+    lat = ctypes.c_double()
+    _check(None, load_library().msort_server_poll(server, int(req_id), ctypes.byref(done), ctypes.byref(lat)))
+    return bool(done.value), float(lat.value)
+
+
+def msort_server_wait(server, req_id: int, timeout_ms: float = 60000.0) -> float:
+    lat = ctypes.c_double()
+    _check(None, load_library().msort_server_wait(server, int(req_id), float(timeout_ms), ctypes.byref(lat)))
+    return float(lat.value)
+
+
+def msort_server_get_stats(server) -> dict:
+    st = msort_server_stats()
+    _check(None, load_library().msort_server_get_stats(server, ctypes.byref(st)))
+    return {name: getattr(st, name) for name, _ in st._fields_}
+
+
+def msort_server_reset_stats(server) -> None:
+    _check(None, load_library().msort_server_reset_stats(server))
+
+
+def msort_server_destroy(server) -> None:
+    _check(None, load_library().msort_server_destroy(server))
+
+
+class Server:
+    """Owns a msort serving loop; usable as a context manager."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 8 << 30, max_slots: int = 8):
+        self.handle = msort_server_create(device, mem_budget_bytes, max_slots)
+
+    def submit(self, keys, vals=None) -> int:
+        return msort_server_submit(self.handle, keys, vals)
+
+    def wait(self, req_id: int, timeout_ms: float = 60000.0) -> float:
+        return msort_server_wait(self.handle, req_id, timeout_ms)
+
+    def stats(self) -> dict:
+        return msort_server_get_stats(self.handle)
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            msort_server_destroy(self.handle)
+        self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class Context:

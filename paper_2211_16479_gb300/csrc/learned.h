@@ -29,4 +29,10 @@ size_t sort_keys_scratch(size_t n);
 template <class K>
 msort_status sort_keys_internal(msort_ctx* ctx, const K* in, K* out, size_t n, void* scratch, cudaStream_t st);
 
+// Any sort with caller-provided scratch (serving loop arena).
+template <class K, bool PAIRS>
+msort_status sort_with_scratch(msort_ctx* ctx, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n,
+                               void* scratch, cudaStream_t st);
+size_t sort_scratch_need(size_t n, int key_bytes, bool pairs);
+
 }  // namespace msort

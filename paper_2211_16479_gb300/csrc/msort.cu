@@ -197,6 +197,40 @@ msort_status sort_keys_internal(msort_ctx* ctx, const K* in, K* out, size_t n, v
     return run_sort<K, false>(ctx, in, nullptr, out, nullptr, n, pl, scratch, false, st);
 }
 
+// Any sort (keys or pairs, in or out of place) with caller-provided scratch
+// of scratch_need bytes; used by the serving loop, whose scratch comes from
+// its own arena.  No allocation, no host synchronisation.
+template <class K, bool PAIRS>
+msort_status sort_with_scratch(msort_ctx* ctx, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n,
+                               void* scratch, cudaStream_t st) {
+    Plan pl;
+    std::string why;
+    if (!make_plan<K, PAIRS>(n, nullptr, &pl, &why)) return fail(MSORT_ERR_INVALID_ARG, why);
+    if (n == 0) return MSORT_OK;
+    pl.status = ctx->d_status;
+    return run_sort<K, PAIRS>(ctx, kin, vin, kout, vout, n, pl, scratch, false, st);
+}
+
+size_t sort_scratch_need(size_t n, int key_bytes, bool pairs) {
+    Plan pl;
+    std::string why;
+    if (key_bytes == 4) {
+        if (pairs) return make_plan<uint32_t, true>(n, nullptr, &pl, &why) ? scratch_need<uint32_t, true>(n, pl) : 0;
+        return make_plan<uint32_t, false>(n, nullptr, &pl, &why) ? scratch_need<uint32_t, false>(n, pl) : 0;
+    }
+    if (pairs) return make_plan<uint64_t, true>(n, nullptr, &pl, &why) ? scratch_need<uint64_t, true>(n, pl) : 0;
+    return make_plan<uint64_t, false>(n, nullptr, &pl, &why) ? scratch_need<uint64_t, false>(n, pl) : 0;
+}
+
+template msort_status sort_with_scratch<uint32_t, false>(msort_ctx*, const uint32_t*, const uint32_t*, uint32_t*,
+                                                         uint32_t*, size_t, void*, cudaStream_t);
+template msort_status sort_with_scratch<uint32_t, true>(msort_ctx*, const uint32_t*, const uint32_t*, uint32_t*,
+                                                        uint32_t*, size_t, void*, cudaStream_t);
+template msort_status sort_with_scratch<uint64_t, false>(msort_ctx*, const uint64_t*, const uint32_t*, uint64_t*,
+                                                         uint32_t*, size_t, void*, cudaStream_t);
+template msort_status sort_with_scratch<uint64_t, true>(msort_ctx*, const uint64_t*, const uint32_t*, uint64_t*,
+                                                        uint32_t*, size_t, void*, cudaStream_t);
+
 template size_t sort_keys_scratch<uint32_t>(size_t);
 template size_t sort_keys_scratch<uint64_t>(size_t);
 template msort_status sort_keys_internal<uint32_t>(msort_ctx*, const uint32_t*, uint32_t*, size_t, void*,
