@@ -267,11 +267,8 @@ def run_ours(args):
         s1.synchronize()
         per_dist[d] = round(3 * n / (s0.elapsed_time(s1) * 1e-3) / 1e9, 3)
 
-    t_max = elapsed_ms
-    if dist:
-        tt = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
-        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    from paper_2211_16479_gb300 import dist as msdist
+    t_max = msdist.max_over_ranks(elapsed_ms, device=dev)
     keys_total = args.steps * len(DISTS) * n * world
     value = keys_total / (t_max * 1e-3) / 1e9
 
@@ -298,11 +295,7 @@ def run_ours(args):
             for a in h_in:
                 ms.msort_sort_host(h, a, out_keys=h_out, options=opts, stream=stream)
         barrier()
-        te = time.perf_counter() - t0
-        if dist:
-            tt = torch.tensor([te], device=dev, dtype=torch.float64)
-            tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
-            te = float(tt.item())
+        te = msdist.max_over_ranks(time.perf_counter() - t0, device=dev)
         e2e = {"value": args.e2e_steps * len(DISTS) * n * world / te / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": len(DISTS) * n * 4, "d2h_bytes_per_step": len(DISTS) * n * 4,
                "steps": args.e2e_steps}

@@ -128,6 +128,15 @@ msort_status msort_segmented_sort(msort_ctx* ctx, void* d_keys, uint32_t* d_vals
                                   size_t nseg, size_t n, msort_key_type kt, const msort_options* opt,
                                   void* stream);
 
+/* Stable merge of two sorted arrays: d_out[0:na+nb) = merge(d_a[0:na),
+ * d_b[0:nb)), equal keys taking from d_a first (one round of the paper's
+ * merge tree, Section "MPI Merge Sort", Fig. 13).  d_vout non-NULL merges
+ * values alongside (d_va, d_vb required).  The output must not overlap the
+ * inputs.  Scratch: the context's split table. */
+msort_status msort_merge(msort_ctx* ctx, const void* d_a, const uint32_t* d_va, size_t na, const void* d_b,
+                         const uint32_t* d_vb, size_t nb, void* d_out, uint32_t* d_vout, msort_key_type kt,
+                         void* stream);
+
 /* Host-buffer sort: copies h_keys_in (and h_vals_in, nullable) to the
  * device, sorts there, and copies the result to h_keys_out (and h_vals_out;
  * give both value pointers or neither).  Output may be the same buffer as

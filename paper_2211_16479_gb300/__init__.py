@@ -55,6 +55,7 @@ _SIGS = {
     "msort_sort_pairs": ([_P, _P, _P, _SZ, _I, _OPT, _P], _ST),
     "msort_sort_copy": ([_P, _P, _P, _P, _P, _SZ, _I, _OPT, _P], _ST),
     "msort_sort_host": ([_P, _P, _P, _P, _P, _SZ, _I, _OPT, _P], _ST),
+    "msort_merge": ([_P, _P, _P, _SZ, _P, _P, _SZ, _P, _P, _I, _P], _ST),
     "msort_segmented_sort": ([_P, _P, _P, _P, _SZ, _SZ, _I, _OPT, _P], _ST),
     "msort_sort_noalloc": ([_P, _P, _P, _P, _SZ, _I, _P], _ST),
     "msort_noalloc_max_keys": ([_I, _I], _SZ),
@@ -223,6 +224,13 @@ def msort_segmented_sort(ctx, keys, offsets, vals=None, nseg=None, n=None, key_t
     _check(ctx, load_library().msort_segmented_sort(ctx, _ptr(keys), _ptr(vals), _ptr(offsets), nseg,
                                                     _numel(keys, n), _key_type(keys, key_type), _opts(options),
                                                     _stream(stream, keys)))
+
+
+def msort_merge(ctx, a, b, out, va=None, vb=None, vout=None, key_type=None, stream=None) -> None:
+    """out = stable merge of sorted a and b (ties from a first)."""
+    _check(ctx, load_library().msort_merge(ctx, _ptr(a), _ptr(va), _numel(a, None), _ptr(b), _ptr(vb),
+                                           _numel(b, None), _ptr(out), _ptr(vout), _key_type(a, key_type),
+                                           _stream(stream, out)))
 
 
 def msort_sort_host(ctx, keys, vals=None, out_keys=None, out_vals=None, n=None, key_type=None,

@@ -30,6 +30,13 @@ cudaError_t launch_merge(const Plan& pl, const K* src, K* dst, const uint32_t* v
 template <class K>
 cudaError_t launch_partition(const Plan& pl, const K* src, size_t n, size_t L, unsigned long long* splits,
                              cudaStream_t st);
+// Stable merge of two separate sorted arrays into out (splits: nblocks + 1).
+template <class K, bool PAIRS>
+cudaError_t launch_merge_two(const K* A, size_t na, const K* B, size_t nb, const uint32_t* va, const uint32_t* vb,
+                             K* out, uint32_t* vout, unsigned long long* splits, unsigned int* status,
+                             cudaStream_t st);
+template <class K, bool PAIRS>
+size_t merge_two_block();
 // Resource summary of the last kernel the calling thread prepared to launch.
 const std::string& last_launch_info();
 

@@ -94,6 +94,38 @@ cudaError_t launch_partition(const Plan& pl, const K* src, size_t n, size_t L, u
     return cudaGetLastError();
 }
 
+// Merge blocks of 256 threads x 33 keys for 32-bit keys-only merges, 256 x 17
+// otherwise (register pressure).
+template <class K, bool PAIRS>
+size_t merge_two_block() {
+    return (sizeof(K) == 4 && !PAIRS) ? 256 * 33 : 256 * 17;
+}
+
+template <class K, bool PAIRS>
+cudaError_t launch_merge_two(const K* A, size_t na, const K* B, size_t nb, const uint32_t* va, const uint32_t* vb,
+                             K* out, uint32_t* vout, unsigned long long* splits, unsigned int* status,
+                             cudaStream_t st) {
+    const size_t W = merge_two_block<K, PAIRS>();
+    const size_t total = na + nb;
+    if (total == 0) return cudaSuccess;
+    const size_t nblocks = (total + W - 1) / W;
+    k_partition_two<K><<<(unsigned)((nblocks + 127) / 128), 128, 0, st>>>(A, na, B, nb, W, nblocks, splits);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (W == 256 * 33) {
+        auto f = k_merge_two<K, PAIRS, 256, 33>;
+        const size_t sm = merge_block_smem<K, PAIRS, 256, 33>();
+        if ((e = prepare(f, sm)) != cudaSuccess) return e;
+        f<<<(unsigned)nblocks, 256, sm, st>>>(A, na, B, nb, va, vb, out, vout, splits, status);
+    } else {
+        auto f = k_merge_two<K, PAIRS, 256, 17>;
+        const size_t sm = merge_block_smem<K, PAIRS, 256, 17>();
+        if ((e = prepare(f, sm)) != cudaSuccess) return e;
+        f<<<(unsigned)nblocks, 256, sm, st>>>(A, na, B, nb, va, vb, out, vout, splits, status);
+    }
+    return cudaGetLastError();
+}
+
 #define MSORT_INSTANTIATE(K)                                                                                    \
     template size_t tile_smem_bytes<K, false>(int);                                                             \
     template size_t tile_smem_bytes<K, true>(int);                                                              \
@@ -110,6 +142,14 @@ cudaError_t launch_partition(const Plan& pl, const K* src, size_t n, size_t L, u
     template cudaError_t launch_merge<K, true>(const Plan&, const K*, K*, const uint32_t*, uint32_t*, size_t,   \
                                                size_t, const unsigned long long*, cudaStream_t);                \
     template cudaError_t launch_partition<K>(const Plan&, const K*, size_t, size_t, unsigned long long*,        \
-                                             cudaStream_t);
+                                             cudaStream_t);                                                     \
+    template size_t merge_two_block<K, false>();                                                                \
+    template size_t merge_two_block<K, true>();                                                                 \
+    template cudaError_t launch_merge_two<K, false>(const K*, size_t, const K*, size_t, const uint32_t*,         \
+                                                    const uint32_t*, K*, uint32_t*, unsigned long long*,        \
+                                                    unsigned int*, cudaStream_t);                               \
+    template cudaError_t launch_merge_two<K, true>(const K*, size_t, const K*, size_t, const uint32_t*,          \
+                                                   const uint32_t*, K*, uint32_t*, unsigned long long*,         \
+                                                   unsigned int*, cudaStream_t);
 
 }  // namespace msort

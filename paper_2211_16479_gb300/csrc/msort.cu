@@ -395,6 +395,48 @@ msort_status msort_sort_copy(msort_ctx* ctx, const void* kin, const uint32_t* vi
                : sort_entry<uint64_t, false>(ctx, kin, nullptr, kout, nullptr, n, opt, st);
 }
 
+msort_status msort_merge(msort_ctx* ctx, const void* d_a, const uint32_t* d_va, size_t na, const void* d_b,
+                         const uint32_t* d_vb, size_t nb, void* d_out, uint32_t* d_vout, msort_key_type kt,
+                         void* stream) {
+    msort_status s = check_common(ctx, kt, nullptr);
+    if (s != MSORT_OK) return s;
+    if (na + nb == 0) return MSORT_OK;
+    if ((na && !d_a) || (nb && !d_b) || !d_out) return fail(MSORT_ERR_INVALID_ARG, "key pointer is NULL");
+    const bool pairs = d_vout != nullptr;
+    if (pairs && ((na && !d_va) || (nb && !d_vb))) return fail(MSORT_ERR_INVALID_ARG, "value pointer is NULL");
+    const size_t ks = kt == MSORT_U32 ? 4 : 8;
+    const size_t W = kt == MSORT_U32 ? (pairs ? merge_two_block<uint32_t, true>() : merge_two_block<uint32_t, false>())
+                                     : (pairs ? merge_two_block<uint64_t, true>() : merge_two_block<uint64_t, false>());
+    const size_t nblocks = (na + nb + W - 1) / W;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    s = ensure_scratch(ctx, (nblocks + 1) * sizeof(unsigned long long), st);
+    if (s != MSORT_OK) return s;
+    unsigned long long* splits = static_cast<unsigned long long*>(ctx->scratch);
+    cudaError_t e;
+    if (kt == MSORT_U32) {
+        const uint32_t* a = static_cast<const uint32_t*>(d_a);
+        const uint32_t* b = static_cast<const uint32_t*>(d_b);
+        uint32_t* o = static_cast<uint32_t*>(d_out);
+        e = pairs ? launch_merge_two<uint32_t, true>(a, na, b, nb, d_va, d_vb, o, d_vout, splits, ctx->d_status, st)
+                  : launch_merge_two<uint32_t, false>(a, na, b, nb, nullptr, nullptr, o, nullptr, splits,
+                                                      ctx->d_status, st);
+    } else {
+        const uint64_t* a = static_cast<const uint64_t*>(d_a);
+        const uint64_t* b = static_cast<const uint64_t*>(d_b);
+        uint64_t* o = static_cast<uint64_t*>(d_out);
+        e = pairs ? launch_merge_two<uint64_t, true>(a, na, b, nb, d_va, d_vb, o, d_vout, splits, ctx->d_status, st)
+                  : launch_merge_two<uint64_t, false>(a, na, b, nb, nullptr, nullptr, o, nullptr, splits,
+                                                      ctx->d_status, st);
+    }
+    ctx->launches += 2;
+    scratch_release(ctx, st);
+    if (e != cudaSuccess) return cuda_fail(e, ("merge launch" + last_launch_info()).c_str());
+    (void)ks;
+    return MSORT_OK;
+}
+
 msort_status msort_sort(msort_ctx* ctx, void* d_keys, size_t n, msort_key_type kt, const msort_options* opt,
                         void* stream) {
     return msort_sort_copy(ctx, d_keys, nullptr, d_keys, nullptr, n, kt, opt, stream);

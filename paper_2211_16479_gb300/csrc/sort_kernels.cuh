@@ -612,4 +612,42 @@ k_merge_pass(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __r
                                         smem_raw, &bar, phase, status);
 }
 
+// ---------------------------------------------------------------------------
+// Merge of two separate sorted arrays (one round of the paper's merge tree
+// as a library call): splits over out[0, na + nb), then one merge block per
+// W outputs.
+// ---------------------------------------------------------------------------
+template <class K>
+__global__ void k_partition_two(const K* __restrict__ A, size_t na, const K* __restrict__ B, size_t nb, size_t W,
+                                size_t nblocks, unsigned long long* __restrict__ splits) {
+    const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nblocks) return;
+    splits[c] = corank_search(A, na, B, nb, c * W);
+}
+
+template <class K, bool PAIRS, int THREADS, int IPT>
+__global__ void __launch_bounds__(THREADS)
+k_merge_two(const K* __restrict__ A, size_t na, const K* __restrict__ B, size_t nb, const uint32_t* __restrict__ va,
+            const uint32_t* __restrict__ vb, K* __restrict__ out, uint32_t* __restrict__ vout,
+            const unsigned long long* __restrict__ splits, unsigned int* status) {
+    constexpr int W = THREADS * IPT;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    const size_t c = blockIdx.x;
+    const size_t d0 = c * W, dend = na + nb;
+    const size_t d1 = d0 + W < dend ? d0 + W : dend;
+    const size_t a0 = splits[c];
+    const size_t a1 = d1 == dend ? na : (size_t)splits[c + 1];
+    const size_t b0 = d0 - a0;
+    const int nA = (int)(a1 - a0);
+    const int nB = (int)(d1 - d0) - nA;
+    uint32_t phase = 0;
+    merge_block<K, PAIRS, THREADS, IPT>(A + a0, nA, B + b0, nB, PAIRS ? va + a0 : nullptr, PAIRS ? vb + b0 : nullptr,
+                                        out + d0, PAIRS ? vout + d0 : nullptr, smem_raw, &bar, phase, status);
+}
+
 }  // namespace msort

@@ -1,0 +1,67 @@
+"""GPU parity of msort_merge (one round of the merge tree) and of the
+distributed tree-merge sort on one GPU rank."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_util import need_gpu, to_dev, to_host, torch
+
+ms = pytest.importorskip("paper_2211_16479_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    need_gpu()
+    c = ms.Context(0)
+    yield c.handle
+    c.close()
+
+
+@pytest.mark.parametrize("kt", ["u32", "u64"])
+@pytest.mark.parametrize("pairs", [False, True])
+@pytest.mark.parametrize("na,nb", [(0, 0), (0, 5), (7, 0), (1, 1), (4351, 4353), (8448, 1), (100000, 37),
+                                   (1 << 20, (1 << 19) + 3)])
+def test_merge_two_runs(ctx, kt, pairs, na, nb):
+    if kt == "u32":
+        a = np.sort(synth.uniform_u32(na, 1) % np.uint32(500))
+        b = np.sort(synth.uniform_u32(nb, 2) % np.uint32(500))
+    else:
+        a = np.sort(synth.dup_u64(na, 1, distinct=300)[0])
+        b = np.sort(synth.dup_u64(nb, 2, distinct=300)[0])
+    va = np.arange(na, dtype=np.uint32) if pairs else None
+    vb = np.arange(na, na + nb, dtype=np.uint32) if pairs else None
+    da, db = to_dev(a), to_dev(b)
+    out = torch.empty(na + nb, dtype=da.dtype, device="cuda")
+    dva = to_dev(va) if pairs else None
+    dvb = to_dev(vb) if pairs else None
+    vout = torch.empty(na + nb, dtype=torch.uint32, device="cuda") if pairs else None
+    ms.msort_merge(ctx, da, db, out, va=dva, vb=dvb, vout=vout)
+    ek, ev = oracle.merge(a, b, va, vb)
+    assert np.array_equal(to_host(out), ek)
+    if pairs:
+        assert np.array_equal(to_host(vout), ev)
+
+
+def test_tree_merge_sort_single_gpu_rank(ctx):
+    import datetime
+    import os
+    import socket
+
+    import torch.distributed as tdist
+
+    from paper_2211_16479_gb300 import dist
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    tdist.init_process_group("nccl", rank=0, world_size=1, timeout=datetime.timedelta(seconds=60))
+    try:
+        keys = synth.uniform_u32(300001, 4)
+        out = dist.tree_merge_sort(to_dev(keys), ctx=ctx)
+        assert np.array_equal(to_host(out), oracle.sort(keys)[0])
+    finally:
+        tdist.destroy_process_group()
