@@ -211,6 +211,23 @@ msort_status msort_sort_noalloc(const void* d_keys_in, const uint32_t* d_vals_in
  * values). */
 size_t msort_noalloc_max_keys(msort_key_type kt, int with_vals);
 
+/* ---- autotuning ---------------------------------------------------------- */
+
+/* Times every tile shape (tile size = threads x keys per thread, which also
+ * fixes the merge block) of the plain sort for 32/64-bit keys, with and
+ * without values, at n = 2^16, 2^20 and 2^24 (quick != 0: 2^20 only), and
+ * the segmented sort's bucket shapes for 32-bit keys; each candidate's output
+ * must equal the first candidate's bit for bit or the candidate is rejected.
+ * The winners are used by later calls on ctx whose options leave tile at 0
+ * (size class = largest tuned class not above log2(n)).  cache_path
+ * (nullable) receives the results as JSON.  Allocates its own test buffers
+ * and synchronises the device; meant for start-up, not for a hot loop. */
+msort_status msort_tune(msort_ctx* ctx, const char* cache_path, int quick);
+/* Loads results written by msort_tune into ctx. */
+msort_status msort_tune_load(msort_ctx* ctx, const char* cache_path);
+/* Forgets tuned choices (back to the built-in defaults). */
+msort_status msort_tune_clear(msort_ctx* ctx);
+
 /* ---- learned partitioner: model access and checks ---------------------- */
 
 /* The network of partition_mode 1 (1 -> 32 -> 1, ReLU; 97 fp32 parameters

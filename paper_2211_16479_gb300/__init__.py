@@ -59,6 +59,9 @@ _SIGS = {
     "msort_segmented_sort": ([_P, _P, _P, _P, _SZ, _SZ, _I, _OPT, _P], _ST),
     "msort_sort_noalloc": ([_P, _P, _P, _P, _SZ, _I, _P], _ST),
     "msort_noalloc_max_keys": ([_I, _I], _SZ),
+    "msort_tune": ([_P, ctypes.c_char_p, _I], _ST),
+    "msort_tune_load": ([_P, ctypes.c_char_p], _ST),
+    "msort_tune_clear": ([_P], _ST),
     "msort_mlp_grad": ([_P, _P, _SZ, _P, _P, _P], _ST),
     "msort_mlp_train": ([_P, _P, _SZ, _P, _I, _I, ctypes.c_float, _P], _ST),
     "msort_learned_model": ([_P, _P, _P], _ST),
@@ -256,6 +259,18 @@ def msort_sort_noalloc(keys_in, keys_out, vals_in=None, vals_out=None, n=None, k
 
 def msort_noalloc_max_keys(key_type: int, with_vals: bool) -> int:
     return int(load_library().msort_noalloc_max_keys(int(key_type), int(bool(with_vals))))
+
+
+def msort_tune(ctx, cache_path=None, quick: bool = False) -> None:
+    _check(ctx, load_library().msort_tune(ctx, cache_path.encode() if cache_path else None, int(bool(quick))))
+
+
+def msort_tune_load(ctx, cache_path: str) -> None:
+    _check(ctx, load_library().msort_tune_load(ctx, cache_path.encode()))
+
+
+def msort_tune_clear(ctx) -> None:
+    _check(ctx, load_library().msort_tune_clear(ctx))
 
 
 def msort_mlp_grad(ctx, x, params, grad, m=None, stream=None) -> None:

@@ -4,8 +4,10 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/msort.h"
@@ -50,8 +52,13 @@ struct msort_ctx {
     std::mutex mu;
     // learned partitioner state (owned by learned.cu)
     void* learned = nullptr;
-    // graph cache (owned by msort.cu)
+    // graph cache (owned by segmented.cu)
     void* graphs = nullptr;
+    // autotuned choices (msort_tune): (key bytes, values, log2 size class) -> tile
+    std::map<std::tuple<int, int, int>, int> tuned_tile;
+    // segmented sort of 32-bit keys: largest on-chip bucket and large-segment tile (0 = default)
+    int seg_max_small = 0;
+    int seg_large_tile = 0;
 };
 
 namespace msort {

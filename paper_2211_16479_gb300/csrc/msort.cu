@@ -96,8 +96,10 @@ const std::string& last_launch_info() { return launch_info_ref(); }
 
 template <class K, bool PAIRS>
 static int default_tile() {
-    if (!PAIRS) return sizeof(K) == 4 ? 16896 : 8448;
-    return sizeof(K) == 4 ? 8448 : 8704;
+    // measured best on GB300 (msort_tune): 512 x 33 for 32-bit keys alone,
+    // 512 x 17 for 64-bit keys or key-value pairs
+    if (!PAIRS && sizeof(K) == 4) return 16896;
+    return 8704;
 }
 
 template <class K, bool PAIRS>
@@ -238,9 +240,39 @@ template msort_status sort_keys_internal<uint32_t>(msort_ctx*, const uint32_t*, 
 template msort_status sort_keys_internal<uint64_t>(msort_ctx*, const uint64_t*, uint64_t*, size_t, void*,
                                                    cudaStream_t);
 
+// Tuned tile for (key type, values, n): the entry of the largest tuned size
+// class not above log2(n) (or the smallest class), 0 if nothing was tuned.
+static int tuned_tile_for(const msort_ctx* ctx, int key_bytes, bool pairs, size_t n) {
+    int best = 0, best_cls = -1, lowest = 0, lowest_cls = 1 << 30;
+    int lg = 0;
+    while (lg < 63 && (size_t(1) << (lg + 1)) <= n) ++lg;
+    for (const auto& kv : ctx->tuned_tile) {
+        if (std::get<0>(kv.first) != key_bytes || std::get<1>(kv.first) != (int)pairs) continue;
+        const int cls = std::get<2>(kv.first);
+        if (cls <= lg && cls > best_cls) {
+            best_cls = cls;
+            best = kv.second;
+        }
+        if (cls < lowest_cls) {
+            lowest_cls = cls;
+            lowest = kv.second;
+        }
+    }
+    return best ? best : lowest;
+}
+
 template <class K, bool PAIRS>
 static msort_status sort_entry(msort_ctx* ctx, const void* kin, const uint32_t* vin, void* kout, uint32_t* vout,
                                size_t n, const msort_options* opt, cudaStream_t st) {
+    msort_options tuned_opt{};
+    if (!opt || !opt->tile) {
+        const int tile = tuned_tile_for(ctx, (int)sizeof(K), PAIRS, n);
+        if (tile) {
+            if (opt) tuned_opt = *opt;
+            tuned_opt.tile = tile;
+            opt = &tuned_opt;
+        }
+    }
     Plan pl;
     std::string why;
     if (!make_plan<K, PAIRS>(n, opt, &pl, &why)) return fail(MSORT_ERR_INVALID_ARG, why);

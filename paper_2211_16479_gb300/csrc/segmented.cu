@@ -264,26 +264,36 @@ struct SegPlan;
     if ((e = launch_small<K, PAIRS, 128, 17>(keys, vals, off, nseg, lists, counters, 1, status, st))) return e; \
     if ((e = launch_small<K, PAIRS, 256, 33>(keys, vals, off, nseg, lists, counters, 2, status, st))) return e;
 
+// 32-bit keys only: the largest on-chip bucket (16896 or 33792 keys) and the
+// large-segment tile (8448 or 16896) are tunable (msort_tune).
 template <>
 struct SegPlan<uint32_t, false> {
-    static SegBuckets buckets() { return SegBuckets{5, {544, 2176, 8448, 16896, 33792, 0}}; }
-    static cudaError_t run(uint32_t* keys, uint32_t* vals, uint32_t* tk, uint32_t* tv, const unsigned long long* off,
-                           size_t nseg, const unsigned int* lists, unsigned int* counters, unsigned int* status,
-                           cudaStream_t st) {
+    static SegBuckets buckets(const msort_ctx* ctx) {
+        if (ctx && ctx->seg_max_small == 16896) return SegBuckets{4, {544, 2176, 8448, 16896, 0, 0}};
+        return SegBuckets{5, {544, 2176, 8448, 16896, 33792, 0}};
+    }
+    static cudaError_t run(const msort_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t* tk, uint32_t* tv,
+                           const unsigned long long* off, size_t nseg, const unsigned int* lists,
+                           unsigned int* counters, unsigned int* status, cudaStream_t st) {
         cudaError_t e;
         MSORT_SMALL_LAUNCHES(uint32_t, false)
         if ((e = launch_small<uint32_t, false, 512, 33>(keys, vals, off, nseg, lists, counters, 3, status, st)))
             return e;
-        if ((e = launch_small<uint32_t, false, 1024, 33>(keys, vals, off, nseg, lists, counters, 4, status, st)))
+        if (buckets(ctx).n == 5 &&
+            (e = launch_small<uint32_t, false, 1024, 33>(keys, vals, off, nseg, lists, counters, 4, status, st)))
             return e;
+        if (ctx && ctx->seg_large_tile == 8448)
+            return launch_large<uint32_t, false, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, status,
+                                                          st);
         return launch_large<uint32_t, false, 512, 33>(keys, vals, tk, tv, off, nseg, lists, counters, status, st);
     }
 };
 
 template <>
 struct SegPlan<uint32_t, true> {
-    static SegBuckets buckets() { return SegBuckets{4, {544, 2176, 8448, 16896, 0, 0}}; }
-    static cudaError_t run(uint32_t* keys, uint32_t* vals, uint32_t* tk, uint32_t* tv, const unsigned long long* off,
+    static SegBuckets buckets(const msort_ctx*) { return SegBuckets{4, {544, 2176, 8448, 16896, 0, 0}}; }
+    static cudaError_t run(const msort_ctx*, uint32_t* keys, uint32_t* vals, uint32_t* tk, uint32_t* tv,
+                           const unsigned long long* off,
                            size_t nseg, const unsigned int* lists, unsigned int* counters, unsigned int* status,
                            cudaStream_t st) {
         cudaError_t e;
@@ -296,8 +306,9 @@ struct SegPlan<uint32_t, true> {
 
 template <>
 struct SegPlan<uint64_t, false> {
-    static SegBuckets buckets() { return SegBuckets{4, {544, 2176, 8448, 16896, 0, 0}}; }
-    static cudaError_t run(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv, const unsigned long long* off,
+    static SegBuckets buckets(const msort_ctx*) { return SegBuckets{4, {544, 2176, 8448, 16896, 0, 0}}; }
+    static cudaError_t run(const msort_ctx*, uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv,
+                           const unsigned long long* off,
                            size_t nseg, const unsigned int* lists, unsigned int* counters, unsigned int* status,
                            cudaStream_t st) {
         cudaError_t e;
@@ -310,8 +321,9 @@ struct SegPlan<uint64_t, false> {
 
 template <>
 struct SegPlan<uint64_t, true> {
-    static SegBuckets buckets() { return SegBuckets{3, {544, 2176, 8448, 0, 0, 0}}; }
-    static cudaError_t run(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv, const unsigned long long* off,
+    static SegBuckets buckets(const msort_ctx*) { return SegBuckets{3, {544, 2176, 8448, 0, 0, 0}}; }
+    static cudaError_t run(const msort_ctx*, uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv,
+                           const unsigned long long* off,
                            size_t nseg, const unsigned int* lists, unsigned int* counters, unsigned int* status,
                            cudaStream_t st) {
         cudaError_t e;
@@ -347,12 +359,13 @@ msort_status seg_enqueue(msort_ctx* ctx, K* keys, uint32_t* vals, const unsigned
     cudaError_t e = cudaMemsetAsync(counters, 0, 256, st);
     if (e != cudaSuccess) return cuda_fail(e, "clearing segment counters");
     prof_begin(ctx, KK_SEGMENTED, st);
-    k_seg_classify<<<(unsigned)((nseg + 255) / 256), 256, 0, st>>>(off, nseg, n, SegPlan<K, PAIRS>::buckets(), lists,
-                                                                   counters, ctx->d_status);
+    k_seg_classify<<<(unsigned)((nseg + 255) / 256), 256, 0, st>>>(off, nseg, n, SegPlan<K, PAIRS>::buckets(ctx),
+                                                                   lists, counters, ctx->d_status);
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = SegPlan<K, PAIRS>::run(keys, vals, tk, tv, off, nseg, lists, counters, ctx->d_status, st);
+    if (e == cudaSuccess)
+        e = SegPlan<K, PAIRS>::run(ctx, keys, vals, tk, tv, off, nseg, lists, counters, ctx->d_status, st);
     prof_end(ctx, KK_SEGMENTED, st);
-    ctx->launches += 1 + SegPlan<K, PAIRS>::buckets().n + 1;
+    ctx->launches += 1 + SegPlan<K, PAIRS>::buckets(ctx).n + 1;
     if (e != cudaSuccess) return cuda_fail(e, "segmented sort launch");
     return MSORT_OK;
 }
@@ -364,10 +377,10 @@ struct SegGraphKey {
     size_t nseg, n;
     int kt;
     const void* scratch;
-    cudaStream_t st;
+    int tune_small, tune_large;
     bool operator<(const SegGraphKey& o) const {
-        return std::tie(keys, vals, off, nseg, n, kt, scratch, st) <
-               std::tie(o.keys, o.vals, o.off, o.nseg, o.n, o.kt, o.scratch, o.st);
+        return std::tie(keys, vals, off, nseg, n, kt, scratch, tune_small, tune_large) <
+               std::tie(o.keys, o.vals, o.off, o.nseg, o.n, o.kt, o.scratch, o.tune_small, o.tune_large);
     }
 };
 
@@ -403,7 +416,8 @@ msort_status seg_sort(msort_ctx* ctx, K* keys, uint32_t* vals, const unsigned lo
         s = seg_enqueue<K, PAIRS>(ctx, keys, vals, off, nseg, n, st);
     } else {
         GraphCache* gc = graph_cache(ctx);
-        const SegGraphKey key{keys, vals, off, nseg, n, (int)sizeof(K) * 2 + PAIRS, ctx->scratch, st};
+        const SegGraphKey key{keys,      vals, off, nseg, n, (int)sizeof(K) * 2 + PAIRS, ctx->scratch, ctx->seg_max_small,
+                              ctx->seg_large_tile};
         auto it = gc->seg.find(key);
         if (it == gc->seg.end()) {
             cudaStream_t cap;
@@ -433,7 +447,7 @@ msort_status seg_sort(msort_ctx* ctx, K* keys, uint32_t* vals, const unsigned lo
         }
         e = cudaGraphLaunch(it->second, st);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
-        ctx->launches += 1 + SegPlan<K, PAIRS>::buckets().n + 1;
+        ctx->launches += 1 + SegPlan<K, PAIRS>::buckets(ctx).n + 1;
     }
     cudaEventRecord(ctx->scratch_done, st);
     ctx->last_stream = st;

@@ -1,0 +1,45 @@
+"""The autotuner: it records a verified choice per class, the cache file
+round-trips, and sorts after tuning stay bit-exact against the oracle."""
+import json
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_util import need_gpu, to_dev, to_host
+
+ms = pytest.importorskip("paper_2211_16479_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+def test_tune_quick_then_sort_exact(tmp_path):
+    need_gpu()
+    path = str(tmp_path / "tune.json")
+    with ms.Context(0) as c:
+        ms.msort_tune(c.handle, path, quick=True)
+        data = json.load(open(path))
+        assert {(e["key_bytes"], e["values"]) for e in data["plain"]} == {(4, 0), (4, 1), (8, 0), (8, 1)}
+        for e in data["plain"]:
+            assert e["tile"] in (4352, 8448, 8704, 16896)
+            assert all(v > 0 for v in e["ms"].values()), e   # every candidate agreed bit for bit
+        assert data["segmented_u32"]["max_small"] in (16896, 33792)
+        for n in (5, 70001, (1 << 20) + 3):
+            keys = synth.zipf_u32(n, 3)
+            d = to_dev(keys)
+            ms.msort_sort(c.handle, d)
+            assert np.array_equal(to_host(d), oracle.sort(keys)[0])
+        lens = synth.segment_lengths(500, 2)
+        off = synth.segment_offsets(lens)
+        keys = synth.uniform_u32(int(off[-1]), 4)
+        d = to_dev(keys)
+        ms.msort_segmented_sort(c.handle, d, to_dev(off))
+        ms.msort_ctx_sync(c.handle)
+        assert np.array_equal(to_host(d), oracle.segmented_sort(keys, off)[0])
+    with ms.Context(0) as c2:
+        ms.msort_tune_load(c2.handle, path)
+        keys = synth.uniform_u32(123457, 5)
+        d = to_dev(keys)
+        ms.msort_sort(c2.handle, d)
+        assert np.array_equal(to_host(d), oracle.sort(keys)[0])
