@@ -390,13 +390,20 @@ def run_pairs(args):
     same = k64[1:] == k64[:-1]
     assert bool((k64[1:] >= k64[:-1]).all()) and bool((v64[1:][same] > v64[:-1][same]).all())
     t = _events_ms(step, args.steps)
+    ms.msort_ctx_set_profiling(h, True)
+    step()
+    kern = {name: ms.msort_ctx_kernel_times(h, k)[1] for name, k in
+            (("tile_sort", ms.MSORT_KERNEL_TILE), ("partition", ms.MSORT_KERNEL_PARTITION),
+             ("merge", ms.MSORT_KERNEL_MERGE))}
+    ms.msort_ctx_set_profiling(h, False)
     T, W, P = ms.msort_plan_info(n, ms.MSORT_U64, True)
     alg = 2 * n * 12 * (1 + P)
     peak, kind = _peaks()
     line = _base_line("Gpairs/s sorted (stable, 2^27 uint64 keys + uint32 values)", n / t / 1e6, "Gpairs/s", args, t,
                       {"workload": "2^27 (uint64 key, uint32 original index) pairs, keys from 2^20 distinct values",
                        "n": n, "tile": T, "merge_block_outputs": W, "merge_passes": P},
-                      dtype="u64+u32",
+                      dtype="u64+u32", kernel_ms_per_sort=kern,
+                      merge_pass_gbs=2 * n * 12 * P / (kern["merge"] * 1e-3) / 1e9,
                       whole_sort_roofline={"algorithmic_bytes": alg,
                                            "frac_of_measured_hbm": alg / (t * 1e-3) / 1e9 / peak,
                                            "frac_of_8tbs": alg / (t * 1e-3) / 1e9 / NOMINAL_HBM_GBS})
