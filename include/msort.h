@@ -58,8 +58,9 @@ typedef struct msort_ctx msort_ctx;
 
 /* Tuning knobs; a zeroed struct (or NULL) selects the defaults. */
 typedef struct {
-    int tile;           /* keys per tile-sort block: 0 = default, else 4352 (256 x 17),
-                           8448 (256 x 33), 8704 (512 x 17) or 16896 (512 x 33); 16896 is
+    int tile;           /* keys per tile-sort block: 0 = default (or tuned), else 4352
+                           (256 x 17), 8448 (256 x 33), 8704 (512 x 17), 16896 (512 x 33)
+                           or 33792 (1024 x 33, 32-bit keys without values only); 16896 is
                            not available for 64-bit key-value sorts */
     int merge_block;    /* outputs per merge block: 0, or the value the tile implies
                            (4352 for tiles of 17 keys per thread, 8448 for 33) */

@@ -24,10 +24,17 @@ static cudaError_t prepare(F* f, size_t smem) {
                                 (int)smem);
 }
 
+static inline int tile_threads(int tile) {
+    return tile == 33792 ? 1024 : (tile == 8704 || tile == 16896) ? 512 : 256;
+}
+
 template <class K, bool PAIRS>
 size_t tile_smem_bytes(int tile) {
-    const int threads = (tile == 8704 || tile == 16896) ? 512 : 256;
-    return threads == 512 ? tile_block_smem<K, PAIRS, 512>(tile) : tile_block_smem<K, PAIRS, 256>(tile);
+    switch (tile_threads(tile)) {
+        case 1024: return tile_block_smem<K, PAIRS, 1024>(tile);
+        case 512: return tile_block_smem<K, PAIRS, 512>(tile);
+        default: return tile_block_smem<K, PAIRS, 256>(tile);
+    }
 }
 
 // ipt = outputs per thread of the merge block (W = 256 * ipt).
@@ -39,13 +46,14 @@ size_t merge_smem_bytes(int W) {
 
 template <class K, bool PAIRS>
 bool tile_supported(int tile) {
-    if (tile != 4352 && tile != 8448 && tile != 8704 && tile != 16896) return false;
+    if (tile != 4352 && tile != 8448 && tile != 8704 && tile != 16896 && tile != 33792) return false;
+    if (tile == 33792 && (PAIRS || sizeof(K) != 4)) return false;  // 32-bit keys alone
     return tile_smem_bytes<K, PAIRS>(tile) <= 227 * 1024;
 }
 
 // tile = threads * keys per thread (odd); merge blocks use 256 threads with
 // the same keys per thread, so W divides 2 * tile.
-#define MSORT_TILE_CFG(X) X(4352, 256, 17) X(8448, 256, 33) X(8704, 512, 17) X(16896, 512, 33)
+#define MSORT_TILE_CFG(X) X(4352, 256, 17) X(8448, 256, 33) X(8704, 512, 17) X(16896, 512, 33) X(33792, 1024, 33)
 
 template <class K, bool PAIRS>
 cudaError_t launch_tile(const Plan& pl, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n,

@@ -97,8 +97,9 @@ const std::string& last_launch_info() { return launch_info_ref(); }
 template <class K, bool PAIRS>
 static int default_tile() {
     // measured best on GB300 (msort_tune): 512 x 33 for 32-bit keys alone,
-    // 512 x 17 for 64-bit keys or key-value pairs
+    // 256 x 17 for 64-bit key-value pairs, 512 x 17 otherwise
     if (!PAIRS && sizeof(K) == 4) return 16896;
+    if (PAIRS && sizeof(K) == 8) return 4352;
     return 8704;
 }
 
@@ -112,7 +113,7 @@ static bool make_plan(size_t n, const msort_options* opt, Plan* pl, std::string*
         return false;
     }
     // merge blocks use 256 threads and the tile's keys per thread
-    const int ipt = (p.tile == 4352 || p.tile == 8704) ? 17 : 33;
+    const int ipt = (p.tile == 4352 || p.tile == 8704) ? 17 : 33;  // W = 256 * ipt divides 2 * tile
     p.W = 256 * ipt;
     if (opt && opt->merge_block && opt->merge_block != p.W) {
         *why = "options.merge_block must be 0 or " + std::to_string(p.W) + " for tile " + std::to_string(p.tile);

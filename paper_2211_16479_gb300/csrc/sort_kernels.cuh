@@ -227,6 +227,144 @@ __device__ __forceinline__ bool aligned16(const K* p) {
 }
 
 // ---------------------------------------------------------------------------
+// Key-value tile sort for 64-bit keys: keys and values live in separate
+// shared arrays (12 bytes per element instead of 16-byte (key, position)
+// items).  The per-thread network compares (key, original register index),
+// which makes it stable; the merge rounds keep ties in the left run, which
+// keeps them stable; so the values can ride along and no position gather is
+// needed at the end.
+// ---------------------------------------------------------------------------
+template <class K, int N, int C>
+__device__ __forceinline__ void kv_cas(K (&k)[N], uint32_t (&v)[N], int (&tag)[N]) {
+    constexpr int a = OddEvenNet<N>::net.a[C];
+    constexpr int b = OddEvenNet<N>::net.b[C];
+    const bool sw = k[b] < k[a] || (k[b] == k[a] && tag[b] < tag[a]);
+    const K ka = k[a], kb = k[b];
+    const uint32_t va = v[a], vb = v[b];
+    const int ta = tag[a], tb = tag[b];
+    k[a] = sw ? kb : ka;
+    k[b] = sw ? ka : kb;
+    v[a] = sw ? vb : va;
+    v[b] = sw ? va : vb;
+    tag[a] = sw ? tb : ta;
+    tag[b] = sw ? ta : tb;
+}
+
+template <class K, int N, int... C>
+__device__ __forceinline__ void kv_net(K (&k)[N], uint32_t (&v)[N], int (&tag)[N], std::integer_sequence<int, C...>) {
+    (kv_cas<K, N, C>(k, v, tag), ...);
+}
+
+// Keys in bitonic layout (see store_bitonic), values at the same slots.
+template <class K, int IPT>
+__device__ __forceinline__ void kv_store_bitonic(K* sk, uint32_t* sv, int t, int lg, const K (&k)[IPT],
+                                                 const uint32_t (&v)[IPT]) {
+    const int p0 = t * IPT;
+    const bool rev = (t >> lg) & 1;
+    const int run = IPT << lg;
+    const int qb = (t >> lg) * run;
+    const int start = (rev ? qb + run - 1 - (p0 - qb) : p0) + (t >> (lg + 1));
+    const int step = rev ? -1 : 1;
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        sk[start + i * step] = k[i];
+        sv[start + i * step] = v[i];
+    }
+}
+
+// The merge round of smem_merge_round on separate key and value arrays.
+// Unlike the key-only and (key, position) rounds, equal keys here carry
+// different values, so an exhausted run must not be "overrun" into its
+// partner's largest element: the run bounds decide the side once a run is
+// used up (A occupies [base, base + R), the reversed B [base + R, base + 2R)).
+template <class K, int IPT>
+__device__ __forceinline__ void kv_merge_round(const K* sk, const uint32_t* sv, int lg, int t, K (&k)[IPT],
+                                               uint32_t (&v)[IPT]) {
+    const int R = IPT << lg;
+    const int g = t >> (lg + 1);
+    const int base = g * (2 * R + 1);
+    const int diag = (t & ((2 << lg) - 1)) * IPT;
+    const int BE = base + 2 * R - 1;
+    int lo = diag > R ? diag - R : 0;
+    int hi = diag < R ? diag : R;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (!(sk[BE - (diag - 1 - mid)] < sk[base + mid]))
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    int io = base + lo, jo = BE - (diag - lo);
+    const int mid_end = base + R;  // first slot of B; A is exhausted at it, B below it
+    K av = sk[io], bv = sk[jo];
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        const bool tb = io >= mid_end || (jo >= mid_end && bv < av);
+        k[i] = tb ? bv : av;
+        v[i] = sv[tb ? jo : io];
+        io += tb ? 0 : 1;
+        jo -= tb ? 1 : 0;
+        if (i + 1 < IPT) {
+            const K nx = sk[tb ? jo : io];
+            av = tb ? av : nx;
+            bv = tb ? nx : bv;
+        }
+    }
+}
+
+template <class K, int THREADS, int IPT>
+__device__ __forceinline__ bool tile_sort_block_kv(const K* src, const uint32_t* vin, K* dst, uint32_t* vout,
+                                                   int valid, unsigned char* smem_raw) {
+    constexpr int T = THREADS * IPT;
+    constexpr int SLOTS = tile_slots(T, THREADS);
+    K* sk = reinterpret_cast<K*>(smem_raw);
+    uint32_t* sv = reinterpret_cast<uint32_t*>(smem_raw + sizeof(K) * SLOTS);
+    const int t = threadIdx.x;
+    __syncthreads();  // the previous user of this shared memory is done
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        const int p = i * THREADS + t;
+        const bool in = p < valid;
+        sk[p] = in ? src[p] : key_max<K>();
+        sv[p] = in ? vin[p] : 0u;
+    }
+    __syncthreads();
+    K k[IPT];
+    uint32_t v[IPT];
+    int tag[IPT];
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        k[i] = sk[t * IPT + i];
+        v[i] = sv[t * IPT + i];
+        tag[i] = i;
+    }
+    kv_net<K, IPT>(k, v, tag, std::make_integer_sequence<int, OddEvenNet<IPT>::net.count>{});
+    int lg = 0;
+    for (int R = IPT; R < T; R *= 2, ++lg) {
+        __syncthreads();
+        kv_store_bitonic<K, IPT>(sk, sv, t, lg, k, v);
+        __syncthreads();
+        kv_merge_round<K, IPT>(sk, sv, lg, t, k, v);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        sk[t * IPT + i] = k[i];
+        sv[t * IPT + i] = v[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        const int p = i * THREADS + t;
+        if (p < valid) {
+            dst[p] = sk[p];
+            vout[p] = sv[p];
+        }
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
 // Tile sort of one block: sorts src[0, valid) (valid <= T = THREADS * IPT)
 // into dst[0, valid); src may equal dst.  `bar` is an initialised mbarrier
 // of this block and `phase` its next parity (flipped on every bulk load).
@@ -239,6 +377,9 @@ template <class K, bool PAIRS, int THREADS, int IPT>
 __device__ __forceinline__ bool tile_sort_block(const K* src, const uint32_t* vin, K* dst, uint32_t* vout, int valid,
                                                 unsigned char* smem_raw, uint64_t* bar, uint32_t& phase,
                                                 unsigned int* status) {
+    if constexpr (PAIRS && sizeof(K) == 8) {
+        return tile_sort_block_kv<K, THREADS, IPT>(src, vin, dst, vout, valid, smem_raw);
+    }
     using TI = TileItem<K, PAIRS>;
     using Item = typename TI::T;
     constexpr int T = THREADS * IPT;
@@ -328,7 +469,9 @@ __device__ __forceinline__ bool tile_sort_block(const K* src, const uint32_t* vi
 
 template <class K, bool PAIRS, int THREADS>
 __host__ __device__ constexpr size_t tile_block_smem(int T) {
-    return sizeof(typename TileItem<K, PAIRS>::T) * (size_t)tile_slots(T, THREADS) + (PAIRS ? 4u * T : 0u);
+    return (PAIRS && sizeof(K) == 8) ? (8u + 4u) * (size_t)tile_slots(T, THREADS)
+                                     : sizeof(typename TileItem<K, PAIRS>::T) * (size_t)tile_slots(T, THREADS) +
+                                           (PAIRS ? 4u * T : 0u);
 }
 
 // Tile sort kernel: block b sorts kin[b*T, min((b+1)*T, n)) in place into

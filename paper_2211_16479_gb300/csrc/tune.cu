@@ -73,7 +73,7 @@ float time_ms(F&& fn, int reps) {
     return ms / reps;
 }
 
-const int kTiles[] = {4352, 8448, 8704, 16896};
+const int kTiles[] = {4352, 8448, 8704, 16896, 33792};
 
 }  // namespace
 }  // namespace msort
