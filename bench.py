@@ -2,16 +2,18 @@
 
 One step = one out-of-place sort of each of the five 2^28-key arrays
 (uniform, already sorted, reverse sorted, 16 distinct values, Zipf(1.1) over
-2^20 ranks), keys only: the tile sort plus ceil(log2(2^28 / T)) merge passes,
-all in the library's kernels.  value = keys sorted per second (Gkeys/s) over
+2^20 ranks), keys only: the tile sort plus R = ceil(log2(2^28 / T)) rounds of
+the merge tree, one pairwise merge pass per round (--merge-ways 4 merges two
+rounds per pass instead), all in the library's kernels.  value = keys sorted per second (Gkeys/s) over
 the timed steps, inputs resident in HBM.  Each input is 1 GiB, larger than
 the 126 MB L2, so no L2 flush is needed between steps.
 
 Printed as one JSON line on rank 0.  Also reported:
   e2e           the same sort through msort_sort_host: pinned host keys in,
                 host keys out, copies inside the timed region;
-  roofline      the merge pass (the dominant kernel) against measured HBM
-                copy bandwidth, its duration from CUDA events on its stream;
+  roofline      the merge pass (the dominant kernel; one read and one write
+                of every key per launch) against measured HBM copy
+                bandwidth, its duration from CUDA events on its stream;
   cpu_baseline  the CPU oracle (chunked merge sort with a pairwise merge tree
                 on every host core) on a bounded sample of the same inputs;
   clocks        nvidia-smi samples taken during the timed region.
@@ -61,16 +63,16 @@ def _peaks():
 
 def _kernel_source_hash():
     h = hashlib.sha256()
-    for rel in ("paper_2211_16479_gb300/csrc/sort_kernels.cuh",):
+    for rel in ("paper_2211_16479_gb300/csrc/sort_kernels.cuh", "paper_2211_16479_gb300/csrc/merge4.cuh"):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def _ncu_traffic():
+def _ncu_traffic(kernel="k_merge4_pass"):
     """dram bytes per merge-pass launch from the committed ncu summary, if it
     was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "k_merge_pass_u32_2p28.txt")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_u32_2p28.txt")
     try:
         fields = {}
         with open(path) as f:
@@ -208,8 +210,10 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     n = args.n
-    opts = {"tile": args.tile, "merge_block": args.merge_block}
+    opts = {"tile": args.tile, "merge_block": args.merge_block, "merge_ways": args.merge_ways}
     T, W, passes = ms.msort_plan_info(n, ms.MSORT_U32, False, opts)
+    ways, mem_passes = ms.msort_plan_passes(n, ms.MSORT_U32, False, opts)
+    merge_kernel = "k_merge4_pass" if ways == 4 else "k_merge_pass"
 
     inputs = [torch_gen.u32_distribution(d, n, 1, device=dev) for d in DISTS]
     out = torch.empty_like(inputs[0])
@@ -280,7 +284,7 @@ def run_ours(args):
     bytes_per_merge = 2 * n * 4
     merge_avg_s = (m_ms / max(1, m_launches)) * 1e-3
     achieved = bytes_per_merge / merge_avg_s / 1e9
-    alg_bytes_sort = 2 * n * 4 * (1 + passes)
+    alg_bytes_sort = 2 * n * 4 * (1 + mem_passes)
 
     # end to end through the host-buffer API
     e2e = None
@@ -316,14 +320,14 @@ def run_ours(args):
             "data": "synthetic (seeded SplitMix64 recipes, generated on the device)",
             "config": {"workload": "2^28 uint32 keys x 5 distributions (uniform, sorted, reverse, 16 distinct, "
                                    "Zipf 1.1 over 2^20 ranks), keys only, stable out-of-place sort",
-                       "n": n, "distributions": list(DISTS), "tile": T, "merge_passes": passes,
-                       "merge_block_outputs": W,
+                       "n": n, "distributions": list(DISTS), "tile": T, "merge_rounds": passes,
+                       "merge_ways": ways, "memory_passes": mem_passes,
                        "l2": "inputs are 1 GiB each (> 126 MB L2); no flush between steps",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_kind": peak_kind, "kernel": "k_merge_pass<u32>",
-                         "traffic": _ncu_traffic(), "algorithmic_bytes_per_launch": bytes_per_merge,
+                         "frac": achieved / peak, "peak_kind": peak_kind, "kernel": merge_kernel + "<u32>",
+                         "traffic": _ncu_traffic(merge_kernel), "algorithmic_bytes_per_launch": bytes_per_merge,
                          "launches": m_launches, "avg_ms": m_ms / max(1, m_launches)},
             "whole_sort_roofline": {"algorithmic_bytes": alg_bytes_sort,
                                     "frac_of_measured_hbm": alg_bytes_sort * len(DISTS) * args.steps /
@@ -589,6 +593,7 @@ def main():
     ap.add_argument("--n", type=int, default=N)
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--merge-block", type=int, default=0)
+    ap.add_argument("--merge-ways", type=int, default=0, help="0 = plan default, 2 = pairwise passes, 4 = four-way")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

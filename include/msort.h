@@ -73,7 +73,12 @@ typedef struct {
     int learned_passes; /* with modes 1/2: how many final passes use the guided search;
                            0 = the passes whose runs hold >= 2^22 keys */
     int use_graph;      /* 1 = replay the pass sequence from a captured CUDA graph */
-    int reserved[3];    /* must be zero */
+    int merge_ways;     /* merge rounds per pass over memory: 0 = default (2); 2 = one round
+                           of the pairwise merge tree per pass; 4 = two rounds per pass (four
+                           runs merged at once; keys-only sorts with partition_mode 0; half
+                           the HBM traffic of the merge phase but slower on GB300, where the
+                           pairwise pass runs at the copy bandwidth) */
+    int reserved[2];    /* must be zero */
 } msort_options;
 
 /* Context on CUDA device `device`.  scratch_budget_bytes caps the scratch the
@@ -97,6 +102,14 @@ size_t msort_scratch_bytes(size_t n, msort_key_type kt, int with_vals, const mso
  * block and number of merge passes (any output pointer may be NULL). */
 msort_status msort_plan_info(size_t n, msort_key_type kt, int with_vals, const msort_options* opt, int* tile,
                              int* merge_block, int* passes);
+
+/* How the plan's merge rounds map to passes over memory: *ways = 2 (one
+ * round of the merge tree per pass) or 4 (two rounds per pass, four runs
+ * merged at once), *memory_passes = the merge passes that read and write
+ * every element once (rounds for ways = 2; rounds / 2 plus one pairwise pass
+ * when rounds is odd, for ways = 4).  Either pointer may be NULL. */
+msort_status msort_plan_passes(size_t n, msort_key_type kt, int with_vals, const msort_options* opt, int* ways,
+                               int* memory_passes);
 
 /* In-place stable sort of d_keys[0:n). */
 msort_status msort_sort(msort_ctx* ctx, void* d_keys, size_t n, msort_key_type kt,

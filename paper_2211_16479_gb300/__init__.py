@@ -31,7 +31,7 @@ class MsortError(RuntimeError):
 class msort_options(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int), ("merge_block", ctypes.c_int), ("partition_mode", ctypes.c_int),
                 ("learned_passes", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("merge_ways", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 _P, _SZ, _I, _ST = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int
@@ -51,6 +51,7 @@ _SIGS = {
     "msort_ctx_sync": ([_P, _P], _ST),
     "msort_scratch_bytes": ([_SZ, _I, _I, _OPT], _SZ),
     "msort_plan_info": ([_SZ, _I, _I, _OPT, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)], _ST),
+    "msort_plan_passes": ([_SZ, _I, _I, _OPT, ctypes.POINTER(_I), ctypes.POINTER(_I)], _ST),
     "msort_sort": ([_P, _P, _SZ, _I, _OPT, _P], _ST),
     "msort_sort_pairs": ([_P, _P, _P, _SZ, _I, _OPT, _P], _ST),
     "msort_sort_copy": ([_P, _P, _P, _P, _P, _SZ, _I, _OPT, _P], _ST),
@@ -192,6 +193,15 @@ def msort_ctx_sync(ctx, stream=None) -> None:
 
 def msort_scratch_bytes(n: int, key_type: int, with_vals: bool, options=None) -> int:
     return int(load_library().msort_scratch_bytes(int(n), int(key_type), int(bool(with_vals)), _opts(options)))
+
+
+def msort_plan_passes(n: int, key_type: int, with_vals: bool, options=None):
+    """(ways, memory_passes): merge rounds per pass over memory (2 or 4) and
+    the number of merge passes over memory the plan makes."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(None, load_library().msort_plan_passes(int(n), int(key_type), int(bool(with_vals)), _opts(options),
+                                                  ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def msort_plan_info(n: int, key_type: int, with_vals: bool, options=None):

@@ -17,7 +17,7 @@ namespace msort {
 enum KernelKind { KK_TILE = 0, KK_PARTITION = 1, KK_MERGE = 2, KK_SEGMENTED = 3, KK_MLP = 4, KK_COUNT = 5 };
 
 // Status bits a kernel may raise in the context's device status word.
-enum : unsigned int { DEV_OK = 0, DEV_TIMEOUT = 1u, DEV_BAD_INPUT = 2u };
+enum : unsigned int { DEV_OK = 0, DEV_TIMEOUT = 1u, DEV_BAD_INPUT = 2u, DEV_INTERNAL = 4u };
 
 struct EventPair {
     cudaEvent_t a = nullptr, b = nullptr;
@@ -29,6 +29,9 @@ struct Plan {
     int passes;     // merge passes after the tile sort
     int partition_mode;
     int learned_passes;
+    int ways;   // 2: one merge round per pass; 4: two rounds per pass (four-way)
+    int W4;     // outputs per four-way merge block
+    int G4;     // grid step of the four-way partition
     unsigned int* status;  // device status word of the context
 };
 

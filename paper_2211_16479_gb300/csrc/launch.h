@@ -30,6 +30,19 @@ cudaError_t launch_merge(const Plan& pl, const K* src, K* dst, const uint32_t* v
 template <class K>
 cudaError_t launch_partition(const Plan& pl, const K* src, size_t n, size_t L, unsigned long long* splits,
                              cudaStream_t st);
+// Four-way pass (two merge-tree rounds): runs of L -> runs of 4L.  The grid
+// arrays hold merge4_grid_points(n, L, G) entries each; brk 6 * blocks.
+inline size_t merge4_grid_points(size_t n, size_t L, size_t G) {
+    return (n + 4 * L - 1) / (4 * L) * (4 * L / G);
+}
+template <class K>
+cudaError_t launch_merge4_partition(const Plan& pl, const K* src, size_t n, size_t L, unsigned long long* gco,
+                                    K* gval, unsigned long long* gpos, unsigned long long* brk, cudaStream_t st);
+template <class K>
+cudaError_t launch_merge4(const Plan& pl, const K* src, K* dst, size_t n, size_t L, const unsigned long long* brk,
+                          cudaStream_t st);
+template <class K>
+size_t merge4_smem_bytes(int W4);
 // Stable merge of two separate sorted arrays into out (splits: nblocks + 1).
 template <class K, bool PAIRS>
 cudaError_t launch_merge_two(const K* A, size_t na, const K* B, size_t nb, const uint32_t* va, const uint32_t* vb,

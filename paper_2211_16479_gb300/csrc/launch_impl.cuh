@@ -4,6 +4,7 @@
 #include <cstdio>
 
 #include "launch.h"
+#include "merge4.cuh"
 #include "sort_kernels.cuh"
 
 namespace msort {
@@ -102,6 +103,56 @@ cudaError_t launch_partition(const Plan& pl, const K* src, size_t n, size_t L, u
     return cudaGetLastError();
 }
 
+// Four-way merge blocks of 256 threads: 11 outputs per thread (W = 2816,
+// which divides 4 x every tile of 33 keys per thread) or 17 (W = 4352, for
+// tiles of 17 keys per thread); grid step an eighth of the block.
+#define MSORT_MERGE4_CFG(X) X(2816, 256, 11) X(4352, 256, 17)
+
+template <class K>
+size_t merge4_smem_bytes(int W4) {
+#define MSORT_M4_SMEM(WW, TH, IPT) \
+    if (W4 == WW) return merge4_smem<K, TH, IPT, 8>();
+    MSORT_MERGE4_CFG(MSORT_M4_SMEM)
+#undef MSORT_M4_SMEM
+    return 0;
+}
+
+template <class K>
+cudaError_t launch_merge4_partition(const Plan& pl, const K* src, size_t n, size_t L, unsigned long long* gco,
+                                    K* gval, unsigned long long* gpos, unsigned long long* brk, cudaStream_t st) {
+    const size_t G = (size_t)pl.G4;
+    const size_t total = merge4_grid_points(n, L, G);
+    const size_t nblocks = (n + pl.W4 - 1) / pl.W4;
+    const unsigned th = 128;
+    const unsigned gb = (unsigned)((total + th - 1) / th);
+    k_grid4<K><<<gb, th, 0, st>>>(src, n, L, G, total, gco, gval);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_pos4<K><<<gb, th, 0, st>>>(src, n, L, G, total, gco, gval, gpos);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_bracket4<K><<<(unsigned)((2 * nblocks + th - 1) / th), th, 0, st>>>(n, L, G, (size_t)pl.W4, nblocks, gpos,
+                                                                          gco, brk);
+    return cudaGetLastError();
+}
+
+template <class K>
+cudaError_t launch_merge4(const Plan& pl, const K* src, K* dst, size_t n, size_t L, const unsigned long long* brk,
+                          cudaStream_t st) {
+    const size_t nblocks = (n + pl.W4 - 1) / pl.W4;
+    cudaError_t e;
+#define MSORT_M4_CASE(WW, TH, IPT)                                             \
+    if (pl.W4 == WW) {                                                         \
+        auto f = k_merge4_pass<K, TH, IPT, 8>;                                 \
+        const size_t sm = merge4_smem<K, TH, IPT, 8>();                        \
+        if ((e = prepare(f, sm)) != cudaSuccess) return e;                     \
+        f<<<(unsigned)nblocks, TH, sm, st>>>(src, dst, n, L, brk, pl.status);      \
+        return cudaGetLastError();                                             \
+    }
+    MSORT_MERGE4_CFG(MSORT_M4_CASE)
+#undef MSORT_M4_CASE
+    return cudaErrorInvalidConfiguration;
+}
+
 // Merge blocks of 256 threads x 33 keys for 32-bit keys-only merges, 256 x 17
 // otherwise (register pressure).
 template <class K, bool PAIRS>
@@ -151,6 +202,11 @@ cudaError_t launch_merge_two(const K* A, size_t na, const K* B, size_t nb, const
                                                size_t, const unsigned long long*, cudaStream_t);                \
     template cudaError_t launch_partition<K>(const Plan&, const K*, size_t, size_t, unsigned long long*,        \
                                              cudaStream_t);                                                     \
+    template size_t merge4_smem_bytes<K>(int);                                                                  \
+    template cudaError_t launch_merge4_partition<K>(const Plan&, const K*, size_t, size_t, unsigned long long*, \
+                                                    K*, unsigned long long*, unsigned long long*, cudaStream_t); \
+    template cudaError_t launch_merge4<K>(const Plan&, const K*, K*, size_t, size_t, const unsigned long long*, \
+                                          cudaStream_t);                                                        \
     template size_t merge_two_block<K, false>();                                                                \
     template size_t merge_two_block<K, true>();                                                                 \
     template cudaError_t launch_merge_two<K, false>(const K*, size_t, const K*, size_t, const uint32_t*,         \

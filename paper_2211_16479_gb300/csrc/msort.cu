@@ -123,9 +123,37 @@ static bool make_plan(size_t n, const msort_options* opt, Plan* pl, std::string*
     for (size_t L = (size_t)p.tile; L < n; L *= 2) ++p.passes;
     p.partition_mode = opt ? opt->partition_mode : 0;
     p.learned_passes = opt ? opt->learned_passes : 0;
+    // Four-way passes (two merge rounds per pass over memory) are offered
+    // for keys-only sorts with the exact partition.  They are not the
+    // default: on GB300 the pairwise pass already runs at the copy
+    // bandwidth, and the four-way pass spends more time merging twice in
+    // shared memory and partitioning than it saves in HBM traffic.
+    const bool four_ok = !PAIRS && p.partition_mode == 0;
+    const int ways = opt && opt->merge_ways ? opt->merge_ways : 2;
+    if (ways != 2 && ways != 4) {
+        *why = "options.merge_ways must be 0, 2 or 4";
+        return false;
+    }
+    if (ways == 4 && !four_ok) {
+        *why = "options.merge_ways = 4 needs a keys-only sort with partition_mode 0";
+        return false;
+    }
+    p.ways = ways;
+    p.W4 = ipt == 33 ? 2816 : 4352;  // four-way block: 256 threads x 11 or 17 outputs
+    p.G4 = p.W4 / 8;
     p.status = nullptr;
     *pl = p;
     return true;
+}
+
+// Run length of the first four-way pass (the pairwise pass, if the pass
+// count is odd, goes first), and the largest four-way grid over the plan.
+static size_t merge4_grid_max(size_t n, const Plan& pl) {
+    size_t m = 0;
+    if (pl.ways != 4) return 0;
+    for (int p = pl.passes & 1; p + 1 < pl.passes; p += 2)
+        m = std::max(m, merge4_grid_points(n, (size_t)pl.tile << p, (size_t)pl.G4));
+    return m;
 }
 
 template <class K, bool PAIRS>
@@ -134,6 +162,12 @@ static size_t scratch_need(size_t n, const Plan& pl) {
     if (PAIRS) b += align_up(n * sizeof(uint32_t), 256);
     size_t nblocks = (n + pl.W - 1) / pl.W;
     b += align_up((nblocks + 1) * sizeof(unsigned long long), 256);
+    const size_t gm = merge4_grid_max(n, pl);
+    if (gm) {
+        const size_t nb4 = (n + pl.W4 - 1) / pl.W4;
+        b += 2 * align_up(gm * sizeof(unsigned long long), 256) + align_up(gm * sizeof(K), 256) +
+             align_up(6 * (nb4 + 1) * sizeof(unsigned long long), 256);
+    }
     return b;
 }
 
@@ -152,10 +186,24 @@ static msort_status run_sort(msort_ctx* ctx, const K* kin, const uint32_t* vin, 
         sp += align_up(n * sizeof(uint32_t), 256);
     }
     unsigned long long* splits = reinterpret_cast<unsigned long long*>(sp);
+    sp += align_up(((n + pl.W - 1) / pl.W + 1) * sizeof(unsigned long long), 256);
+    // four-way grid: co-ranks, positions, keys, block brackets
+    const size_t gm = merge4_grid_max(n, pl);
+    unsigned long long* gco = reinterpret_cast<unsigned long long*>(sp);
+    sp += align_up(gm * sizeof(unsigned long long), 256);
+    unsigned long long* gpos = reinterpret_cast<unsigned long long*>(sp);
+    sp += align_up(gm * sizeof(unsigned long long), 256);
+    K* gval = reinterpret_cast<K*>(sp);
+    sp += align_up(gm * sizeof(K), 256);
+    unsigned long long* brk = reinterpret_cast<unsigned long long*>(sp);
 
+    // Passes over memory: with four-way passes, one pairwise pass first when
+    // the number of merge rounds is odd, then one pass per two rounds.
+    const int four = gm ? pl.passes / 2 : 0;
+    const int two = pl.passes - 2 * four;
     K* bk[2] = {kout, tk};
     uint32_t* bv[2] = {vout, tv};
-    int cur = (pl.passes & 1) ? 1 : 0;
+    int cur = ((two + four) & 1) ? 1 : 0;
     cudaError_t e;
     if (log) prof_begin(ctx, KK_TILE, st);
     e = launch_tile<K, PAIRS>(pl, kin, vin, bk[cur], bv[cur], n, st);
@@ -163,7 +211,7 @@ static msort_status run_sort(msort_ctx* ctx, const K* kin, const uint32_t* vin, 
     ++ctx->launches;
     if (e != cudaSuccess) return cuda_fail(e, ("tile sort launch" + last_launch_info()).c_str());
     const int first_guided = pl.partition_mode != 0 ? learned_first_pass(pl, n) : pl.passes;
-    for (int p = 0; p < pl.passes; ++p) {
+    for (int p = 0; p < two; ++p) {
         const size_t L = (size_t)pl.tile << p;
         if (log) prof_begin(ctx, KK_PARTITION, st);
         if (p >= first_guided)
@@ -178,6 +226,20 @@ static msort_status run_sort(msort_ctx* ctx, const K* kin, const uint32_t* vin, 
         if (log) prof_end(ctx, KK_MERGE, st);
         ++ctx->launches;
         if (e != cudaSuccess) return cuda_fail(e, ("merge pass launch" + last_launch_info()).c_str());
+        cur ^= 1;
+    }
+    for (int p = two; p < pl.passes; p += 2) {
+        const size_t L = (size_t)pl.tile << p;
+        if (log) prof_begin(ctx, KK_PARTITION, st);
+        e = launch_merge4_partition<K>(pl, bk[cur], n, L, gco, gval, gpos, brk, st);
+        if (log) prof_end(ctx, KK_PARTITION, st);
+        ctx->launches += 3;
+        if (e != cudaSuccess) return cuda_fail(e, "four-way partition launch");
+        if (log) prof_begin(ctx, KK_MERGE, st);
+        e = launch_merge4<K>(pl, bk[cur], bk[cur ^ 1], n, L, brk, st);
+        if (log) prof_end(ctx, KK_MERGE, st);
+        ++ctx->launches;
+        if (e != cudaSuccess) return cuda_fail(e, ("four-way merge launch" + last_launch_info()).c_str());
         cur ^= 1;
     }
     return MSORT_OK;
@@ -319,6 +381,17 @@ msort_status plan_info_for(size_t n, const msort_options* opt, int* tile, int* W
 }
 
 template <class K, bool PAIRS>
+msort_status plan_passes_for(size_t n, const msort_options* opt, int* ways, int* memory_passes) {
+    Plan pl;
+    std::string why;
+    if (!make_plan<K, PAIRS>(n, opt, &pl, &why)) return fail(MSORT_ERR_INVALID_ARG, why);
+    const bool four = merge4_grid_max(n, pl) != 0;
+    if (ways) *ways = four ? 4 : 2;
+    if (memory_passes) *memory_passes = four ? pl.passes / 2 + (pl.passes & 1) : pl.passes;
+    return MSORT_OK;
+}
+
+template <class K, bool PAIRS>
 size_t scratch_bytes_for(size_t n, const msort_options* opt) {
     Plan pl;
     std::string why;
@@ -388,6 +461,7 @@ msort_status msort_ctx_sync(msort_ctx* ctx, void* stream) {
     if (st) {
         cudaMemset(ctx->d_status, 0, sizeof(unsigned int));
         if (st & DEV_TIMEOUT) return fail(MSORT_ERR_TIMEOUT, "a kernel gave up a bounded wait");
+        if (st & DEV_INTERNAL) return fail(MSORT_ERR_CUDA, "a four-way merge block found inconsistent geometry");
         return fail(MSORT_ERR_INVALID_ARG, "a kernel rejected its input (status " + std::to_string(st) + ")");
     }
     return MSORT_OK;
@@ -396,6 +470,17 @@ msort_status msort_ctx_sync(msort_ctx* ctx, void* stream) {
 size_t msort_scratch_bytes(size_t n, msort_key_type kt, int with_vals, const msort_options* opt) {
     if (kt == MSORT_U32) return with_vals ? scratch_bytes_for<uint32_t, true>(n, opt) : scratch_bytes_for<uint32_t, false>(n, opt);
     return with_vals ? scratch_bytes_for<uint64_t, true>(n, opt) : scratch_bytes_for<uint64_t, false>(n, opt);
+}
+
+msort_status msort_plan_passes(size_t n, msort_key_type kt, int with_vals, const msort_options* opt, int* ways,
+                               int* memory_passes) {
+    if (kt == MSORT_U32)
+        return with_vals ? plan_passes_for<uint32_t, true>(n, opt, ways, memory_passes)
+                         : plan_passes_for<uint32_t, false>(n, opt, ways, memory_passes);
+    if (kt == MSORT_U64)
+        return with_vals ? plan_passes_for<uint64_t, true>(n, opt, ways, memory_passes)
+                         : plan_passes_for<uint64_t, false>(n, opt, ways, memory_passes);
+    return fail(MSORT_ERR_INVALID_ARG, "unknown key type");
 }
 
 msort_status msort_plan_info(size_t n, msort_key_type kt, int with_vals, const msort_options* opt, int* tile,

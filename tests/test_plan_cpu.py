@@ -1,0 +1,57 @@
+"""Host-side plan logic of the plain sort (no GPU needed): tile, merge rounds,
+and how the rounds map to passes over memory (pairwise or four-way)."""
+import pytest
+
+ms = pytest.importorskip("paper_2211_16479_gb300")
+
+
+def _rounds(n, tile):
+    r, L = 0, tile
+    while L < n:
+        r, L = r + 1, 2 * L
+    return r
+
+
+@pytest.mark.parametrize("n", [1, 16896, 16897, 2 * 16896 + 1, 4 * 16896 + 1, 1 << 20, 1 << 28, (1 << 28) + 1])
+def test_pass_mapping(n):
+    T, W, rounds = ms.msort_plan_info(n, ms.MSORT_U32, False)
+    assert T == 16896 and rounds == _rounds(n, T)
+    ways, mem = ms.msort_plan_passes(n, ms.MSORT_U32, False)
+    assert ways == 2 and mem == rounds  # default: one merge round per pass
+    ways, mem = ms.msort_plan_passes(n, ms.MSORT_U32, False, {"merge_ways": 4})
+    if rounds >= 2:
+        assert ways == 4 and mem == rounds // 2 + rounds % 2
+    else:
+        assert ways == 2 and mem == rounds
+
+
+def test_pairs_and_guided_partition_stay_pairwise():
+    n = 1 << 24
+    for kt in (ms.MSORT_U32, ms.MSORT_U64):
+        ways, mem = ms.msort_plan_passes(n, kt, True)
+        assert ways == 2 and mem == ms.msort_plan_info(n, kt, True)[2]
+    ways, mem = ms.msort_plan_passes(n, ms.MSORT_U32, False, {"partition_mode": 1})
+    assert ways == 2
+    ways, mem = ms.msort_plan_passes(n, ms.MSORT_U32, False, {"merge_ways": 2})
+    assert ways == 2 and mem == ms.msort_plan_info(n, ms.MSORT_U32, False)[2]
+
+
+def test_invalid_merge_ways():
+    n = 1 << 20
+    with pytest.raises(ms.MsortError):
+        ms.msort_plan_passes(n, ms.MSORT_U32, False, {"merge_ways": 3})
+    with pytest.raises(ms.MsortError):
+        ms.msort_plan_passes(n, ms.MSORT_U32, True, {"merge_ways": 4})
+    with pytest.raises(ms.MsortError):
+        ms.msort_plan_passes(n, ms.MSORT_U64, False, {"merge_ways": 4, "partition_mode": 2})
+    assert ms.msort_scratch_bytes(n, ms.MSORT_U32, True, {"merge_ways": 4}) == 0
+
+
+@pytest.mark.parametrize("kt,ks", [(ms.MSORT_U32, 4), (ms.MSORT_U64, 8)])
+def test_four_way_scratch_is_small(kt, ks):
+    # the four-way grid adds a few bytes per G keys on top of the ping-pong buffer
+    n = 1 << 26
+    s4 = ms.msort_scratch_bytes(n, kt, False, {"merge_ways": 4})
+    s2 = ms.msort_scratch_bytes(n, kt, False)
+    assert s2 >= n * ks and s4 > s2
+    assert s4 - s2 < 0.05 * n * ks
