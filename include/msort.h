@@ -154,11 +154,35 @@ msort_status msort_merge(msort_ctx* ctx, const void* d_a, const uint32_t* d_va, 
 /* Host-buffer sort: copies h_keys_in (and h_vals_in, nullable) to the
  * device, sorts there, and copies the result to h_keys_out (and h_vals_out;
  * give both value pointers or neither).  Output may be the same buffer as
- * input.  Device buffers come from the context (its staging area grows to
- * the largest n seen).  Synchronises on `stream` before returning. */
+ * input.  Pinned host memory is fastest; pageable memory works but its
+ * copies do not overlap.  With the default exact pairwise plan the copies
+ * are pipelined with the sort: the host-to-device copy goes in chunks of
+ * about n/8 keys whose tile sorts and chunk-local merge rounds start as
+ * each chunk arrives, and the last merge round is written in slices whose
+ * device-to-host copies start as each slice is done (other options copy
+ * the whole array each way around the sort).  Device buffers come from the
+ * context: three staging slots, used by consecutive calls in turn, each
+ * growing to the largest n it served, plus the sort scratch.  Synchronises on `stream`
+ * before returning. */
 msort_status msort_sort_host(msort_ctx* ctx, const void* h_keys_in, const uint32_t* h_vals_in,
                              void* h_keys_out, uint32_t* h_vals_out, size_t n, msort_key_type kt,
                              const msort_options* opt, void* stream);
+
+/* The same, asynchronous: enqueues the copies and the sort on the
+ * context's own copy and compute streams and returns; `stream` is made to
+ * wait for the last device-to-host copy, so the result is in h_keys_out
+ * (h_vals_out) once `stream` has completed the work enqueued so far
+ * (cudaStreamSynchronize or msort_ctx_sync).  The copies do not wait for
+ * earlier work on `stream` (the call reads and writes only host memory and
+ * its own device buffers): the input must hold its final contents when the
+ * call is made, and the host buffers must stay allocated and the input
+ * unmodified until `stream` completes.  Consecutive calls take the three
+ * staging slots in turn, so one call's device-to-host copy overlaps the next
+ * calls' host-to-device copies and sorts; a fourth call waits (on the
+ * device) for the first call's slot to be copied out. */
+msort_status msort_sort_host_async(msort_ctx* ctx, const void* h_keys_in, const uint32_t* h_vals_in,
+                                   void* h_keys_out, uint32_t* h_vals_out, size_t n, msort_key_type kt,
+                                   const msort_options* opt, void* stream);
 
 /* ---- serving: continuous batching of sort requests ---------------------- */
 

@@ -56,6 +56,7 @@ _SIGS = {
     "msort_sort_pairs": ([_P, _P, _P, _SZ, _I, _OPT, _P], _ST),
     "msort_sort_copy": ([_P, _P, _P, _P, _P, _SZ, _I, _OPT, _P], _ST),
     "msort_sort_host": ([_P, _P, _P, _P, _P, _SZ, _I, _OPT, _P], _ST),
+    "msort_sort_host_async": ([_P, _P, _P, _P, _P, _SZ, _I, _OPT, _P], _ST),
     "msort_merge": ([_P, _P, _P, _SZ, _P, _P, _SZ, _P, _P, _I, _P], _ST),
     "msort_segmented_sort": ([_P, _P, _P, _P, _SZ, _SZ, _I, _OPT, _P], _ST),
     "msort_sort_noalloc": ([_P, _P, _P, _P, _SZ, _I, _P], _ST),
@@ -255,6 +256,19 @@ def msort_sort_host(ctx, keys, vals=None, out_keys=None, out_vals=None, n=None, 
     _check(ctx, load_library().msort_sort_host(ctx, _ptr(keys), _ptr(vals), _ptr(out_keys), _ptr(out_vals),
                                                _numel(keys, n), _key_type(keys, key_type), _opts(options),
                                                _stream(stream)))
+
+
+def msort_sort_host_async(ctx, keys, vals=None, out_keys=None, out_vals=None, n=None, key_type=None,
+                          options=None, stream=None) -> None:
+    """Enqueue a host-buffer sort and return; the result is in out_keys
+    (out_vals) once `stream` completes (torch stream .synchronize() or
+    msort_ctx_sync).  Keep the host buffers alive and the input unchanged
+    until then."""
+    if out_keys is None:
+        out_keys, out_vals = keys, vals
+    _check(ctx, load_library().msort_sort_host_async(ctx, _ptr(keys), _ptr(vals), _ptr(out_keys), _ptr(out_vals),
+                                                     _numel(keys, n), _key_type(keys, key_type), _opts(options),
+                                                     _stream(stream)))
 
 
 def msort_sort_noalloc(keys_in, keys_out, vals_in=None, vals_out=None, n=None, key_type=None,

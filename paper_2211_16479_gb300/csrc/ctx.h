@@ -42,8 +42,8 @@ struct msort_ctx {
     size_t budget = 0;  // 0 = unlimited
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
-    void* staging = nullptr;  // device buffers for msort_sort_host
-    size_t staging_bytes = 0;
+    void* host_pipe = nullptr;  // msort_sort_host staging slots, copy streams and events (msort.cu)
+    size_t staging_bytes = 0;   // device bytes those slots hold
     unsigned int* d_status = nullptr;
     cudaEvent_t scratch_done = nullptr;
     cudaStream_t last_stream = nullptr;

@@ -77,15 +77,17 @@ cudaError_t launch_tile(const Plan& pl, const K* kin, const uint32_t* vin, K* ko
 
 template <class K, bool PAIRS>
 cudaError_t launch_merge(const Plan& pl, const K* src, K* dst, const uint32_t* vsrc, uint32_t* vdst, size_t n,
-                         size_t L, const unsigned long long* splits, cudaStream_t st) {
+                         size_t L, const unsigned long long* splits, cudaStream_t st, size_t c0, size_t c1) {
     const size_t nblocks = (n + pl.W - 1) / pl.W;
+    if (c1 > nblocks) c1 = nblocks;
+    if (c0 >= c1) return cudaSuccess;
     const size_t sm = merge_smem_bytes<K, PAIRS>(pl.W);
     cudaError_t e;
 #define MSORT_MERGE_CASE(WW, TH, IPT)                                          \
     if (pl.W == WW) {                                                          \
         auto f = k_merge_pass<K, PAIRS, TH, IPT>;                              \
         if ((e = prepare(f, sm)) != cudaSuccess) return e;                     \
-        f<<<(unsigned)nblocks, TH, sm, st>>>(src, dst, vsrc, vdst, n, L, splits, pl.status); \
+        f<<<(unsigned)(c1 - c0), TH, sm, st>>>(src, dst, vsrc, vdst, n, L, splits, pl.status, c0); \
         return cudaGetLastError();                                             \
     }
     MSORT_MERGE_CASE(4352, 256, 17)
@@ -197,9 +199,9 @@ cudaError_t launch_merge_two(const K* A, size_t na, const K* B, size_t nb, const
     template cudaError_t launch_tile<K, true>(const Plan&, const K*, const uint32_t*, K*, uint32_t*, size_t,    \
                                               cudaStream_t);                                                    \
     template cudaError_t launch_merge<K, false>(const Plan&, const K*, K*, const uint32_t*, uint32_t*, size_t,  \
-                                                size_t, const unsigned long long*, cudaStream_t);               \
+                                                size_t, const unsigned long long*, cudaStream_t, size_t, size_t); \
     template cudaError_t launch_merge<K, true>(const Plan&, const K*, K*, const uint32_t*, uint32_t*, size_t,   \
-                                               size_t, const unsigned long long*, cudaStream_t);                \
+                                               size_t, const unsigned long long*, cudaStream_t, size_t, size_t); \
     template cudaError_t launch_partition<K>(const Plan&, const K*, size_t, size_t, unsigned long long*,        \
                                              cudaStream_t);                                                     \
     template size_t merge4_smem_bytes<K>(int);                                                                  \

@@ -399,6 +399,251 @@ size_t scratch_bytes_for(size_t n, const msort_options* opt) {
     return scratch_need<K, PAIRS>(n, pl);
 }
 
+// ---------------------------------------------------------------------------
+// Sorting host buffers.  The sort of n keys is the same plan as on device
+// buffers; what changes is where the copies go:
+//  * the host-to-device copy is issued in chunks of T * 2^m keys (about n/8)
+//    on a copy stream, and each chunk's tile sort and its chunk-local merge
+//    rounds (runs shorter than a chunk) start as soon as the chunk arrives;
+//  * the remaining log2(chunks) rounds run over the whole array; the last
+//    one is launched in slices, and each slice's device-to-host copy starts
+//    on a second copy stream as soon as the slice is written;
+//  * three staging slots serve consecutive calls in turn, and the work runs on the
+//    context's own copy and compute streams (the caller's stream only waits
+//    for the last copy), so with the asynchronous entry point one sort's
+//    device-to-host copy overlaps the next sort's host-to-device copy and
+//    sort (the link carries both directions at once).
+// The tile sort writes to whichever buffer makes the last round land in the
+// staging slot, so the shared scratch is free as soon as the compute stream
+// moves on.
+// ---------------------------------------------------------------------------
+constexpr int kHostChunks = 8;  // target chunks of the host-to-device copy
+constexpr int kHostSlices = 8;  // slices of the last merge round
+constexpr int kHostSlots = 3;   // staging slots used by consecutive calls in turn
+
+struct HostPipe {
+    cudaStream_t h2d = nullptr, cs = nullptr, d2h = nullptr;
+    void* slot[kHostSlots] = {};
+    size_t slot_bytes[kHostSlots] = {};
+    cudaEvent_t done[kHostSlots] = {};
+    cudaEvent_t in_ev[kHostSlots][kHostChunks] = {};
+    cudaEvent_t out_ev[kHostSlots][kHostSlices] = {};
+    bool used[kHostSlots] = {};
+    int next = 0;
+};
+
+static msort_status host_pipe_get(msort_ctx* ctx, HostPipe** out) {
+    if (ctx->host_pipe) {
+        *out = static_cast<HostPipe*>(ctx->host_pipe);
+        return MSORT_OK;
+    }
+    HostPipe* hp = new HostPipe();
+    cudaError_t e = cudaStreamCreateWithFlags(&hp->h2d, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hp->cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hp->d2h, cudaStreamNonBlocking);
+    for (int s = 0; s < kHostSlots && e == cudaSuccess; ++s) {
+        e = cudaEventCreateWithFlags(&hp->done[s], cudaEventDisableTiming);
+        for (int i = 0; i < kHostChunks && e == cudaSuccess; ++i)
+            e = cudaEventCreateWithFlags(&hp->in_ev[s][i], cudaEventDisableTiming);
+        for (int i = 0; i < kHostSlices && e == cudaSuccess; ++i)
+            e = cudaEventCreateWithFlags(&hp->out_ev[s][i], cudaEventDisableTiming);
+    }
+    ctx->host_pipe = hp;  // destroyed (with whatever was created) by host_pipe_destroy
+    if (e != cudaSuccess) return cuda_fail(e, "host-sort streams/events");
+    *out = hp;
+    return MSORT_OK;
+}
+
+void host_pipe_destroy(msort_ctx* ctx) {
+    HostPipe* hp = static_cast<HostPipe*>(ctx->host_pipe);
+    if (!hp) return;
+    for (int s = 0; s < kHostSlots; ++s) {
+        if (hp->slot[s]) cudaFree(hp->slot[s]);
+        if (hp->done[s]) cudaEventDestroy(hp->done[s]);
+        for (cudaEvent_t ev : hp->in_ev[s])
+            if (ev) cudaEventDestroy(ev);
+        for (cudaEvent_t ev : hp->out_ev[s])
+            if (ev) cudaEventDestroy(ev);
+    }
+    if (hp->h2d) cudaStreamDestroy(hp->h2d);
+    if (hp->cs) cudaStreamDestroy(hp->cs);
+    if (hp->d2h) cudaStreamDestroy(hp->d2h);
+    delete hp;
+    ctx->host_pipe = nullptr;
+    ctx->staging_bytes = 0;
+}
+
+template <class K, bool PAIRS>
+static msort_status host_sort(msort_ctx* ctx, const void* h_kin_v, const uint32_t* h_vin, void* h_kout_v,
+                              uint32_t* h_vout, size_t n, const msort_options* opt, cudaStream_t st) {
+    const K* h_kin = static_cast<const K*>(h_kin_v);
+    K* h_kout = static_cast<K*>(h_kout_v);
+    msort_options tuned_opt{};
+    if (!opt || !opt->tile) {
+        const int tile = tuned_tile_for(ctx, (int)sizeof(K), PAIRS, n);
+        if (tile) {
+            if (opt) tuned_opt = *opt;
+            tuned_opt.tile = tile;
+            opt = &tuned_opt;
+        }
+    }
+    Plan pl;
+    std::string why;
+    if (!make_plan<K, PAIRS>(n, opt, &pl, &why)) return fail(MSORT_ERR_INVALID_ARG, why);
+    std::lock_guard<std::mutex> g(ctx->mu);
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    pl.status = ctx->d_status;
+    HostPipe* hp = nullptr;
+    msort_status s = host_pipe_get(ctx, &hp);
+    if (s != MSORT_OK) return s;
+
+    // staging slot for this call
+    const int sl = hp->next;
+    const size_t kbytes = align_up(n * sizeof(K), 256);
+    const size_t need = kbytes + (PAIRS ? align_up(n * sizeof(uint32_t), 256) : 0);
+    if (hp->slot_bytes[sl] < need) {
+        const size_t others = ctx->staging_bytes - hp->slot_bytes[sl];
+        if (ctx->budget && need + others + ctx->scratch_bytes > ctx->budget)
+            return fail(MSORT_ERR_OOM, "host-sort staging exceeds the context budget");
+        e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+        if (hp->slot[sl]) cudaFree(hp->slot[sl]);
+        hp->slot[sl] = nullptr;
+        ctx->staging_bytes = others;
+        hp->slot_bytes[sl] = 0;
+        if (cudaMalloc(&hp->slot[sl], need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(MSORT_ERR_OOM, "cudaMalloc of host-sort staging failed");
+        }
+        hp->slot_bytes[sl] = need;
+        ctx->staging_bytes = others + need;
+    }
+    const cudaStream_t cs = hp->cs;
+    s = ensure_scratch(ctx, scratch_need<K, PAIRS>(n, pl), cs);
+    if (s != MSORT_OK) return s;
+    hp->next = (hp->next + 1) % kHostSlots;
+
+    unsigned char* sbase = static_cast<unsigned char*>(hp->slot[sl]);
+    K* S = reinterpret_cast<K*>(sbase);
+    uint32_t* SV = PAIRS ? reinterpret_cast<uint32_t*>(sbase + kbytes) : nullptr;
+    unsigned char* sp = static_cast<unsigned char*>(ctx->scratch);
+    K* Tk = reinterpret_cast<K*>(sp);
+    sp += align_up(n * sizeof(K), 256);
+    uint32_t* Tv = nullptr;
+    if (PAIRS) {
+        Tv = reinterpret_cast<uint32_t*>(sp);
+        sp += align_up(n * sizeof(uint32_t), 256);
+    }
+    unsigned long long* splits = reinterpret_cast<unsigned long long*>(sp);
+
+    // The copies and kernels run on the context's own streams (host to
+    // device, compute, device to host); `st` only waits for the last
+    // device-to-host copy, so consecutive calls overlap.  A slot's
+    // host-to-device copy waits for the last device-to-host copy out of it.
+    if (hp->used[sl]) cudaStreamWaitEvent(hp->h2d, hp->done[sl], 0);
+
+    // Pipelined schedule for the exact pairwise plan; the guided partition
+    // and four-way passes keep one whole copy each way around the sort.
+    const bool pipelined = pl.partition_mode == 0 && pl.ways == 2;
+    const int P = pl.passes;
+    int m = 0;  // chunk-local rounds: chunk = T << m, about n / kHostChunks
+    if (pipelined)
+        while (m < P && ((size_t)pl.tile << m) * kHostChunks < n) ++m;
+    const size_t chunk = pipelined && m < P ? (size_t)pl.tile << m : n;
+    const size_t nc = (n + chunk - 1) / chunk;
+    const int mloc = nc > 1 ? m : 0;
+
+    K* bk[2] = {S, Tk};
+    uint32_t* bv[2] = {SV, Tv};
+    if (!pipelined) {
+        if ((e = cudaMemcpyAsync(S, h_kin, n * sizeof(K), cudaMemcpyHostToDevice, hp->h2d)) != cudaSuccess ||
+            (PAIRS && (e = cudaMemcpyAsync(SV, h_vin, n * 4, cudaMemcpyHostToDevice, hp->h2d)) != cudaSuccess))
+            return cuda_fail(e, "host to device copy");
+        cudaEventRecord(hp->in_ev[sl][0], hp->h2d);
+        cudaStreamWaitEvent(cs, hp->in_ev[sl][0], 0);
+        if (pl.partition_mode == 1 && P > 0) {
+            s = learned_prepare<K>(ctx, pl, S, n, cs);
+            if (s != MSORT_OK) return s;
+        }
+        s = run_sort<K, PAIRS>(ctx, S, SV, S, SV, n, pl, ctx->scratch, false, cs);
+        if (s != MSORT_OK) return s;
+        cudaEventRecord(hp->out_ev[sl][0], cs);
+        cudaStreamWaitEvent(hp->d2h, hp->out_ev[sl][0], 0);
+        if ((e = cudaMemcpyAsync(h_kout, S, n * sizeof(K), cudaMemcpyDeviceToHost, hp->d2h)) != cudaSuccess ||
+            (PAIRS && (e = cudaMemcpyAsync(h_vout, SV, n * 4, cudaMemcpyDeviceToHost, hp->d2h)) != cudaSuccess))
+            return cuda_fail(e, "device to host copy");
+    } else {
+        // the tile sort writes where the last of the P rounds lands in S
+        const int cur0 = (P & 1) ? 1 : 0;
+        for (size_t i = 0; i < nc; ++i) {
+            const size_t off = i * chunk;
+            const size_t ni = n - off < chunk ? n - off : chunk;
+            if ((e = cudaMemcpyAsync(S + off, h_kin + off, ni * sizeof(K), cudaMemcpyHostToDevice, hp->h2d)) !=
+                    cudaSuccess ||
+                (PAIRS && (e = cudaMemcpyAsync(SV + off, h_vin + off, ni * 4, cudaMemcpyHostToDevice, hp->h2d)) !=
+                              cudaSuccess))
+                return cuda_fail(e, "host to device copy");
+            cudaEventRecord(hp->in_ev[sl][i], hp->h2d);
+            cudaStreamWaitEvent(cs, hp->in_ev[sl][i], 0);
+            e = launch_tile<K, PAIRS>(pl, S + off, PAIRS ? SV + off : nullptr, bk[cur0] + off,
+                                      PAIRS ? bv[cur0] + off : nullptr, ni, cs);
+            ++ctx->launches;
+            if (e != cudaSuccess) return cuda_fail(e, ("tile sort launch" + last_launch_info()).c_str());
+            int cur = cur0;
+            for (int p = 0; p < mloc; ++p) {
+                const size_t L = (size_t)pl.tile << p;
+                e = launch_partition<K>(pl, bk[cur] + off, ni, L, splits, cs);
+                if (e == cudaSuccess)
+                    e = launch_merge<K, PAIRS>(pl, bk[cur] + off, bk[cur ^ 1] + off, PAIRS ? bv[cur] + off : nullptr,
+                                               PAIRS ? bv[cur ^ 1] + off : nullptr, ni, L, splits, cs);
+                ctx->launches += 2;
+                if (e != cudaSuccess) return cuda_fail(e, ("merge pass launch" + last_launch_info()).c_str());
+                cur ^= 1;
+            }
+        }
+        int cur = cur0 ^ (mloc & 1);
+        const size_t nblocks = (n + pl.W - 1) / pl.W;
+        for (int p = mloc; p < P; ++p) {
+            const size_t L = (size_t)pl.tile << p;
+            e = launch_partition<K>(pl, bk[cur], n, L, splits, cs);
+            ++ctx->launches;
+            if (e != cudaSuccess) return cuda_fail(e, "partition launch");
+            const int slices = p + 1 == P ? kHostSlices : 1;
+            for (int j = 0; j < slices; ++j) {
+                const size_t c0 = nblocks * j / slices, c1 = nblocks * (j + 1) / slices;
+                e = launch_merge<K, PAIRS>(pl, bk[cur], bk[cur ^ 1], bv[cur], bv[cur ^ 1], n, L, splits, cs, c0, c1);
+                ++ctx->launches;
+                if (e != cudaSuccess) return cuda_fail(e, ("merge pass launch" + last_launch_info()).c_str());
+                if (p + 1 == P && c1 > c0) {
+                    const size_t o0 = c0 * pl.W, o1 = c1 * pl.W < n ? c1 * pl.W : n;
+                    cudaEventRecord(hp->out_ev[sl][j], cs);
+                    cudaStreamWaitEvent(hp->d2h, hp->out_ev[sl][j], 0);
+                    if ((e = cudaMemcpyAsync(h_kout + o0, S + o0, (o1 - o0) * sizeof(K), cudaMemcpyDeviceToHost,
+                                             hp->d2h)) != cudaSuccess ||
+                        (PAIRS && (e = cudaMemcpyAsync(h_vout + o0, SV + o0, (o1 - o0) * 4, cudaMemcpyDeviceToHost,
+                                                       hp->d2h)) != cudaSuccess))
+                        return cuda_fail(e, "device to host copy");
+                }
+            }
+            cur ^= 1;
+        }
+        if (P == mloc) {  // no global round (P == 0): the tile sort's output in S is the result
+            cudaEventRecord(hp->out_ev[sl][0], cs);
+            cudaStreamWaitEvent(hp->d2h, hp->out_ev[sl][0], 0);
+            if ((e = cudaMemcpyAsync(h_kout, S, n * sizeof(K), cudaMemcpyDeviceToHost, hp->d2h)) != cudaSuccess ||
+                (PAIRS && (e = cudaMemcpyAsync(h_vout, SV, n * 4, cudaMemcpyDeviceToHost, hp->d2h)) != cudaSuccess))
+                return cuda_fail(e, "device to host copy");
+        }
+    }
+    // st completes only after the device-to-host copies
+    cudaEventRecord(hp->done[sl], hp->d2h);
+    cudaStreamWaitEvent(st, hp->done[sl], 0);
+    hp->used[sl] = true;
+    scratch_release(ctx, cs);
+    return MSORT_OK;
+}
+
 }  // namespace msort
 
 using namespace msort;
@@ -436,7 +681,7 @@ msort_status msort_ctx_destroy(msort_ctx* ctx) {
     learned_destroy(ctx);
     graphs_destroy(ctx);
     if (ctx->scratch) cudaFree(ctx->scratch);
-    if (ctx->staging) cudaFree(ctx->staging);
+    host_pipe_destroy(ctx);
     if (ctx->d_status) cudaFree(ctx->d_status);
     for (auto& v : ctx->prof)
         for (auto& p : v) {
@@ -566,48 +811,36 @@ msort_status msort_sort_pairs(msort_ctx* ctx, void* d_keys, uint32_t* d_vals, si
     return msort_sort_copy(ctx, d_keys, d_vals, d_keys, d_vals, n, kt, opt, stream);
 }
 
-msort_status msort_sort_host(msort_ctx* ctx, const void* h_kin, const uint32_t* h_vin, void* h_kout,
-                             uint32_t* h_vout, size_t n, msort_key_type kt, const msort_options* opt, void* stream) {
+static msort_status host_sort_call(msort_ctx* ctx, const void* h_kin, const uint32_t* h_vin, void* h_kout,
+                                   uint32_t* h_vout, size_t n, msort_key_type kt, const msort_options* opt,
+                                   void* stream, bool wait) {
     msort_status s = check_common(ctx, kt, opt);
     if (s != MSORT_OK) return s;
     if (n == 0) return MSORT_OK;
     if (!h_kin || !h_kout) return fail(MSORT_ERR_INVALID_ARG, "host key pointer is NULL");
     if ((h_vin == nullptr) != (h_vout == nullptr)) return fail(MSORT_ERR_INVALID_ARG, "give both value pointers or none");
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t ks = kt == MSORT_U32 ? 4 : 8;
-    const size_t kb = align_up(n * ks, 256);
-    const size_t need = kb + (h_vin ? align_up(n * 4, 256) : 0);
-    {
-        std::lock_guard<std::mutex> g(ctx->mu);
-        cudaSetDevice(ctx->device);
-        if (need > ctx->staging_bytes) {
-            if (ctx->budget && need + ctx->scratch_bytes > ctx->budget)
-                return fail(MSORT_ERR_OOM, "host-sort staging exceeds the context budget");
-            cudaError_t e = cudaDeviceSynchronize();
-            if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
-            if (ctx->staging) cudaFree(ctx->staging);
-            ctx->staging = nullptr;
-            ctx->staging_bytes = 0;
-            if (cudaMalloc(&ctx->staging, need) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(MSORT_ERR_OOM, "cudaMalloc of host-sort staging failed");
-            }
-            ctx->staging_bytes = need;
-        }
-    }
-    unsigned char* dk = static_cast<unsigned char*>(ctx->staging);
-    uint32_t* dv = h_vin ? reinterpret_cast<uint32_t*>(dk + kb) : nullptr;
-    cudaError_t e = cudaMemcpyAsync(dk, h_kin, n * ks, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && h_vin) e = cudaMemcpyAsync(dv, h_vin, n * 4, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "host to device copy");
-    s = msort_sort_copy(ctx, dk, dv, dk, dv, n, kt, opt, stream);
-    if (s != MSORT_OK) return s;
-    e = cudaMemcpyAsync(h_kout, dk, n * ks, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && h_vin) e = cudaMemcpyAsync(h_vout, dv, n * 4, cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return cuda_fail(e, "device to host copy");
-    e = cudaStreamSynchronize(st);
+    if (kt == MSORT_U32)
+        s = h_vin ? host_sort<uint32_t, true>(ctx, h_kin, h_vin, h_kout, h_vout, n, opt, st)
+                  : host_sort<uint32_t, false>(ctx, h_kin, nullptr, h_kout, nullptr, n, opt, st);
+    else
+        s = h_vin ? host_sort<uint64_t, true>(ctx, h_kin, h_vin, h_kout, h_vout, n, opt, st)
+                  : host_sort<uint64_t, false>(ctx, h_kin, nullptr, h_kout, nullptr, n, opt, st);
+    if (s != MSORT_OK || !wait) return s;
+    cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     return MSORT_OK;
+}
+
+msort_status msort_sort_host(msort_ctx* ctx, const void* h_kin, const uint32_t* h_vin, void* h_kout,
+                             uint32_t* h_vout, size_t n, msort_key_type kt, const msort_options* opt, void* stream) {
+    return host_sort_call(ctx, h_kin, h_vin, h_kout, h_vout, n, kt, opt, stream, true);
+}
+
+msort_status msort_sort_host_async(msort_ctx* ctx, const void* h_kin, const uint32_t* h_vin, void* h_kout,
+                                   uint32_t* h_vout, size_t n, msort_key_type kt, const msort_options* opt,
+                                   void* stream) {
+    return host_sort_call(ctx, h_kin, h_vin, h_kout, h_vout, n, kt, opt, stream, false);
 }
 
 msort_status msort_ctx_set_profiling(msort_ctx* ctx, int on) {

@@ -725,12 +725,13 @@ __host__ __device__ constexpr size_t merge_block_smem() {
            (PAIRS ? 4u * merge_slots(THREADS * IPT, IPT, 4) : 0u);
 }
 
-// Merge pass kernel: block c writes dst[c*W, min((c+1)*W, pair end)).
+// Merge pass kernel: block c = c0 + blockIdx.x writes dst[c*W, min((c+1)*W,
+// pair end)) (c0 lets a pass be launched in slices).
 template <class K, bool PAIRS, int THREADS, int IPT>
 __global__ void __launch_bounds__(THREADS)
 k_merge_pass(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __restrict__ vsrc,
              uint32_t* __restrict__ vdst, size_t n, size_t L, const unsigned long long* __restrict__ splits,
-             unsigned int* status) {
+             unsigned int* status, size_t c0) {
     constexpr int W = THREADS * IPT;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
@@ -738,7 +739,7 @@ k_merge_pass(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __r
         mbar_init(&bar, 1);
         fence_mbar_init();
     }
-    const size_t c = blockIdx.x;
+    const size_t c = c0 + blockIdx.x;
     const size_t out0 = c * W;
     const PassGeom g = pass_geom(out0, n, L);
     const size_t d0 = out0 - g.pb;
