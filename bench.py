@@ -275,6 +275,8 @@ def run_ours(args):
         s1.synchronize()
         per_dist[d] = round(3 * n / (s0.elapsed_time(s1) * 1e-3) / 1e9, 3)
 
+    torch_sort = _torch_sort_gkeys(inputs[0], 3) if not args.no_torch_sort else None
+
     from paper_2211_16479_gb300 import dist as msdist
     t_max = msdist.max_over_ranks(elapsed_ms, device=dev)
     keys_total = args.steps * len(DISTS) * n * world
@@ -356,6 +358,7 @@ def run_ours(args):
             "kernel_ms_per_step": {"tile_sort": t_ms / args.steps, "partition": p_ms / args.steps,
                                    "merge": m_ms / args.steps},
             "per_distribution_gkeys": per_dist,
+            "torch_sort_stable_gkeys_uniform": torch_sort,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clocks,
@@ -389,6 +392,53 @@ def _base_line(metric, value, unit, args, ms_per_step, config, **extra):
             "config": config}
     line.update(extra)
     return line
+
+
+def _torch_sort_gkeys(a_u32, reps):
+    """torch.sort(stable=True) on the same keys, for context: the uint32 keys
+    are viewed as int32 with the sign bit flipped (same order)."""
+    import torch
+    k = a_u32.view(torch.int32) ^ torch.iinfo(torch.int32).min
+    torch.sort(k, stable=True)
+    torch.cuda.synchronize()
+    t = _events_ms(lambda: torch.sort(k, stable=True), reps)
+    return a_u32.numel() / t / 1e6
+
+
+def run_small(args):
+    """The small configuration: one stable sort of 2^20 uniform uint32 keys
+    (4 MiB, L2-resident, so launch cost dominates), replayed from a CUDA
+    graph; without the graph and torch.sort(stable=True) as context."""
+    import torch
+
+    import paper_2211_16479_gb300 as ms
+    from synth import torch_gen
+    n = 1 << 20
+    a = torch_gen.u32_distribution("uniform", n, 1, device="cuda")
+    out = torch.empty_like(a)
+    ctx = ms.Context(0)
+    h = ctx.handle
+    reps = max(args.steps, 10) * 50
+    res = {}
+    for name, o in (("graph", {"use_graph": 1}), ("launches", {})):
+        step = lambda: ms.msort_sort_copy(h, a, out, options=o)
+        for _ in range(max(args.warmup, 3)):
+            step()
+        torch.cuda.synchronize()
+        exp = torch.sort(a.to(torch.int64)).values.to(torch.uint32)
+        assert bool((out == exp).all()), "small sort mismatch"
+        res[name] = _events_ms(step, reps)
+    T, W, P = ms.msort_plan_info(n, ms.MSORT_U32, False)
+    line = _base_line("Gkeys/s sorted (stable merge sort, 2^20 uint32 keys)", n / res["graph"] / 1e6, "Gkeys/s",
+                      args, res["graph"],
+                      {"workload": "2^20 uniform uint32 keys, keys only, stable out-of-place sort, CUDA-graph replay",
+                       "n": n, "tile": T, "merge_passes": P,
+                       "l2": "4 MiB input stays in the 126 MB L2 (a launch-bound size)"},
+                      dtype="u32", us_per_sort={"graph": res["graph"] * 1e3, "launches": res["launches"] * 1e3},
+                      without_graph_gkeys=n / res["launches"] / 1e6,
+                      torch_sort_stable_gkeys=_torch_sort_gkeys(a, reps))
+    print(json.dumps(line), flush=True)
+    ctx.close()
 
 
 def run_pairs(args):
@@ -613,18 +663,21 @@ def main():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--merge-block", type=int, default=0)
     ap.add_argument("--merge-ways", type=int, default=0, help="0 = plan default, 2 = pairwise passes, 4 = four-way")
+    ap.add_argument("--no-torch-sort", action="store_true", help="skip the torch.sort(stable=True) context figure")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="sort", choices=["sort", "pairs", "segmented", "learned", "serving"])
+    ap.add_argument("--workload", default="sort",
+                    choices=["sort", "small", "pairs", "segmented", "learned", "serving"])
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         return run_reference(args)
     if args.workload != "sort":
-        fn = {"pairs": run_pairs, "segmented": run_segmented, "learned": run_learned, "serving": run_serving}
+        fn = {"small": run_small, "pairs": run_pairs, "segmented": run_segmented, "learned": run_learned,
+              "serving": run_serving}
         fn[args.workload](args)
         return 0
     return run_ours(args)

@@ -72,7 +72,10 @@ typedef struct {
                            probes are counted like modes 1 and 2) */
     int learned_passes; /* with modes 1/2: how many final passes use the guided search;
                            0 = the passes whose runs hold >= 2^22 keys */
-    int use_graph;      /* 1 = replay the pass sequence from a captured CUDA graph */
+    int use_graph;      /* 1 = replay the launch sequence from a CUDA graph captured on the first
+                           call with the same buffers, size and plan (plain sorts with
+                           partition_mode 0, and segmented sorts); removes the per-launch
+                           host cost that dominates small sorts */
     int merge_ways;     /* merge rounds per pass over memory: 0 = default (2); 2 = one round
                            of the pairwise merge tree per pass; 4 = two rounds per pass (four
                            runs merged at once; keys-only sorts with partition_mode 0; half

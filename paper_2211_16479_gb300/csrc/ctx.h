@@ -57,6 +57,8 @@ struct msort_ctx {
     void* learned = nullptr;
     // graph cache (owned by segmented.cu)
     void* graphs = nullptr;
+    // graph cache of plain sorts (owned by msort.cu)
+    void* plain_graphs = nullptr;
     // autotuned choices (msort_tune): (key bytes, values, log2 size class) -> tile
     std::map<std::tuple<int, int, int>, int> tuned_tile;
     // segmented sort of 32-bit keys: largest on-chip bucket and large-segment tile (0 = default)

@@ -245,6 +245,74 @@ static msort_status run_sort(msort_ctx* ctx, const K* kin, const uint32_t* vin, 
     return MSORT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// CUDA-graph replay of plain sorts (options.use_graph): the launch sequence
+// of a (buffers, size, plan) is captured once and replayed, which removes
+// the per-launch host cost that dominates small sorts.
+// ---------------------------------------------------------------------------
+struct PlainGraphKey {
+    const void *kin, *vin, *kout, *vout, *scratch;
+    size_t n;
+    int type, tile, W, passes, ways;
+    bool operator<(const PlainGraphKey& o) const {
+        return std::tie(kin, vin, kout, vout, scratch, n, type, tile, W, passes, ways) <
+               std::tie(o.kin, o.vin, o.kout, o.vout, o.scratch, o.n, o.type, o.tile, o.W, o.passes, o.ways);
+    }
+};
+struct PlainGraphs {
+    std::map<PlainGraphKey, std::pair<cudaGraphExec_t, unsigned long long>> exec;  // graph, launches
+};
+
+void plain_graphs_destroy(msort_ctx* ctx) {
+    PlainGraphs* pg = static_cast<PlainGraphs*>(ctx->plain_graphs);
+    if (!pg) return;
+    for (auto& kv : pg->exec) cudaGraphExecDestroy(kv.second.first);
+    delete pg;
+    ctx->plain_graphs = nullptr;
+}
+
+template <class K, bool PAIRS>
+static msort_status run_sort_graph(msort_ctx* ctx, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout,
+                                   size_t n, const Plan& pl, cudaStream_t st) {
+    if (!ctx->plain_graphs) ctx->plain_graphs = new PlainGraphs();
+    PlainGraphs* pg = static_cast<PlainGraphs*>(ctx->plain_graphs);
+    const PlainGraphKey key{kin, vin, kout, vout, ctx->scratch, n, (int)sizeof(K) * 2 + (PAIRS ? 1 : 0),
+                            pl.tile, pl.W, pl.passes, pl.ways};
+    auto it = pg->exec.find(key);
+    if (it == pg->exec.end()) {
+        cudaStream_t cap;
+        cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+        cudaGraph_t graph = nullptr;
+        msort_status s = MSORT_OK;
+        const unsigned long long before = ctx->launches;
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            s = run_sort<K, PAIRS>(ctx, kin, vin, kout, vout, n, pl, ctx->scratch, false, cap);
+            cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+            if (s == MSORT_OK && e2 != cudaSuccess) s = cuda_fail(e2, "cudaStreamEndCapture");
+        } else {
+            s = cuda_fail(e, "cudaStreamBeginCapture");
+        }
+        const unsigned long long nl = ctx->launches - before;
+        ctx->launches = before;
+        cudaStreamDestroy(cap);
+        if (s != MSORT_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        it = pg->exec.emplace(key, std::make_pair(exec, nl)).first;
+    }
+    cudaError_t e = cudaGraphLaunch(it->second.first, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    ctx->launches += it->second.second;
+    return MSORT_OK;
+}
+
 template <class K>
 size_t sort_keys_scratch(size_t n) {
     Plan pl;
@@ -350,8 +418,14 @@ static msort_status sort_entry(msort_ctx* ctx, const void* kin, const uint32_t* 
         s = learned_prepare<K>(ctx, pl, static_cast<const K*>(kin), n, st);
         if (s != MSORT_OK) return s;
     }
-    s = run_sort<K, PAIRS>(ctx, static_cast<const K*>(kin), vin, static_cast<K*>(kout), vout, n, pl, ctx->scratch,
-                           true, st);
+    // Graph replay for the exact partition (the learned one prepares its
+    // model on the host side per call); not while profiling, whose events
+    // bracket individual launches.
+    if (opt && opt->use_graph && pl.partition_mode == 0 && !ctx->profiling)
+        s = run_sort_graph<K, PAIRS>(ctx, static_cast<const K*>(kin), vin, static_cast<K*>(kout), vout, n, pl, st);
+    else
+        s = run_sort<K, PAIRS>(ctx, static_cast<const K*>(kin), vin, static_cast<K*>(kout), vout, n, pl,
+                               ctx->scratch, true, st);
     scratch_release(ctx, st);
     return s;
 }
@@ -682,6 +756,7 @@ msort_status msort_ctx_destroy(msort_ctx* ctx) {
     graphs_destroy(ctx);
     if (ctx->scratch) cudaFree(ctx->scratch);
     host_pipe_destroy(ctx);
+    plain_graphs_destroy(ctx);
     if (ctx->d_status) cudaFree(ctx->d_status);
     for (auto& v : ctx->prof)
         for (auto& p : v) {

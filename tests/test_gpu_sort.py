@@ -172,3 +172,33 @@ def test_full_size_2_28(ctx, name):
     assert multiset_hash(out) == multiset_hash(d)
     exp, _ = oracle.par_sort(keys, workers=len(os.sched_getaffinity(0)))
     assert np.array_equal(to_host(out), exp)
+
+
+@pytest.mark.parametrize("kt", ["u32", "u64"])
+@pytest.mark.parametrize("pairs", [False, True])
+def test_graph_replay(ctx, kt, pairs):
+    # options.use_graph: the first call captures the launch sequence, later
+    # calls on the same buffers replay it on new data
+    for n in (1000, 16897, (1 << 20) + 3):
+        dk = torch.empty(n, dtype=torch.uint32 if kt == "u32" else torch.uint64, device="cuda")
+        dv = torch.empty(n, dtype=torch.uint32, device="cuda") if pairs else None
+        ok = torch.empty_like(dk)
+        ov = torch.empty_like(dv) if pairs else None
+        for rep in range(3):
+            keys = (synth.uniform_u32(n, 50 + rep) % np.uint32(5000)) if kt == "u32" else \
+                synth.dup_u64(n, 50 + rep, distinct=5000)[0]
+            vals = np.arange(n, dtype=np.uint32)
+            dk.copy_(torch.from_numpy(keys))
+            if pairs:
+                dv.copy_(torch.from_numpy(vals))
+            ms.msort_sort_copy(ctx, dk, ok, dv, ov, options={"use_graph": 1})
+            ek, ev = oracle.sort(keys, vals)
+            assert np.array_equal(to_host(ok), ek), (n, rep)
+            if pairs:
+                assert np.array_equal(to_host(ov), ev), (n, rep)
+        # in place, replayed twice
+        for rep in range(2):
+            keys = synth.zipf_u32(n, 70 + rep).astype(np.uint32 if kt == "u32" else np.uint64)
+            dk.copy_(torch.from_numpy(keys))
+            ms.msort_sort(ctx, dk, options={"use_graph": 1})
+            assert np.array_equal(to_host(dk), oracle.sort(keys)[0])
