@@ -160,7 +160,7 @@ msort_status msort_merge(msort_ctx* ctx, const void* d_a, const uint32_t* d_va, 
  * input.  Pinned host memory is fastest; pageable memory works but its
  * copies do not overlap.  With the default exact pairwise plan the copies
  * are pipelined with the sort: the host-to-device copy goes in chunks of
- * about n/8 keys whose tile sorts and chunk-local merge rounds start as
+ * about n/4 keys whose tile sorts and chunk-local merge rounds start as
  * each chunk arrives, and the last merge round is written in slices whose
  * device-to-host copies start as each slice is done (other options copy
  * the whole array each way around the sort).  Device buffers come from the
@@ -179,7 +179,9 @@ msort_status msort_sort_host(msort_ctx* ctx, const void* h_keys_in, const uint32
  * earlier work on `stream` (the call reads and writes only host memory and
  * its own device buffers): the input must hold its final contents when the
  * call is made, and the host buffers must stay allocated and the input
- * unmodified until `stream` completes.  Consecutive calls take the three
+ * unmodified until `stream` completes.  Tuned for throughput: one
+ * host-to-device copy per call and the last round in two slices, since
+ * consecutive calls overlap one another.  Consecutive calls take the three
  * staging slots in turn, so one call's device-to-host copy overlaps the next
  * calls' host-to-device copies and sorts; a fourth call waits (on the
  * device) for the first call's slot to be copied out. */

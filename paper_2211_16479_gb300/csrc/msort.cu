@@ -491,8 +491,16 @@ size_t scratch_bytes_for(size_t n, const msort_options* opt) {
 // staging slot, so the shared scratch is free as soon as the compute stream
 // moves on.
 // ---------------------------------------------------------------------------
-constexpr int kHostChunks = 8;  // target chunks of the host-to-device copy
-constexpr int kHostSlices = 8;  // slices of the last merge round
+// Chunks of the host-to-device copy and slices of the last merge round.  A
+// synchronous call has nothing else to overlap with, so it splits finely;
+// back-to-back asynchronous calls overlap one another's copies anyway, and
+// every chunk repeats the latency-bound partition launches of the
+// chunk-local rounds, so they split coarsely (measured on GB300 at 2^28
+// keys: 4/4 gives the fastest single call, 1/2 the highest throughput).
+constexpr int kHostChunks = 8;  // array sizes (maximum chunks / slices)
+constexpr int kHostSlices = 8;
+constexpr int kSyncChunks = 4, kSyncSlices = 4;
+constexpr int kAsyncChunks = 1, kAsyncSlices = 2;
 constexpr int kHostSlots = 3;   // staging slots used by consecutive calls in turn
 
 struct HostPipe {
@@ -549,7 +557,8 @@ void host_pipe_destroy(msort_ctx* ctx) {
 
 template <class K, bool PAIRS>
 static msort_status host_sort(msort_ctx* ctx, const void* h_kin_v, const uint32_t* h_vin, void* h_kout_v,
-                              uint32_t* h_vout, size_t n, const msort_options* opt, cudaStream_t st) {
+                              uint32_t* h_vout, size_t n, const msort_options* opt, cudaStream_t st, int chunks,
+                              int slices) {
     const K* h_kin = static_cast<const K*>(h_kin_v);
     K* h_kout = static_cast<K*>(h_kout_v);
     msort_options tuned_opt{};
@@ -621,9 +630,9 @@ static msort_status host_sort(msort_ctx* ctx, const void* h_kin_v, const uint32_
     // and four-way passes keep one whole copy each way around the sort.
     const bool pipelined = pl.partition_mode == 0 && pl.ways == 2;
     const int P = pl.passes;
-    int m = 0;  // chunk-local rounds: chunk = T << m, about n / kHostChunks
+    int m = 0;  // chunk-local rounds: chunk = T << m, about n / chunks
     if (pipelined)
-        while (m < P && ((size_t)pl.tile << m) * kHostChunks < n) ++m;
+        while (m < P && ((size_t)pl.tile << m) * (size_t)chunks < n) ++m;
     const size_t chunk = pipelined && m < P ? (size_t)pl.tile << m : n;
     const size_t nc = (n + chunk - 1) / chunk;
     const int mloc = nc > 1 ? m : 0;
@@ -683,9 +692,9 @@ static msort_status host_sort(msort_ctx* ctx, const void* h_kin_v, const uint32_
             e = launch_partition<K>(pl, bk[cur], n, L, splits, cs);
             ++ctx->launches;
             if (e != cudaSuccess) return cuda_fail(e, "partition launch");
-            const int slices = p + 1 == P ? kHostSlices : 1;
-            for (int j = 0; j < slices; ++j) {
-                const size_t c0 = nblocks * j / slices, c1 = nblocks * (j + 1) / slices;
+            const int ns = p + 1 == P ? slices : 1;
+            for (int j = 0; j < ns; ++j) {
+                const size_t c0 = nblocks * j / ns, c1 = nblocks * (j + 1) / ns;
                 e = launch_merge<K, PAIRS>(pl, bk[cur], bk[cur ^ 1], bv[cur], bv[cur ^ 1], n, L, splits, cs, c0, c1);
                 ++ctx->launches;
                 if (e != cudaSuccess) return cuda_fail(e, ("merge pass launch" + last_launch_info()).c_str());
@@ -895,12 +904,13 @@ static msort_status host_sort_call(msort_ctx* ctx, const void* h_kin, const uint
     if (!h_kin || !h_kout) return fail(MSORT_ERR_INVALID_ARG, "host key pointer is NULL");
     if ((h_vin == nullptr) != (h_vout == nullptr)) return fail(MSORT_ERR_INVALID_ARG, "give both value pointers or none");
     cudaStream_t st = (cudaStream_t)stream;
+    const int ch = wait ? kSyncChunks : kAsyncChunks, sl = wait ? kSyncSlices : kAsyncSlices;
     if (kt == MSORT_U32)
-        s = h_vin ? host_sort<uint32_t, true>(ctx, h_kin, h_vin, h_kout, h_vout, n, opt, st)
-                  : host_sort<uint32_t, false>(ctx, h_kin, nullptr, h_kout, nullptr, n, opt, st);
+        s = h_vin ? host_sort<uint32_t, true>(ctx, h_kin, h_vin, h_kout, h_vout, n, opt, st, ch, sl)
+                  : host_sort<uint32_t, false>(ctx, h_kin, nullptr, h_kout, nullptr, n, opt, st, ch, sl);
     else
-        s = h_vin ? host_sort<uint64_t, true>(ctx, h_kin, h_vin, h_kout, h_vout, n, opt, st)
-                  : host_sort<uint64_t, false>(ctx, h_kin, nullptr, h_kout, nullptr, n, opt, st);
+        s = h_vin ? host_sort<uint64_t, true>(ctx, h_kin, h_vin, h_kout, h_vout, n, opt, st, ch, sl)
+                  : host_sort<uint64_t, false>(ctx, h_kin, nullptr, h_kout, nullptr, n, opt, st, ch, sl);
     if (s != MSORT_OK || !wait) return s;
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
