@@ -348,7 +348,7 @@ def run_ours(args):
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind, "kernel": merge_kernel + "<u32>",
-                         "traffic": _ncu_traffic(merge_kernel), "algorithmic_bytes_per_launch": bytes_per_merge,
+                         "traffic": _ncu_traffic(merge_kernel) if n == N else None, "algorithmic_bytes_per_launch": bytes_per_merge,
                          "launches": m_launches, "avg_ms": m_ms / max(1, m_launches)},
             "whole_sort_roofline": {"algorithmic_bytes": alg_bytes_sort,
                                     "frac_of_measured_hbm": alg_bytes_sort * len(DISTS) * args.steps /
@@ -551,7 +551,7 @@ def run_learned(args):
 
     import paper_2211_16479_gb300 as ms
     from synth import torch_gen
-    n = 1 << 30
+    n = 1 << args.learned_log2n
     src = torch_gen.lognormal3_u32(n, 1, device="cuda")
     out = torch.empty_like(src)
     ctx = ms.Context(0)
@@ -579,9 +579,10 @@ def run_learned(args):
         probes[name] = {"partition_ms": pt, "probes_per_search": (pr / se) if se else None}
     _, err = ms.msort_learned_model(h)
     best = times["learned_all_passes"]
-    line = _base_line("Gkeys/s sorted (2^30 uint32 lognormal mixture, learned co-rank partition)", n / best / 1e6,
+    line = _base_line(f"Gkeys/s sorted (2^{args.learned_log2n} uint32 lognormal mixture, learned co-rank partition)",
+                      n / best / 1e6,
                       "Gkeys/s", args, best,
-                      {"workload": "2^30 uint32 keys, lognormal mixture (0.5/0.3/0.2; mu 14/18/21; sigma 1/0.5/0.3)",
+                      {"workload": f"2^{args.learned_log2n} uint32 keys, lognormal mixture (0.5/0.3/0.2; mu 14/18/21; sigma 1/0.5/0.3)",
                        "n": n},
                       dtype="u32",
                       modes_ms=times, gkeys_per_s={k: n / v / 1e6 for k, v in times.items()},
@@ -665,6 +666,7 @@ def main():
     ap.add_argument("--merge-ways", type=int, default=0, help="0 = plan default, 2 = pairwise passes, 4 = four-way")
     ap.add_argument("--no-torch-sort", action="store_true", help="skip the torch.sort(stable=True) context figure")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--learned-log2n", type=int, default=30, help="size of the learned-partition workload (log2)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

@@ -110,8 +110,11 @@ __device__ __forceinline__ void block_pass_barrier() {
 
 // Large segments: tiles of THREADS x IPT keys, then merge passes with merge
 // blocks of the same size, all by one block per segment.
+// At least two blocks per SM: left unbounded the compiler took 128
+// registers, which fits only one 512-thread block per SM; the 512-thread
+// keys-only variant fits in 64 (a 12-byte spill).
 template <class K, bool PAIRS, int THREADS, int IPT>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 3 : 2)
 k_seg_large(K* keys, uint32_t* vals, K* tkeys, uint32_t* tvals, const unsigned long long* __restrict__ off,
             size_t nseg, const unsigned int* __restrict__ lists, unsigned int* counters, unsigned int* status) {
     constexpr int T = THREADS * IPT;
