@@ -17,7 +17,10 @@ Printed as one JSON line on rank 0.  Also reported:
                 time);
   roofline      the merge pass (the dominant kernel; one read and one write
                 of every key per launch) against measured HBM copy
-                bandwidth, its duration from CUDA events on its stream;
+                bandwidth, its duration from CUDA events on its stream,
+                taken in a second timed region of K steps with an event pair
+                around every launch (value comes from the first region,
+                without those events, the sorts replayed from CUDA graphs);
   cpu_baseline  the CPU oracle (chunked merge sort with a pairwise merge tree
                 on every host core) on a bounded sample of the same inputs;
   clocks        nvidia-smi samples taken during the timed region.
@@ -214,7 +217,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     n = args.n
-    opts = {"tile": args.tile, "merge_block": args.merge_block, "merge_ways": args.merge_ways}
+    opts = {"tile": args.tile, "merge_block": args.merge_block, "merge_ways": args.merge_ways,
+            "use_graph": args.graph}  # graph replay is skipped while launches are profiled
     T, W, passes = ms.msort_plan_info(n, ms.MSORT_U32, False, opts)
     ways, mem_passes = ms.msort_plan_passes(n, ms.MSORT_U32, False, opts)
     merge_kernel = "k_merge4_pass" if ways == 4 else "k_merge_pass"
@@ -244,24 +248,33 @@ def run_ours(args):
     assert bool((last[1:] >= last[:-1]).all()), "output not sorted"
     del last
 
+    def timed(profiled):
+        # K steps bracketed by a barrier and a device synchronisation, CUDA
+        # events on the launching stream
+        ms.msort_ctx_set_profiling(h, profiled)
+        launches0 = ms.msort_ctx_launch_count(h)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        barrier()
+        kt = {k: ms.msort_ctx_kernel_times(h, k) for k in
+              (ms.MSORT_KERNEL_TILE, ms.MSORT_KERNEL_PARTITION, ms.MSORT_KERNEL_MERGE)} if profiled else None
+        ms.msort_ctx_set_profiling(h, False)
+        return e0.elapsed_time(e1), ms.msort_ctx_launch_count(h) - launches0, kt
+
+    # Timed region 1 (the value): the sorts alone, replayed from CUDA graphs
+    # unless --graph 0.  Timed region 2 (the roofline): the same steps with
+    # a CUDA event pair around every launch, which adds host work between
+    # launches (the kernels themselves are unchanged).
     sampler = ClockSampler(local)
     sampler.start()
-    ms.msort_ctx_set_profiling(h, True)
-    launches0 = ms.msort_ctx_launch_count(h)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    barrier()
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    barrier()
-    elapsed_ms = e0.elapsed_time(e1)
-    launches = ms.msort_ctx_launch_count(h) - launches0
+    elapsed_ms, launches, _ = timed(False)
     clocks = sampler.stop()
-    kt = {k: ms.msort_ctx_kernel_times(h, k) for k in
-          (ms.MSORT_KERNEL_TILE, ms.MSORT_KERNEL_PARTITION, ms.MSORT_KERNEL_MERGE)}
-    ms.msort_ctx_set_profiling(h, False)
+    prof_ms, _, kt = timed(True)
 
     # per-distribution rates (single timed sort each, profiling off)
     per_dist = {}
@@ -344,6 +357,9 @@ def run_ours(args):
                        "n": n, "distributions": list(DISTS), "tile": T, "merge_rounds": passes,
                        "merge_ways": ways, "memory_passes": mem_passes,
                        "l2": "inputs are 1 GiB each (> 126 MB L2); no flush between steps",
+                       "graph_replay": bool(args.graph),
+                       "timed_regions": "value: K steps without per-launch events; roofline and "
+                                        "kernel_ms_per_step: K more steps with a CUDA event pair per launch",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -357,6 +373,7 @@ def run_ours(args):
                                     (t_max * 1e-3) / 1e9 / NOMINAL_HBM_GBS},
             "kernel_ms_per_step": {"tile_sort": t_ms / args.steps, "partition": p_ms / args.steps,
                                    "merge": m_ms / args.steps},
+            "profiled_ms_per_step": prof_ms / args.steps,
             "per_distribution_gkeys": per_dist,
             "torch_sort_stable_gkeys_uniform": torch_sort,
             "e2e": e2e,
@@ -665,6 +682,7 @@ def main():
     ap.add_argument("--merge-block", type=int, default=0)
     ap.add_argument("--merge-ways", type=int, default=0, help="0 = plan default, 2 = pairwise passes, 4 = four-way")
     ap.add_argument("--no-torch-sort", action="store_true", help="skip the torch.sort(stable=True) context figure")
+    ap.add_argument("--graph", type=int, default=1, help="1 = replay each sort from a captured CUDA graph")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--learned-log2n", type=int, default=30, help="size of the learned-partition workload (log2)")
     ap.add_argument("--no-e2e", action="store_true")
