@@ -166,6 +166,26 @@ def cpu_oracle_rate(sample_keys, seconds_target=12.0):
     return total_keys / total_t / 1e9, cores, reps
 
 
+def cpu_context_rates(sample_keys):
+    """Context for the CPU baseline on the same sample (one pass each): the
+    oracle's merge sort on one core (the paper's sequential merge sort) and
+    numpy's stable sort (a library routine; a radix sort for integers)."""
+    import numpy as np
+
+    import oracle
+    lib = oracle.load()
+    n = sum(len(a) for a in sample_keys)
+    t0 = time.perf_counter()
+    for a in sample_keys:
+        work = np.array(a, copy=True)
+        oracle.sort_inplace(work, None, workers=1, lib=lib)
+    t1 = time.perf_counter()
+    for a in sample_keys:
+        np.sort(a, kind="stable")
+    t2 = time.perf_counter()
+    return {"oracle_one_core_gkeys": n / (t1 - t0) / 1e9, "numpy_stable_sort_gkeys": n / (t2 - t1) / 1e9}
+
+
 def run_reference(args):
     rank, world, _ = _dist_env()
     if rank != 0:
@@ -344,7 +364,8 @@ def run_ours(args):
         v, cores, reps = cpu_oracle_rate(sample, seconds_target=args.cpu_seconds)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"first 2^22 keys of each of the 5 inputs, {reps} rounds, chunked oracle "
-                         f"merge sort + pairwise merge tree on {cores} threads"}
+                         f"merge sort + pairwise merge tree on {cores} threads",
+               "context": cpu_context_rates(sample)}
 
     if rank == 0:
         line = {
