@@ -479,6 +479,42 @@ def run_small(args):
     ctx.close()
 
 
+def run_float(args):
+    """2^28 float32 keys uniform in [-1, 1) (both signs): the same sort with
+    the order-preserving key transform folded into the tile sort's load and
+    the last merge round's store, timed beside 2^28 uint32 keys."""
+    import torch
+
+    import paper_2211_16479_gb300 as ms
+    from synth import torch_gen
+    n = 1 << 28
+    bits = torch_gen.uniform_u32(n, 1, device="cuda")
+    top24 = (bits.view(torch.int32) >> 8) & 0xFFFFFF  # the top 24 bits of each word
+    keys = (top24.to(torch.float32) * (2.0 ** -23) - 1.0).contiguous()
+    out = torch.empty_like(keys)
+    u_out = torch.empty_like(bits)
+    ctx = ms.Context(0)
+    h = ctx.handle
+    o = {"use_graph": args.graph}
+    res = {}
+    for name, src, dst in (("float32", keys, out), ("uint32", bits, u_out)):
+        step = lambda: ms.msort_sort_copy(h, src, dst, options=o)
+        for _ in range(args.warmup):
+            step()
+        res[name] = _events_ms(step, args.steps)
+    torch.cuda.synchronize()
+    assert bool((out[1:] >= out[:-1]).all()), "float output not sorted"
+    line = _base_line("Gkeys/s sorted (stable merge sort, 2^28 float32 keys, IEEE totalOrder)", n / res["float32"] / 1e6,
+                      "Gkeys/s", args, res["float32"],
+                      {"workload": "2^28 float32 keys uniform in [-1, 1), keys only, stable out-of-place sort",
+                       "n": n, "graph_replay": bool(args.graph)},
+                      dtype="f32 (sorted as u32 after an order-preserving transform)",
+                      uint32_same_size_gkeys=n / res["uint32"] / 1e6,
+                      float_over_uint32=res["uint32"] / res["float32"])
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_pairs(args):
     """Stable key-value sort of 2^27 pairs: uint64 keys from 2^20 distinct
     values, uint32 values = original index."""
@@ -710,14 +746,14 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="sort",
-                    choices=["sort", "small", "pairs", "segmented", "learned", "serving"])
+                    choices=["sort", "small", "float", "pairs", "segmented", "learned", "serving"])
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         return run_reference(args)
     if args.workload != "sort":
-        fn = {"small": run_small, "pairs": run_pairs, "segmented": run_segmented, "learned": run_learned,
+        fn = {"small": run_small, "float": run_float, "pairs": run_pairs, "segmented": run_segmented, "learned": run_learned,
               "serving": run_serving}
         fn[args.workload](args)
         return 0

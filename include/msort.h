@@ -52,7 +52,26 @@ typedef enum {
     MSORT_ERR_BUSY = 6
 } msort_status;
 
-typedef enum { MSORT_U32 = 0, MSORT_U64 = 1 } msort_key_type;
+/* Key types.  Unsigned keys compare as unsigned integers; signed keys as
+ * two's-complement integers; floating-point keys by the IEEE 754 totalOrder
+ * relation: -NaN < -inf < negative numbers < -0 < +0 < positive numbers <
+ * +inf < +NaN, NaNs ordered among themselves by payload (their bit pattern),
+ * so every bit pattern has one place and equal bit patterns keep their input
+ * order.  Signed and floating-point keys are accepted by msort_sort,
+ * msort_sort_pairs, msort_sort_copy, msort_sort_host(_async),
+ * msort_scratch_bytes and the plan queries, with partition_mode 0 and
+ * pairwise passes; the other entry points return MSORT_ERR_UNSUPPORTED for
+ * them.  They are sorted as unsigned keys after an order-preserving bit
+ * transform that the tile sort applies as it reads the input and the last
+ * merge round undoes as it writes the output (no extra pass over memory). */
+typedef enum {
+    MSORT_U32 = 0,
+    MSORT_U64 = 1,
+    MSORT_I32 = 2,
+    MSORT_I64 = 3,
+    MSORT_F32 = 4,
+    MSORT_F64 = 5
+} msort_key_type;
 
 typedef struct msort_ctx msort_ctx;
 

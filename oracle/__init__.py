@@ -50,7 +50,7 @@ _SZ = ctypes.c_size_t
 
 
 def _bind(lib):
-    for suf in ("u32", "u64"):
+    for suf in _SUFFIXES.values():
         f = getattr(lib, f"oracle_sort_{suf}")
         f.argtypes, f.restype = [_P, _P, _SZ], ctypes.c_int
         f = getattr(lib, f"oracle_par_sort_{suf}")
@@ -73,12 +73,17 @@ def load(mutant: int = 0, outdir: str | None = None):
         return _LIBS[key]
 
 
+# Key dtypes and the oracle's order for each: unsigned and signed integers
+# by value, floating point by IEEE 754 totalOrder on the bit patterns.
+_SUFFIXES = {np.dtype(np.uint32): "u32", np.dtype(np.uint64): "u64", np.dtype(np.int32): "i32",
+             np.dtype(np.int64): "i64", np.dtype(np.float32): "f32", np.dtype(np.float64): "f64"}
+
+
 def _suffix(keys: np.ndarray) -> str:
-    if keys.dtype == np.uint32:
-        return "u32"
-    if keys.dtype == np.uint64:
-        return "u64"
-    raise TypeError(f"oracle keys must be uint32 or uint64, got {keys.dtype}")
+    try:
+        return _SUFFIXES[keys.dtype]
+    except KeyError:
+        raise TypeError(f"oracle keys must be 32/64-bit unsigned, signed or float, got {keys.dtype}") from None
 
 
 def _ptr(a):

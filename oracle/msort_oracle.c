@@ -31,7 +31,9 @@
  *  - oracle_segmented_sort_*: oracle_sort_* applied to each segment
  *    [off[i], off[i+1]) on its own.
  *
- * Keys are compared as unsigned integers; values ride along with their key.
+ * Keys are compared as unsigned integers (u32, u64), as signed integers
+ * (i32, i64), or, for floating-point keys held as bit patterns (f32, f64),
+ * by IEEE 754 totalOrder; values ride along with their key.
  * Memory: the sorts allocate an n-element temporary (Table 1: merge sort takes
  * O(n) extra space) and return -1 if malloc fails, 0 on success.
  */
@@ -44,13 +46,13 @@
 #define ORACLE_MUTANT 0 /* tests rebuild this file with planted mistakes */
 #endif
 
-#define DEFINE_ORACLE(SUF, KT)                                                          \
+#define DEFINE_ORACLE(SUF, KT, LE)                                                      \
     /* merge(left, right): take from the left run while left <= right. */               \
     static void merge_##SUF(const KT* ak, const uint32_t* av, size_t na, const KT* bk,  \
                             const uint32_t* bv, size_t nb, KT* ok, uint32_t* ov) {     \
         size_t i = 0, j = 0, o = 0;                                                     \
         while (i < na && j < nb) {                                                      \
-            int take_left = (ORACLE_MUTANT == 1) ? (ak[i] < bk[j]) : (ak[i] <= bk[j]);  \
+            int take_left = (ORACLE_MUTANT == 1) ? !LE(bk[j], ak[i]) : LE(ak[i], bk[j]); \
             if (take_left) {                                                            \
                 ok[o] = ak[i];                                                          \
                 if (ov) ov[o] = av[i];                                                  \
@@ -112,7 +114,7 @@
         if (d > na + nb) return -1;                                                     \
         size_t i = 0, j = 0;                                                            \
         while (i + j < d) {                                                             \
-            int take_left = (j >= nb) || (i < na && a[i] <= b[j]);                      \
+            int take_left = (j >= nb) || (i < na && LE(a[i], b[j]));                    \
             if (ORACLE_MUTANT == 4 && i < na && j < nb && a[i] == b[j]) take_left = 0;  \
             if (take_left)                                                              \
                 ++i;                                                                    \
@@ -201,7 +203,30 @@
         return 0;                                                                       \
     }
 
-DEFINE_ORACLE(u32, uint32_t)
-DEFINE_ORACLE(u64, uint64_t)
+/* Key orders.  Unsigned and signed keys: the integers' own order.
+ * Floating-point keys (held as their bit patterns): the totalOrder relation
+ * of IEEE 754 (2008/2019, clause 5.10): a value with the sign bit set comes
+ * before one without (so -0 < +0 and -NaN before everything); among
+ * non-negative patterns the larger magnitude field is the larger value
+ * (+inf below +NaN, NaNs by payload); among negative ones the larger
+ * magnitude is the smaller value. */
+#define NATIVE_LE(a, b) ((a) <= (b))
+static int total_le_f32(uint32_t a, uint32_t b) {
+    const int na = (a >> 31) != 0, nb = (b >> 31) != 0;
+    if (na != nb) return na;
+    return na ? a >= b : a <= b;
+}
+static int total_le_f64(uint64_t a, uint64_t b) {
+    const int na = (a >> 63) != 0, nb = (b >> 63) != 0;
+    if (na != nb) return na;
+    return na ? a >= b : a <= b;
+}
+
+DEFINE_ORACLE(u32, uint32_t, NATIVE_LE)
+DEFINE_ORACLE(u64, uint64_t, NATIVE_LE)
+DEFINE_ORACLE(i32, int32_t, NATIVE_LE)
+DEFINE_ORACLE(i64, int64_t, NATIVE_LE)
+DEFINE_ORACLE(f32, uint32_t, total_le_f32)
+DEFINE_ORACLE(f64, uint64_t, total_le_f64)
 
 int oracle_mutant_id(void) { return ORACLE_MUTANT; }

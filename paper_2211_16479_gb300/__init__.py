@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libmsort.so")
 
 MSORT_OK, MSORT_ERR_INVALID_ARG, MSORT_ERR_UNSUPPORTED, MSORT_ERR_OOM = 0, 1, 2, 3
 MSORT_ERR_CUDA, MSORT_ERR_TIMEOUT, MSORT_ERR_BUSY = 4, 5, 6
-MSORT_U32, MSORT_U64 = 0, 1
+MSORT_U32, MSORT_U64, MSORT_I32, MSORT_I64, MSORT_F32, MSORT_F64 = 0, 1, 2, 3, 4, 5
 MSORT_KERNEL_TILE, MSORT_KERNEL_PARTITION, MSORT_KERNEL_MERGE = 0, 1, 2
 MSORT_KERNEL_SEGMENTED, MSORT_KERNEL_MLP = 3, 4
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "TIMEOUT", 6: "BUSY"}
@@ -122,15 +122,19 @@ def _ptr(x):
     raise TypeError(f"cannot take a pointer of {type(x)!r}")
 
 
+_KEY_TYPES = {"uint32": MSORT_U32, "uint64": MSORT_U64, "int32": MSORT_I32, "int64": MSORT_I64,
+              "float32": MSORT_F32, "float64": MSORT_F64}
+
+
 def _key_type(x, key_type):
+    """Key type from the dtype: unsigned, signed (two's complement order) or
+    floating point (IEEE totalOrder); key_type overrides it."""
     if key_type is not None:
         return int(key_type)
-    name = str(getattr(x, "dtype", ""))
-    if name.endswith(("uint32", "int32")):
-        return MSORT_U32
-    if name.endswith(("uint64", "int64")):
-        return MSORT_U64
-    raise TypeError(f"key dtype {name!r} is not a 32/64-bit integer; pass key_type explicitly")
+    name = str(getattr(x, "dtype", "")).replace("torch.", "")
+    if name in _KEY_TYPES:
+        return _KEY_TYPES[name]
+    raise TypeError(f"key dtype {name!r} is not a 32/64-bit integer or float; pass key_type explicitly")
 
 
 def _numel(x, n):

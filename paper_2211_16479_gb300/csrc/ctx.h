@@ -32,6 +32,7 @@ struct Plan {
     int ways;   // 2: one merge round per pass; 4: two rounds per pass (four-way)
     int W4;     // outputs per four-way merge block
     int G4;     // grid step of the four-way partition
+    int xform;  // key transform: 0 unsigned keys, 1 signed integers, 2 IEEE floating point
     unsigned int* status;  // device status word of the context
 };
 

@@ -21,14 +21,16 @@ size_t merge_smem_bytes(int W);
 template <class K, bool PAIRS>
 bool tile_supported(int tile);
 
+// xf_in / xf_out: key transform applied as the tile sort reads its input /
+// undone as it writes its output (0 = none; see xf_forward).
 template <class K, bool PAIRS>
 cudaError_t launch_tile(const Plan& pl, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n,
-                        cudaStream_t st);
+                        cudaStream_t st, int xf_in = 0, int xf_out = 0);
 // Merge pass over blocks [c0, min(c1, blocks)) (the whole pass by default).
 template <class K, bool PAIRS>
 cudaError_t launch_merge(const Plan& pl, const K* src, K* dst, const uint32_t* vsrc, uint32_t* vdst, size_t n,
                          size_t L, const unsigned long long* splits, cudaStream_t st, size_t c0 = 0,
-                         size_t c1 = ~size_t(0));
+                         size_t c1 = ~size_t(0), int xf_out = 0);
 template <class K>
 cudaError_t launch_partition(const Plan& pl, const K* src, size_t n, size_t L, unsigned long long* splits,
                              cudaStream_t st);

@@ -58,7 +58,7 @@ bool tile_supported(int tile) {
 
 template <class K, bool PAIRS>
 cudaError_t launch_tile(const Plan& pl, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n,
-                        cudaStream_t st) {
+                        cudaStream_t st, int xf_in, int xf_out) {
     const size_t nblocks = (n + pl.tile - 1) / pl.tile;
     const size_t sm = tile_smem_bytes<K, PAIRS>(pl.tile);
     if (!tile_supported<K, PAIRS>(pl.tile)) return cudaErrorInvalidConfiguration;
@@ -67,7 +67,7 @@ cudaError_t launch_tile(const Plan& pl, const K* kin, const uint32_t* vin, K* ko
     if (pl.tile == TILE) {                                                     \
         auto f = k_tile_sort<K, PAIRS, TH, IPT>;                               \
         if ((e = prepare(f, sm)) != cudaSuccess) return e;                     \
-        f<<<(unsigned)nblocks, TH, sm, st>>>(kin, vin, kout, vout, n, pl.status); \
+        f<<<(unsigned)nblocks, TH, sm, st>>>(kin, vin, kout, vout, n, pl.status, xf_in, xf_out); \
         return cudaGetLastError();                                             \
     }
     MSORT_TILE_CFG(MSORT_TILE_CASE)
@@ -77,7 +77,8 @@ cudaError_t launch_tile(const Plan& pl, const K* kin, const uint32_t* vin, K* ko
 
 template <class K, bool PAIRS>
 cudaError_t launch_merge(const Plan& pl, const K* src, K* dst, const uint32_t* vsrc, uint32_t* vdst, size_t n,
-                         size_t L, const unsigned long long* splits, cudaStream_t st, size_t c0, size_t c1) {
+                         size_t L, const unsigned long long* splits, cudaStream_t st, size_t c0, size_t c1,
+                         int xf_out) {
     const size_t nblocks = (n + pl.W - 1) / pl.W;
     if (c1 > nblocks) c1 = nblocks;
     if (c0 >= c1) return cudaSuccess;
@@ -87,7 +88,7 @@ cudaError_t launch_merge(const Plan& pl, const K* src, K* dst, const uint32_t* v
     if (pl.W == WW) {                                                          \
         auto f = k_merge_pass<K, PAIRS, TH, IPT>;                              \
         if ((e = prepare(f, sm)) != cudaSuccess) return e;                     \
-        f<<<(unsigned)(c1 - c0), TH, sm, st>>>(src, dst, vsrc, vdst, n, L, splits, pl.status, c0); \
+        f<<<(unsigned)(c1 - c0), TH, sm, st>>>(src, dst, vsrc, vdst, n, L, splits, pl.status, c0, xf_out); \
         return cudaGetLastError();                                             \
     }
     MSORT_MERGE_CASE(4352, 256, 17)
@@ -195,13 +196,15 @@ cudaError_t launch_merge_two(const K* A, size_t na, const K* B, size_t nb, const
     template bool tile_supported<K, false>(int);                                                                \
     template bool tile_supported<K, true>(int);                                                                 \
     template cudaError_t launch_tile<K, false>(const Plan&, const K*, const uint32_t*, K*, uint32_t*, size_t,   \
-                                               cudaStream_t);                                                   \
+                                               cudaStream_t, int, int);                                         \
     template cudaError_t launch_tile<K, true>(const Plan&, const K*, const uint32_t*, K*, uint32_t*, size_t,    \
-                                              cudaStream_t);                                                    \
+                                              cudaStream_t, int, int);                                          \
     template cudaError_t launch_merge<K, false>(const Plan&, const K*, K*, const uint32_t*, uint32_t*, size_t,  \
-                                                size_t, const unsigned long long*, cudaStream_t, size_t, size_t); \
+                                                size_t, const unsigned long long*, cudaStream_t, size_t, size_t, \
+                                                int);                                                           \
     template cudaError_t launch_merge<K, true>(const Plan&, const K*, K*, const uint32_t*, uint32_t*, size_t,   \
-                                               size_t, const unsigned long long*, cudaStream_t, size_t, size_t); \
+                                               size_t, const unsigned long long*, cudaStream_t, size_t, size_t, \
+                                               int);                                                            \
     template cudaError_t launch_partition<K>(const Plan&, const K*, size_t, size_t, unsigned long long*,        \
                                              cudaStream_t);                                                     \
     template size_t merge4_smem_bytes<K>(int);                                                                  \

@@ -94,6 +94,19 @@ std::string& launch_info_ref() {
 }
 const std::string& last_launch_info() { return launch_info_ref(); }
 
+// Key types: element size and the order-preserving transform that maps them
+// to unsigned keys (0 unsigned, 1 signed integers, 2 IEEE floating point).
+static int key_bytes(msort_key_type kt) {
+    switch (kt) {
+        case MSORT_U32: case MSORT_I32: case MSORT_F32: return 4;
+        case MSORT_U64: case MSORT_I64: case MSORT_F64: return 8;
+        default: return 0;
+    }
+}
+static int key_xform(msort_key_type kt) {
+    return (kt == MSORT_I32 || kt == MSORT_I64) ? 1 : (kt == MSORT_F32 || kt == MSORT_F64) ? 2 : 0;
+}
+
 template <class K, bool PAIRS>
 static int default_tile() {
     // measured best on GB300 (msort_tune): 512 x 33 for 32-bit keys alone,
@@ -104,7 +117,7 @@ static int default_tile() {
 }
 
 template <class K, bool PAIRS>
-static bool make_plan(size_t n, const msort_options* opt, Plan* pl, std::string* why) {
+static bool make_plan(size_t n, const msort_options* opt, Plan* pl, std::string* why, int xform = 0) {
     Plan p{};
     p.tile = opt && opt->tile ? opt->tile : default_tile<K, PAIRS>();
     if (!tile_supported<K, PAIRS>(p.tile)) {
@@ -139,6 +152,11 @@ static bool make_plan(size_t n, const msort_options* opt, Plan* pl, std::string*
         return false;
     }
     p.ways = ways;
+    p.xform = xform;
+    if (xform && (p.partition_mode != 0 || ways != 2)) {
+        *why = "signed and floating-point keys need partition_mode 0 and pairwise merge passes";
+        return false;
+    }
     p.W4 = ipt == 33 ? 2816 : 4352;  // four-way block: 256 threads x 11 or 17 outputs
     p.G4 = p.W4 / 8;
     p.status = nullptr;
@@ -206,7 +224,7 @@ static msort_status run_sort(msort_ctx* ctx, const K* kin, const uint32_t* vin, 
     int cur = ((two + four) & 1) ? 1 : 0;
     cudaError_t e;
     if (log) prof_begin(ctx, KK_TILE, st);
-    e = launch_tile<K, PAIRS>(pl, kin, vin, bk[cur], bv[cur], n, st);
+    e = launch_tile<K, PAIRS>(pl, kin, vin, bk[cur], bv[cur], n, st, pl.xform, pl.passes == 0 ? pl.xform : 0);
     if (log) prof_end(ctx, KK_TILE, st);
     ++ctx->launches;
     if (e != cudaSuccess) return cuda_fail(e, ("tile sort launch" + last_launch_info()).c_str());
@@ -222,7 +240,9 @@ static msort_status run_sort(msort_ctx* ctx, const K* kin, const uint32_t* vin, 
         ++ctx->launches;
         if (e != cudaSuccess) return cuda_fail(e, "partition launch");
         if (log) prof_begin(ctx, KK_MERGE, st);
-        e = launch_merge<K, PAIRS>(pl, bk[cur], bk[cur ^ 1], bv[cur], bv[cur ^ 1], n, L, splits, st);
+        const int xf_out = (p + 1 == pl.passes) ? pl.xform : 0;  // the last round writes the caller's keys
+        e = launch_merge<K, PAIRS>(pl, bk[cur], bk[cur ^ 1], bv[cur], bv[cur ^ 1], n, L, splits, st, 0, ~size_t(0),
+                                   xf_out);
         if (log) prof_end(ctx, KK_MERGE, st);
         ++ctx->launches;
         if (e != cudaSuccess) return cuda_fail(e, ("merge pass launch" + last_launch_info()).c_str());
@@ -253,10 +273,11 @@ static msort_status run_sort(msort_ctx* ctx, const K* kin, const uint32_t* vin, 
 struct PlainGraphKey {
     const void *kin, *vin, *kout, *vout, *scratch;
     size_t n;
-    int type, tile, W, passes, ways;
+    int type, tile, W, passes, ways, xform;
     bool operator<(const PlainGraphKey& o) const {
-        return std::tie(kin, vin, kout, vout, scratch, n, type, tile, W, passes, ways) <
-               std::tie(o.kin, o.vin, o.kout, o.vout, o.scratch, o.n, o.type, o.tile, o.W, o.passes, o.ways);
+        return std::tie(kin, vin, kout, vout, scratch, n, type, tile, W, passes, ways, xform) <
+               std::tie(o.kin, o.vin, o.kout, o.vout, o.scratch, o.n, o.type, o.tile, o.W, o.passes, o.ways,
+                        o.xform);
     }
 };
 struct PlainGraphs {
@@ -276,8 +297,8 @@ static msort_status run_sort_graph(msort_ctx* ctx, const K* kin, const uint32_t*
                                    size_t n, const Plan& pl, cudaStream_t st) {
     if (!ctx->plain_graphs) ctx->plain_graphs = new PlainGraphs();
     PlainGraphs* pg = static_cast<PlainGraphs*>(ctx->plain_graphs);
-    const PlainGraphKey key{kin, vin, kout, vout, ctx->scratch, n, (int)sizeof(K) * 2 + (PAIRS ? 1 : 0),
-                            pl.tile, pl.W, pl.passes, pl.ways};
+    const PlainGraphKey key{kin,    vin,  kout,      vout,    ctx->scratch, n, (int)sizeof(K) * 2 + (PAIRS ? 1 : 0),
+                            pl.tile, pl.W, pl.passes, pl.ways, pl.xform};
     auto it = pg->exec.find(key);
     if (it == pg->exec.end()) {
         cudaStream_t cap;
@@ -394,7 +415,7 @@ static int tuned_tile_for(const msort_ctx* ctx, int key_bytes, bool pairs, size_
 
 template <class K, bool PAIRS>
 static msort_status sort_entry(msort_ctx* ctx, const void* kin, const uint32_t* vin, void* kout, uint32_t* vout,
-                               size_t n, const msort_options* opt, cudaStream_t st) {
+                               size_t n, const msort_options* opt, cudaStream_t st, int xform) {
     msort_options tuned_opt{};
     if (!opt || !opt->tile) {
         const int tile = tuned_tile_for(ctx, (int)sizeof(K), PAIRS, n);
@@ -406,7 +427,7 @@ static msort_status sort_entry(msort_ctx* ctx, const void* kin, const uint32_t* 
     }
     Plan pl;
     std::string why;
-    if (!make_plan<K, PAIRS>(n, opt, &pl, &why)) return fail(MSORT_ERR_INVALID_ARG, why);
+    if (!make_plan<K, PAIRS>(n, opt, &pl, &why, xform)) return fail(MSORT_ERR_INVALID_ARG, why);
     if (n == 0) return MSORT_OK;
     std::lock_guard<std::mutex> g(ctx->mu);
     cudaError_t e = cudaSetDevice(ctx->device);
@@ -432,7 +453,7 @@ static msort_status sort_entry(msort_ctx* ctx, const void* kin, const uint32_t* 
 
 static msort_status check_common(msort_ctx* ctx, msort_key_type kt, const msort_options* opt) {
     if (!ctx) return fail(MSORT_ERR_INVALID_ARG, "ctx is NULL");
-    if (kt != MSORT_U32 && kt != MSORT_U64) return fail(MSORT_ERR_INVALID_ARG, "unknown key type");
+    if (!key_bytes(kt)) return fail(MSORT_ERR_INVALID_ARG, "unknown key type");
     if (opt) {
         for (int r : opt->reserved)
             if (r) return fail(MSORT_ERR_INVALID_ARG, "options.reserved must be zero");
@@ -444,10 +465,10 @@ static msort_status check_common(msort_ctx* ctx, msort_key_type kt, const msort_
 }
 
 template <class K, bool PAIRS>
-msort_status plan_info_for(size_t n, const msort_options* opt, int* tile, int* W, int* passes) {
+msort_status plan_info_for(size_t n, const msort_options* opt, int* tile, int* W, int* passes, int xform) {
     Plan pl;
     std::string why;
-    if (!make_plan<K, PAIRS>(n, opt, &pl, &why)) return fail(MSORT_ERR_INVALID_ARG, why);
+    if (!make_plan<K, PAIRS>(n, opt, &pl, &why, xform)) return fail(MSORT_ERR_INVALID_ARG, why);
     if (tile) *tile = pl.tile;
     if (W) *W = pl.W;
     if (passes) *passes = pl.passes;
@@ -455,10 +476,10 @@ msort_status plan_info_for(size_t n, const msort_options* opt, int* tile, int* W
 }
 
 template <class K, bool PAIRS>
-msort_status plan_passes_for(size_t n, const msort_options* opt, int* ways, int* memory_passes) {
+msort_status plan_passes_for(size_t n, const msort_options* opt, int* ways, int* memory_passes, int xform) {
     Plan pl;
     std::string why;
-    if (!make_plan<K, PAIRS>(n, opt, &pl, &why)) return fail(MSORT_ERR_INVALID_ARG, why);
+    if (!make_plan<K, PAIRS>(n, opt, &pl, &why, xform)) return fail(MSORT_ERR_INVALID_ARG, why);
     const bool four = merge4_grid_max(n, pl) != 0;
     if (ways) *ways = four ? 4 : 2;
     if (memory_passes) *memory_passes = four ? pl.passes / 2 + (pl.passes & 1) : pl.passes;
@@ -466,10 +487,10 @@ msort_status plan_passes_for(size_t n, const msort_options* opt, int* ways, int*
 }
 
 template <class K, bool PAIRS>
-size_t scratch_bytes_for(size_t n, const msort_options* opt) {
+size_t scratch_bytes_for(size_t n, const msort_options* opt, int xform) {
     Plan pl;
     std::string why;
-    if (!make_plan<K, PAIRS>(n, opt, &pl, &why)) return 0;
+    if (!make_plan<K, PAIRS>(n, opt, &pl, &why, xform)) return 0;
     return scratch_need<K, PAIRS>(n, pl);
 }
 
@@ -558,7 +579,7 @@ void host_pipe_destroy(msort_ctx* ctx) {
 template <class K, bool PAIRS>
 static msort_status host_sort(msort_ctx* ctx, const void* h_kin_v, const uint32_t* h_vin, void* h_kout_v,
                               uint32_t* h_vout, size_t n, const msort_options* opt, cudaStream_t st, int chunks,
-                              int slices) {
+                              int slices, int xform) {
     const K* h_kin = static_cast<const K*>(h_kin_v);
     K* h_kout = static_cast<K*>(h_kout_v);
     msort_options tuned_opt{};
@@ -572,7 +593,7 @@ static msort_status host_sort(msort_ctx* ctx, const void* h_kin_v, const uint32_
     }
     Plan pl;
     std::string why;
-    if (!make_plan<K, PAIRS>(n, opt, &pl, &why)) return fail(MSORT_ERR_INVALID_ARG, why);
+    if (!make_plan<K, PAIRS>(n, opt, &pl, &why, xform)) return fail(MSORT_ERR_INVALID_ARG, why);
     std::lock_guard<std::mutex> g(ctx->mu);
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
@@ -670,7 +691,7 @@ static msort_status host_sort(msort_ctx* ctx, const void* h_kin_v, const uint32_
             cudaEventRecord(hp->in_ev[sl][i], hp->h2d);
             cudaStreamWaitEvent(cs, hp->in_ev[sl][i], 0);
             e = launch_tile<K, PAIRS>(pl, S + off, PAIRS ? SV + off : nullptr, bk[cur0] + off,
-                                      PAIRS ? bv[cur0] + off : nullptr, ni, cs);
+                                      PAIRS ? bv[cur0] + off : nullptr, ni, cs, pl.xform, P == 0 ? pl.xform : 0);
             ++ctx->launches;
             if (e != cudaSuccess) return cuda_fail(e, ("tile sort launch" + last_launch_info()).c_str());
             int cur = cur0;
@@ -695,7 +716,8 @@ static msort_status host_sort(msort_ctx* ctx, const void* h_kin_v, const uint32_
             const int ns = p + 1 == P ? slices : 1;
             for (int j = 0; j < ns; ++j) {
                 const size_t c0 = nblocks * j / ns, c1 = nblocks * (j + 1) / ns;
-                e = launch_merge<K, PAIRS>(pl, bk[cur], bk[cur ^ 1], bv[cur], bv[cur ^ 1], n, L, splits, cs, c0, c1);
+                e = launch_merge<K, PAIRS>(pl, bk[cur], bk[cur ^ 1], bv[cur], bv[cur ^ 1], n, L, splits, cs, c0, c1,
+                                           p + 1 == P ? pl.xform : 0);
                 ++ctx->launches;
                 if (e != cudaSuccess) return cuda_fail(e, ("merge pass launch" + last_launch_info()).c_str());
                 if (p + 1 == P && c1 > c0) {
@@ -797,29 +819,35 @@ msort_status msort_ctx_sync(msort_ctx* ctx, void* stream) {
 }
 
 size_t msort_scratch_bytes(size_t n, msort_key_type kt, int with_vals, const msort_options* opt) {
-    if (kt == MSORT_U32) return with_vals ? scratch_bytes_for<uint32_t, true>(n, opt) : scratch_bytes_for<uint32_t, false>(n, opt);
-    return with_vals ? scratch_bytes_for<uint64_t, true>(n, opt) : scratch_bytes_for<uint64_t, false>(n, opt);
+    const int kb = key_bytes(kt), xf = key_xform(kt);
+    if (kb == 4)
+        return with_vals ? scratch_bytes_for<uint32_t, true>(n, opt, xf) : scratch_bytes_for<uint32_t, false>(n, opt, xf);
+    if (kb == 8)
+        return with_vals ? scratch_bytes_for<uint64_t, true>(n, opt, xf) : scratch_bytes_for<uint64_t, false>(n, opt, xf);
+    return 0;
 }
 
 msort_status msort_plan_passes(size_t n, msort_key_type kt, int with_vals, const msort_options* opt, int* ways,
                                int* memory_passes) {
-    if (kt == MSORT_U32)
-        return with_vals ? plan_passes_for<uint32_t, true>(n, opt, ways, memory_passes)
-                         : plan_passes_for<uint32_t, false>(n, opt, ways, memory_passes);
-    if (kt == MSORT_U64)
-        return with_vals ? plan_passes_for<uint64_t, true>(n, opt, ways, memory_passes)
-                         : plan_passes_for<uint64_t, false>(n, opt, ways, memory_passes);
+    const int kb = key_bytes(kt), xf = key_xform(kt);
+    if (kb == 4)
+        return with_vals ? plan_passes_for<uint32_t, true>(n, opt, ways, memory_passes, xf)
+                         : plan_passes_for<uint32_t, false>(n, opt, ways, memory_passes, xf);
+    if (kb == 8)
+        return with_vals ? plan_passes_for<uint64_t, true>(n, opt, ways, memory_passes, xf)
+                         : plan_passes_for<uint64_t, false>(n, opt, ways, memory_passes, xf);
     return fail(MSORT_ERR_INVALID_ARG, "unknown key type");
 }
 
 msort_status msort_plan_info(size_t n, msort_key_type kt, int with_vals, const msort_options* opt, int* tile,
                              int* merge_block, int* passes) {
-    if (kt == MSORT_U32)
-        return with_vals ? plan_info_for<uint32_t, true>(n, opt, tile, merge_block, passes)
-                         : plan_info_for<uint32_t, false>(n, opt, tile, merge_block, passes);
-    if (kt == MSORT_U64)
-        return with_vals ? plan_info_for<uint64_t, true>(n, opt, tile, merge_block, passes)
-                         : plan_info_for<uint64_t, false>(n, opt, tile, merge_block, passes);
+    const int kb = key_bytes(kt), xf = key_xform(kt);
+    if (kb == 4)
+        return with_vals ? plan_info_for<uint32_t, true>(n, opt, tile, merge_block, passes, xf)
+                         : plan_info_for<uint32_t, false>(n, opt, tile, merge_block, passes, xf);
+    if (kb == 8)
+        return with_vals ? plan_info_for<uint64_t, true>(n, opt, tile, merge_block, passes, xf)
+                         : plan_info_for<uint64_t, false>(n, opt, tile, merge_block, passes, xf);
     return fail(MSORT_ERR_INVALID_ARG, "unknown key type");
 }
 
@@ -830,16 +858,17 @@ msort_status msort_sort_copy(msort_ctx* ctx, const void* kin, const uint32_t* vi
     if (n == 0) return MSORT_OK;
     if (!kin || !kout) return fail(MSORT_ERR_INVALID_ARG, "key pointer is NULL");
     if ((vin == nullptr) != (vout == nullptr)) return fail(MSORT_ERR_INVALID_ARG, "give both value pointers or none");
-    const size_t ks = kt == MSORT_U32 ? 4 : 8;
+    const size_t ks = (size_t)key_bytes(kt);
     if ((reinterpret_cast<uintptr_t>(kin) | reinterpret_cast<uintptr_t>(kout)) % ks ||
         (vin && ((reinterpret_cast<uintptr_t>(vin) | reinterpret_cast<uintptr_t>(vout)) & 3)))
         return fail(MSORT_ERR_INVALID_ARG, "buffers must be aligned to their element size");
     cudaStream_t st = (cudaStream_t)stream;
-    if (kt == MSORT_U32)
-        return vin ? sort_entry<uint32_t, true>(ctx, kin, vin, kout, vout, n, opt, st)
-                   : sort_entry<uint32_t, false>(ctx, kin, nullptr, kout, nullptr, n, opt, st);
-    return vin ? sort_entry<uint64_t, true>(ctx, kin, vin, kout, vout, n, opt, st)
-               : sort_entry<uint64_t, false>(ctx, kin, nullptr, kout, nullptr, n, opt, st);
+    const int xf = key_xform(kt);
+    if (ks == 4)
+        return vin ? sort_entry<uint32_t, true>(ctx, kin, vin, kout, vout, n, opt, st, xf)
+                   : sort_entry<uint32_t, false>(ctx, kin, nullptr, kout, nullptr, n, opt, st, xf);
+    return vin ? sort_entry<uint64_t, true>(ctx, kin, vin, kout, vout, n, opt, st, xf)
+               : sort_entry<uint64_t, false>(ctx, kin, nullptr, kout, nullptr, n, opt, st, xf);
 }
 
 msort_status msort_merge(msort_ctx* ctx, const void* d_a, const uint32_t* d_va, size_t na, const void* d_b,
@@ -847,6 +876,9 @@ msort_status msort_merge(msort_ctx* ctx, const void* d_a, const uint32_t* d_va, 
                          void* stream) {
     msort_status s = check_common(ctx, kt, nullptr);
     if (s != MSORT_OK) return s;
+    if (key_xform(kt))
+        return fail(MSORT_ERR_UNSUPPORTED, "msort_merge takes unsigned keys (signed and floating-point keys: "
+                                           "the plain and host-buffer sorts)");
     if (na + nb == 0) return MSORT_OK;
     if ((na && !d_a) || (nb && !d_b) || !d_out) return fail(MSORT_ERR_INVALID_ARG, "key pointer is NULL");
     const bool pairs = d_vout != nullptr;
@@ -905,12 +937,13 @@ static msort_status host_sort_call(msort_ctx* ctx, const void* h_kin, const uint
     if ((h_vin == nullptr) != (h_vout == nullptr)) return fail(MSORT_ERR_INVALID_ARG, "give both value pointers or none");
     cudaStream_t st = (cudaStream_t)stream;
     const int ch = wait ? kSyncChunks : kAsyncChunks, sl = wait ? kSyncSlices : kAsyncSlices;
-    if (kt == MSORT_U32)
-        s = h_vin ? host_sort<uint32_t, true>(ctx, h_kin, h_vin, h_kout, h_vout, n, opt, st, ch, sl)
-                  : host_sort<uint32_t, false>(ctx, h_kin, nullptr, h_kout, nullptr, n, opt, st, ch, sl);
+    const int xf = key_xform(kt);
+    if (key_bytes(kt) == 4)
+        s = h_vin ? host_sort<uint32_t, true>(ctx, h_kin, h_vin, h_kout, h_vout, n, opt, st, ch, sl, xf)
+                  : host_sort<uint32_t, false>(ctx, h_kin, nullptr, h_kout, nullptr, n, opt, st, ch, sl, xf);
     else
-        s = h_vin ? host_sort<uint64_t, true>(ctx, h_kin, h_vin, h_kout, h_vout, n, opt, st, ch, sl)
-                  : host_sort<uint64_t, false>(ctx, h_kin, nullptr, h_kout, nullptr, n, opt, st, ch, sl);
+        s = h_vin ? host_sort<uint64_t, true>(ctx, h_kin, h_vin, h_kout, h_vout, n, opt, st, ch, sl, xf)
+                  : host_sort<uint64_t, false>(ctx, h_kin, nullptr, h_kout, nullptr, n, opt, st, ch, sl, xf);
     if (s != MSORT_OK || !wait) return s;
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");

@@ -132,6 +132,9 @@ extern "C" {
 
 msort_status msort_sort_noalloc(const void* d_keys_in, const uint32_t* d_vals_in, void* d_keys_out,
                                 uint32_t* d_vals_out, size_t n, msort_key_type kt, void* stream) {
+    if (kt == MSORT_I32 || kt == MSORT_I64 || kt == MSORT_F32 || kt == MSORT_F64)
+        return fail(MSORT_ERR_UNSUPPORTED, "msort_sort_noalloc takes unsigned keys (signed and floating-point keys: the plain "
+                                           "and host-buffer sorts)");
     if (kt != MSORT_U32 && kt != MSORT_U64) return fail(MSORT_ERR_INVALID_ARG, "unknown key type");
     if (n == 0) return MSORT_OK;
     if (!d_keys_in || !d_keys_out) return fail(MSORT_ERR_INVALID_ARG, "key pointer is NULL");

@@ -466,6 +466,9 @@ extern "C" msort_status msort_segmented_sort(msort_ctx* ctx, void* d_keys, uint3
                                              const uint64_t* d_offsets, size_t nseg, size_t n, msort_key_type kt,
                                              const msort_options* opt, void* stream) {
     if (!ctx) return fail(MSORT_ERR_INVALID_ARG, "ctx is NULL");
+    if (kt == MSORT_I32 || kt == MSORT_I64 || kt == MSORT_F32 || kt == MSORT_F64)
+        return fail(MSORT_ERR_UNSUPPORTED, "msort_segmented_sort takes unsigned keys (signed and floating-point keys: the plain "
+                                           "and host-buffer sorts)");
     if (kt != MSORT_U32 && kt != MSORT_U64) return fail(MSORT_ERR_INVALID_ARG, "unknown key type");
     if (nseg == 0) return MSORT_OK;
     if (!d_offsets) return fail(MSORT_ERR_INVALID_ARG, "d_offsets is NULL");

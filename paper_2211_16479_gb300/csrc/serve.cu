@@ -255,6 +255,9 @@ msort_status msort_server_create(int device, size_t mem_budget_bytes, int max_sl
 msort_status msort_server_submit(msort_server* s, void* d_keys, uint32_t* d_vals, size_t n, msort_key_type kt,
                                  uint64_t* req_id) {
     if (!s || !req_id) return fail(MSORT_ERR_INVALID_ARG, "NULL argument");
+    if (kt == MSORT_I32 || kt == MSORT_I64 || kt == MSORT_F32 || kt == MSORT_F64)
+        return fail(MSORT_ERR_UNSUPPORTED, "msort_server_submit takes unsigned keys (signed and floating-point keys: the plain "
+                                           "and host-buffer sorts)");
     if (kt != MSORT_U32 && kt != MSORT_U64) return fail(MSORT_ERR_INVALID_ARG, "unknown key type");
     if (n && !d_keys) return fail(MSORT_ERR_INVALID_ARG, "d_keys is NULL");
     const size_t need = align_up(sort_scratch_need(n, kt == MSORT_U32 ? 4 : 8, d_vals != nullptr), 256);

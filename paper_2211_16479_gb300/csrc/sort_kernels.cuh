@@ -46,6 +46,30 @@ constexpr unsigned int kStatusTimeout = 1u;
 constexpr long long kWaitLimitCycles = 2000000000ll;
 
 // ---------------------------------------------------------------------------
+// Order-preserving key transforms.  Signed and floating-point keys are
+// sorted as unsigned words: xf 1 flips the sign bit (two's complement order
+// becomes unsigned order); xf 2 maps IEEE 754 bit patterns to unsigned
+// words in totalOrder (non-negative patterns get the sign bit set, negative
+// ones are complemented, so larger magnitudes of negative numbers come
+// first).  The tile sort applies the forward map as it reads its input and
+// the last merge round applies the inverse as it writes the output.
+// ---------------------------------------------------------------------------
+template <class K>
+__device__ __forceinline__ K xf_forward(K k, int xf) {
+    constexpr K sign = K(1) << (8 * sizeof(K) - 1);
+    if (xf == 1) return k ^ sign;
+    if (xf == 2) return (k & sign) ? K(~k) : K(k ^ sign);
+    return k;
+}
+template <class K>
+__device__ __forceinline__ K xf_inverse(K u, int xf) {
+    constexpr K sign = K(1) << (8 * sizeof(K) - 1);
+    if (xf == 1) return u ^ sign;
+    if (xf == 2) return (u & sign) ? K(u ^ sign) : K(~u);
+    return u;
+}
+
+// ---------------------------------------------------------------------------
 // Items of a tile: the key alone, or (key, position in tile) for pairs.
 // ---------------------------------------------------------------------------
 template <class K>
@@ -314,7 +338,7 @@ __device__ __forceinline__ void kv_merge_round(const K* sk, const uint32_t* sv, 
 
 template <class K, int THREADS, int IPT>
 __device__ __forceinline__ bool tile_sort_block_kv(const K* src, const uint32_t* vin, K* dst, uint32_t* vout,
-                                                   int valid, unsigned char* smem_raw) {
+                                                   int valid, unsigned char* smem_raw, int xf_in, int xf_out) {
     constexpr int T = THREADS * IPT;
     constexpr int SLOTS = tile_slots(T, THREADS);
     K* sk = reinterpret_cast<K*>(smem_raw);
@@ -325,7 +349,7 @@ __device__ __forceinline__ bool tile_sort_block_kv(const K* src, const uint32_t*
     for (int i = 0; i < IPT; ++i) {
         const int p = i * THREADS + t;
         const bool in = p < valid;
-        sk[p] = in ? src[p] : key_max<K>();
+        sk[p] = in ? xf_forward(src[p], xf_in) : key_max<K>();
         sv[p] = in ? vin[p] : 0u;
     }
     __syncthreads();
@@ -357,7 +381,7 @@ __device__ __forceinline__ bool tile_sort_block_kv(const K* src, const uint32_t*
     for (int i = 0; i < IPT; ++i) {
         const int p = i * THREADS + t;
         if (p < valid) {
-            dst[p] = sk[p];
+            dst[p] = xf_inverse(sk[p], xf_out);
             vout[p] = sv[p];
         }
     }
@@ -376,9 +400,9 @@ __device__ __forceinline__ bool tile_sort_block_kv(const K* src, const uint32_t*
 template <class K, bool PAIRS, int THREADS, int IPT>
 __device__ __forceinline__ bool tile_sort_block(const K* src, const uint32_t* vin, K* dst, uint32_t* vout, int valid,
                                                 unsigned char* smem_raw, uint64_t* bar, uint32_t& phase,
-                                                unsigned int* status) {
+                                                unsigned int* status, int xf_in = 0, int xf_out = 0) {
     if constexpr (PAIRS && sizeof(K) == 8) {
-        return tile_sort_block_kv<K, THREADS, IPT>(src, vin, dst, vout, valid, smem_raw);
+        return tile_sort_block_kv<K, THREADS, IPT>(src, vin, dst, vout, valid, smem_raw, xf_in, xf_out);
     }
     using TI = TileItem<K, PAIRS>;
     using Item = typename TI::T;
@@ -407,7 +431,7 @@ __device__ __forceinline__ bool tile_sort_block(const K* src, const uint32_t* vi
 #pragma unroll
         for (int i = 0; i < IPT; ++i) {
             const int p = i * THREADS + t;
-            s[p] = TI::make(p < valid ? src[p] : key_max<K>(), (uint32_t)p);
+            s[p] = TI::make(p < valid ? xf_forward(src[p], xf_in) : key_max<K>(), (uint32_t)p);
         }
         if (PAIRS) {
             for (int p = t; p < valid; p += THREADS) sv[p] = vin[p];
@@ -418,6 +442,10 @@ __device__ __forceinline__ bool tile_sort_block(const K* src, const uint32_t* vi
     Item r[IPT];
 #pragma unroll
     for (int i = 0; i < IPT; ++i) r[i] = s[t * IPT + i];
+    if (bulk && xf_in) {  // the bulk copy brought the raw keys (keys-only tiles)
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) r[i] = TI::make(xf_forward(TI::key(r[i]), xf_in), TI::pos(r[i]));
+    }
     thread_sort<TI, IPT>(r);
 
     const unsigned char* sb = smem_raw;
@@ -433,7 +461,7 @@ __device__ __forceinline__ bool tile_sort_block(const K* src, const uint32_t* vi
     if (!PAIRS) {
         K* sk = reinterpret_cast<K*>(smem_raw);
 #pragma unroll
-        for (int i = 0; i < IPT; ++i) sk[t * IPT + i] = TI::key(r[i]);
+        for (int i = 0; i < IPT; ++i) sk[t * IPT + i] = xf_inverse(TI::key(r[i]), xf_out);
         if (valid == T && aligned16(dst)) {
             fence_proxy_async_smem();
             __syncthreads();
@@ -459,7 +487,7 @@ __device__ __forceinline__ bool tile_sort_block(const K* src, const uint32_t* vi
             const int p = i * THREADS + t;
             if (p < valid) {
                 const Item it = s[p];
-                dst[p] = TI::key(it);
+                dst[p] = xf_inverse(TI::key(it), xf_out);
                 vout[p] = sv[TI::pos(it)];
             }
         }
@@ -478,7 +506,8 @@ __host__ __device__ constexpr size_t tile_block_smem(int T) {
 // kout.  kin may equal kout (each block reads its whole tile first).
 template <class K, bool PAIRS, int THREADS, int IPT>
 __global__ void __launch_bounds__(THREADS)
-k_tile_sort(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n, unsigned int* status) {
+k_tile_sort(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n, unsigned int* status, int xf_in,
+            int xf_out) {
     constexpr int T = THREADS * IPT;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
@@ -490,7 +519,8 @@ k_tile_sort(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n
     const int valid = (int)((n - base) < (size_t)T ? (n - base) : (size_t)T);
     uint32_t phase = 0;
     tile_sort_block<K, PAIRS, THREADS, IPT>(kin + base, PAIRS ? vin + base : nullptr, kout + base,
-                                            PAIRS ? vout + base : nullptr, valid, smem_raw, &bar, phase, status);
+                                            PAIRS ? vout + base : nullptr, valid, smem_raw, &bar, phase, status,
+                                            xf_in, xf_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -600,7 +630,7 @@ __host__ __device__ constexpr int merge_slots(int W, int IPT, int esize) {
 template <class K, bool PAIRS, int THREADS, int IPT>
 __device__ __forceinline__ bool merge_block(const K* gA, int nA, const K* gB, int nB, const uint32_t* gvA,
                                             const uint32_t* gvB, K* D, uint32_t* VD, unsigned char* smem_raw,
-                                            uint64_t* bar, uint32_t& phase, unsigned int* status) {
+                                            uint64_t* bar, uint32_t& phase, unsigned int* status, int xf_out = 0) {
     constexpr int W = THREADS * IPT;
     constexpr int KS = (int)sizeof(K);
     constexpr int KSLOTS = merge_slots(W, IPT, KS);
@@ -698,7 +728,7 @@ __device__ __forceinline__ bool merge_block(const K* gA, int nA, const K* gB, in
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
         if (i < mine) {
-            sk[t * IPT + i] = ok[i];
+            sk[t * IPT + i] = xf_inverse(ok[i], xf_out);
             if (PAIRS) sv[t * IPT + i] = ov[i];
         }
     }
@@ -731,7 +761,7 @@ template <class K, bool PAIRS, int THREADS, int IPT>
 __global__ void __launch_bounds__(THREADS)
 k_merge_pass(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __restrict__ vsrc,
              uint32_t* __restrict__ vdst, size_t n, size_t L, const unsigned long long* __restrict__ splits,
-             unsigned int* status, size_t c0) {
+             unsigned int* status, size_t c0, int xf_out) {
     constexpr int W = THREADS * IPT;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
@@ -753,7 +783,7 @@ k_merge_pass(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __r
     uint32_t phase = 0;
     merge_block<K, PAIRS, THREADS, IPT>(src + oA, nA, src + oB, nB, PAIRS ? vsrc + oA : nullptr,
                                         PAIRS ? vsrc + oB : nullptr, dst + out0, PAIRS ? vdst + out0 : nullptr,
-                                        smem_raw, &bar, phase, status);
+                                        smem_raw, &bar, phase, status, xf_out);
 }
 
 // ---------------------------------------------------------------------------
