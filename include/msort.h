@@ -59,9 +59,9 @@ typedef enum {
  * so every bit pattern has one place and equal bit patterns keep their input
  * order.  Signed and floating-point keys are accepted by msort_sort,
  * msort_sort_pairs, msort_sort_copy, msort_sort_host(_async),
- * msort_scratch_bytes and the plan queries, with partition_mode 0 and
- * pairwise passes; the other entry points return MSORT_ERR_UNSUPPORTED for
- * them.  They are sorted as unsigned keys after an order-preserving bit
+ * msort_segmented_sort, msort_scratch_bytes and the plan queries, with
+ * partition_mode 0 and pairwise passes; msort_merge, msort_sort_noalloc and
+ * the server return MSORT_ERR_UNSUPPORTED for them.  They are sorted as unsigned keys after an order-preserving bit
  * transform that the tile sort applies as it reads the input and the last
  * merge round undoes as it writes the output (no extra pass over memory). */
 typedef enum {

@@ -77,7 +77,7 @@ __device__ __forceinline__ unsigned int seg_next(unsigned int* counters, int q, 
 template <class K, bool PAIRS, int THREADS, int IPT>
 __global__ void __launch_bounds__(THREADS)
 k_seg_small(K* keys, uint32_t* vals, const unsigned long long* __restrict__ off, size_t nseg,
-            const unsigned int* __restrict__ lists, unsigned int* counters, int q, unsigned int* status) {
+            const unsigned int* __restrict__ lists, unsigned int* counters, int q, unsigned int* status, int xf) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ unsigned int slot;
@@ -94,7 +94,7 @@ k_seg_small(K* keys, uint32_t* vals, const unsigned long long* __restrict__ off,
         const int len = (int)(off[s + 1] - b);
         if (!tile_sort_block<K, PAIRS, THREADS, IPT>(keys + b, PAIRS ? vals + b : nullptr, keys + b,
                                                      PAIRS ? vals + b : nullptr, len, smem_raw, &bar, phase,
-                                                     status))
+                                                     status, xf, xf))
             return;
     }
 }
@@ -116,7 +116,8 @@ __device__ __forceinline__ void block_pass_barrier() {
 template <class K, bool PAIRS, int THREADS, int IPT>
 __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 3 : 2)
 k_seg_large(K* keys, uint32_t* vals, K* tkeys, uint32_t* tvals, const unsigned long long* __restrict__ off,
-            size_t nseg, const unsigned int* __restrict__ lists, unsigned int* counters, unsigned int* status) {
+            size_t nseg, const unsigned int* __restrict__ lists, unsigned int* counters, unsigned int* status,
+            int xf) {
     constexpr int T = THREADS * IPT;
     constexpr int W = T;
     constexpr int kSplitChunk = THREADS;
@@ -146,7 +147,8 @@ k_seg_large(K* keys, uint32_t* vals, K* tkeys, uint32_t* tvals, const unsigned l
             const int valid = (int)(len - j < (size_t)T ? len - j : (size_t)T);
             if (!tile_sort_block<K, PAIRS, THREADS, IPT>(keys + base + j, PAIRS ? vals + base + j : nullptr,
                                                          bk[cur] + j, PAIRS ? bv[cur] + j : nullptr, valid,
-                                                         smem_raw, &bar, phase, status))
+                                                         smem_raw, &bar, phase, status, xf,
+                                                         passes == 0 ? xf : 0))
                 return;
         }
         block_pass_barrier();
@@ -187,7 +189,7 @@ k_seg_large(K* keys, uint32_t* vals, K* tkeys, uint32_t* tvals, const unsigned l
                     if (!merge_block<K, PAIRS, THREADS, IPT>(
                             src + oA, nA, src + oB, nB, PAIRS ? bv[cur] + oA : nullptr,
                             PAIRS ? bv[cur] + oB : nullptr, dst + out0, PAIRS ? bv[cur ^ 1] + out0 : nullptr,
-                            smem_raw, &bar, phase, status))
+                            smem_raw, &bar, phase, status, p + 1 == passes ? xf : 0))
                         return;
                 }
             }
@@ -233,27 +235,27 @@ cudaError_t allow_smem(F* f, size_t smem) {
 template <class K, bool PAIRS, int TH, int IPT>
 cudaError_t launch_small(K* keys, uint32_t* vals, const unsigned long long* off, size_t nseg,
                          const unsigned int* lists, unsigned int* counters, int q, unsigned int* status,
-                         cudaStream_t st) {
+                         cudaStream_t st, int xf) {
     auto f = k_seg_small<K, PAIRS, TH, IPT>;
     const size_t sm = tile_block_smem<K, PAIRS, TH>(TH * IPT);
     cudaError_t e = allow_smem(f, sm);
     if (e != cudaSuccess) return e;
     const int blocks = persistent_blocks(f, TH, sm);
-    f<<<blocks, TH, sm, st>>>(keys, vals, off, nseg, lists, counters, q, status);
+    f<<<blocks, TH, sm, st>>>(keys, vals, off, nseg, lists, counters, q, status, xf);
     return cudaGetLastError();
 }
 
 template <class K, bool PAIRS, int TH, int IPT>
 cudaError_t launch_large(K* keys, uint32_t* vals, K* tk, uint32_t* tv, const unsigned long long* off, size_t nseg,
                          const unsigned int* lists, unsigned int* counters, unsigned int* status,
-                         cudaStream_t st) {
+                         cudaStream_t st, int xf) {
     auto f = k_seg_large<K, PAIRS, TH, IPT>;
     const size_t a = tile_block_smem<K, PAIRS, TH>(TH * IPT), b = merge_block_smem<K, PAIRS, TH, IPT>();
     const size_t sm = a > b ? a : b;
     cudaError_t e = allow_smem(f, sm);
     if (e != cudaSuccess) return e;
     const int blocks = persistent_blocks(f, TH, sm);
-    f<<<blocks, TH, sm, st>>>(keys, vals, tk, tv, off, nseg, lists, counters, status);
+    f<<<blocks, TH, sm, st>>>(keys, vals, tk, tv, off, nseg, lists, counters, status, xf);
     return cudaGetLastError();
 }
 
@@ -263,9 +265,9 @@ template <class K, bool PAIRS>
 struct SegPlan;
 
 #define MSORT_SMALL_LAUNCHES(K, PAIRS)                                                                          \
-    if ((e = launch_small<K, PAIRS, 32, 17>(keys, vals, off, nseg, lists, counters, 0, status, st))) return e;  \
-    if ((e = launch_small<K, PAIRS, 128, 17>(keys, vals, off, nseg, lists, counters, 1, status, st))) return e; \
-    if ((e = launch_small<K, PAIRS, 256, 33>(keys, vals, off, nseg, lists, counters, 2, status, st))) return e;
+    if ((e = launch_small<K, PAIRS, 32, 17>(keys, vals, off, nseg, lists, counters, 0, status, st, xf))) return e;  \
+    if ((e = launch_small<K, PAIRS, 128, 17>(keys, vals, off, nseg, lists, counters, 1, status, st, xf))) return e; \
+    if ((e = launch_small<K, PAIRS, 256, 33>(keys, vals, off, nseg, lists, counters, 2, status, st, xf))) return e;
 
 // 32-bit keys only: the largest on-chip bucket (16896 or 33792 keys) and the
 // large-segment tile (8448 or 16896) are tunable (msort_tune).
@@ -277,18 +279,19 @@ struct SegPlan<uint32_t, false> {
     }
     static cudaError_t run(const msort_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t* tk, uint32_t* tv,
                            const unsigned long long* off, size_t nseg, const unsigned int* lists,
-                           unsigned int* counters, unsigned int* status, cudaStream_t st) {
+                           unsigned int* counters, unsigned int* status, cudaStream_t st,
+                           int xf) {
         cudaError_t e;
         MSORT_SMALL_LAUNCHES(uint32_t, false)
-        if ((e = launch_small<uint32_t, false, 512, 33>(keys, vals, off, nseg, lists, counters, 3, status, st)))
+        if ((e = launch_small<uint32_t, false, 512, 33>(keys, vals, off, nseg, lists, counters, 3, status, st, xf)))
             return e;
         if (buckets(ctx).n == 5 &&
-            (e = launch_small<uint32_t, false, 1024, 33>(keys, vals, off, nseg, lists, counters, 4, status, st)))
+            (e = launch_small<uint32_t, false, 1024, 33>(keys, vals, off, nseg, lists, counters, 4, status, st, xf)))
             return e;
         if (ctx && ctx->seg_large_tile == 8448)
             return launch_large<uint32_t, false, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, status,
-                                                          st);
-        return launch_large<uint32_t, false, 512, 33>(keys, vals, tk, tv, off, nseg, lists, counters, status, st);
+                                                          st, xf);
+        return launch_large<uint32_t, false, 512, 33>(keys, vals, tk, tv, off, nseg, lists, counters, status, st, xf);
     }
 };
 
@@ -298,12 +301,12 @@ struct SegPlan<uint32_t, true> {
     static cudaError_t run(const msort_ctx*, uint32_t* keys, uint32_t* vals, uint32_t* tk, uint32_t* tv,
                            const unsigned long long* off,
                            size_t nseg, const unsigned int* lists, unsigned int* counters, unsigned int* status,
-                           cudaStream_t st) {
+                           cudaStream_t st, int xf) {
         cudaError_t e;
         MSORT_SMALL_LAUNCHES(uint32_t, true)
-        if ((e = launch_small<uint32_t, true, 512, 33>(keys, vals, off, nseg, lists, counters, 3, status, st)))
+        if ((e = launch_small<uint32_t, true, 512, 33>(keys, vals, off, nseg, lists, counters, 3, status, st, xf)))
             return e;
-        return launch_large<uint32_t, true, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, status, st);
+        return launch_large<uint32_t, true, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, status, st, xf);
     }
 };
 
@@ -313,12 +316,12 @@ struct SegPlan<uint64_t, false> {
     static cudaError_t run(const msort_ctx*, uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv,
                            const unsigned long long* off,
                            size_t nseg, const unsigned int* lists, unsigned int* counters, unsigned int* status,
-                           cudaStream_t st) {
+                           cudaStream_t st, int xf) {
         cudaError_t e;
         MSORT_SMALL_LAUNCHES(uint64_t, false)
-        if ((e = launch_small<uint64_t, false, 512, 33>(keys, vals, off, nseg, lists, counters, 3, status, st)))
+        if ((e = launch_small<uint64_t, false, 512, 33>(keys, vals, off, nseg, lists, counters, 3, status, st, xf)))
             return e;
-        return launch_large<uint64_t, false, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, status, st);
+        return launch_large<uint64_t, false, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, status, st, xf);
     }
 };
 
@@ -328,10 +331,10 @@ struct SegPlan<uint64_t, true> {
     static cudaError_t run(const msort_ctx*, uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv,
                            const unsigned long long* off,
                            size_t nseg, const unsigned int* lists, unsigned int* counters, unsigned int* status,
-                           cudaStream_t st) {
+                           cudaStream_t st, int xf) {
         cudaError_t e;
         MSORT_SMALL_LAUNCHES(uint64_t, true)
-        return launch_large<uint64_t, true, 256, 17>(keys, vals, tk, tv, off, nseg, lists, counters, status, st);
+        return launch_large<uint64_t, true, 256, 17>(keys, vals, tk, tv, off, nseg, lists, counters, status, st, xf);
     }
 };
 
@@ -352,7 +355,7 @@ SegLayout seg_layout(size_t n, size_t nseg) {
 
 template <class K, bool PAIRS>
 msort_status seg_enqueue(msort_ctx* ctx, K* keys, uint32_t* vals, const unsigned long long* off, size_t nseg,
-                         size_t n, cudaStream_t st) {
+                         size_t n, cudaStream_t st, int xf) {
     const SegLayout l = seg_layout<K, PAIRS>(n, nseg);
     unsigned char* sp = static_cast<unsigned char*>(ctx->scratch);
     K* tk = reinterpret_cast<K*>(sp + l.keys);
@@ -366,7 +369,7 @@ msort_status seg_enqueue(msort_ctx* ctx, K* keys, uint32_t* vals, const unsigned
                                                                    lists, counters, ctx->d_status);
     e = cudaGetLastError();
     if (e == cudaSuccess)
-        e = SegPlan<K, PAIRS>::run(ctx, keys, vals, tk, tv, off, nseg, lists, counters, ctx->d_status, st);
+        e = SegPlan<K, PAIRS>::run(ctx, keys, vals, tk, tv, off, nseg, lists, counters, ctx->d_status, st, xf);
     prof_end(ctx, KK_SEGMENTED, st);
     ctx->launches += 1 + SegPlan<K, PAIRS>::buckets(ctx).n + 1;
     if (e != cudaSuccess) return cuda_fail(e, "segmented sort launch");
@@ -378,7 +381,7 @@ struct SegGraphKey {
     const void* vals;
     const void* off;
     size_t nseg, n;
-    int kt;
+    int kt;  // key bytes, values and key transform
     const void* scratch;
     int tune_small, tune_large;
     bool operator<(const SegGraphKey& o) const {
@@ -408,7 +411,7 @@ void graphs_destroy(msort_ctx* ctx) {
 
 template <class K, bool PAIRS>
 msort_status seg_sort(msort_ctx* ctx, K* keys, uint32_t* vals, const unsigned long long* off, size_t nseg, size_t n,
-                      const msort_options* opt, cudaStream_t st) {
+                      const msort_options* opt, cudaStream_t st, int xf) {
     std::lock_guard<std::mutex> g(ctx->mu);
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
@@ -416,11 +419,11 @@ msort_status seg_sort(msort_ctx* ctx, K* keys, uint32_t* vals, const unsigned lo
     if (s != MSORT_OK) return s;
     const bool use_graph = opt && opt->use_graph;
     if (!use_graph || ctx->profiling) {
-        s = seg_enqueue<K, PAIRS>(ctx, keys, vals, off, nseg, n, st);
+        s = seg_enqueue<K, PAIRS>(ctx, keys, vals, off, nseg, n, st, xf);
     } else {
         GraphCache* gc = graph_cache(ctx);
-        const SegGraphKey key{keys,      vals, off, nseg, n, (int)sizeof(K) * 2 + PAIRS, ctx->scratch, ctx->seg_max_small,
-                              ctx->seg_large_tile};
+        const SegGraphKey key{keys,         vals, off, nseg, n, ((int)sizeof(K) * 2 + PAIRS) * 4 + xf, ctx->scratch,
+                              ctx->seg_max_small, ctx->seg_large_tile};
         auto it = gc->seg.find(key);
         if (it == gc->seg.end()) {
             cudaStream_t cap;
@@ -430,7 +433,7 @@ msort_status seg_sort(msort_ctx* ctx, K* keys, uint32_t* vals, const unsigned lo
             e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
                 const unsigned long long before = ctx->launches;
-                s = seg_enqueue<K, PAIRS>(ctx, keys, vals, off, nseg, n, cap);
+                s = seg_enqueue<K, PAIRS>(ctx, keys, vals, off, nseg, n, cap, xf);
                 ctx->launches = before;
                 cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
                 if (s == MSORT_OK && e2 != cudaSuccess) s = cuda_fail(e2, "cudaStreamEndCapture");
@@ -466,23 +469,25 @@ extern "C" msort_status msort_segmented_sort(msort_ctx* ctx, void* d_keys, uint3
                                              const uint64_t* d_offsets, size_t nseg, size_t n, msort_key_type kt,
                                              const msort_options* opt, void* stream) {
     if (!ctx) return fail(MSORT_ERR_INVALID_ARG, "ctx is NULL");
-    if (kt == MSORT_I32 || kt == MSORT_I64 || kt == MSORT_F32 || kt == MSORT_F64)
-        return fail(MSORT_ERR_UNSUPPORTED, "msort_segmented_sort takes unsigned keys (signed and floating-point keys: the plain "
-                                           "and host-buffer sorts)");
-    if (kt != MSORT_U32 && kt != MSORT_U64) return fail(MSORT_ERR_INVALID_ARG, "unknown key type");
+    int xf = 0;  // order-preserving key transform (see xf_forward)
+    if (kt == MSORT_I32 || kt == MSORT_I64) xf = 1;
+    if (kt == MSORT_F32 || kt == MSORT_F64) xf = 2;
+    const bool wide = kt == MSORT_U64 || kt == MSORT_I64 || kt == MSORT_F64;
+    if (!xf && kt != MSORT_U32 && kt != MSORT_U64) return fail(MSORT_ERR_INVALID_ARG, "unknown key type");
     if (nseg == 0) return MSORT_OK;
     if (!d_offsets) return fail(MSORT_ERR_INVALID_ARG, "d_offsets is NULL");
     if (n && !d_keys) return fail(MSORT_ERR_INVALID_ARG, "d_keys is NULL");
     if (nseg > 0xFFFFFFFFull) return fail(MSORT_ERR_UNSUPPORTED, "more than 2^32 - 1 segments");
-    const size_t ks = kt == MSORT_U32 ? 4 : 8;
+    const size_t ks = wide ? 8 : 4;
     if (reinterpret_cast<uintptr_t>(d_keys) % ks || reinterpret_cast<uintptr_t>(d_vals) % 4 ||
         reinterpret_cast<uintptr_t>(d_offsets) % 8)
         return fail(MSORT_ERR_INVALID_ARG, "buffers must be aligned to their element size");
     cudaStream_t st = (cudaStream_t)stream;
     const unsigned long long* off = reinterpret_cast<const unsigned long long*>(d_offsets);
-    if (kt == MSORT_U32)
-        return d_vals ? seg_sort<uint32_t, true>(ctx, static_cast<uint32_t*>(d_keys), d_vals, off, nseg, n, opt, st)
-                      : seg_sort<uint32_t, false>(ctx, static_cast<uint32_t*>(d_keys), nullptr, off, nseg, n, opt, st);
-    return d_vals ? seg_sort<uint64_t, true>(ctx, static_cast<uint64_t*>(d_keys), d_vals, off, nseg, n, opt, st)
-                  : seg_sort<uint64_t, false>(ctx, static_cast<uint64_t*>(d_keys), nullptr, off, nseg, n, opt, st);
+    if (!wide)
+        return d_vals ? seg_sort<uint32_t, true>(ctx, static_cast<uint32_t*>(d_keys), d_vals, off, nseg, n, opt, st, xf)
+                      : seg_sort<uint32_t, false>(ctx, static_cast<uint32_t*>(d_keys), nullptr, off, nseg, n, opt, st,
+                                                  xf);
+    return d_vals ? seg_sort<uint64_t, true>(ctx, static_cast<uint64_t*>(d_keys), d_vals, off, nseg, n, opt, st, xf)
+                  : seg_sort<uint64_t, false>(ctx, static_cast<uint64_t*>(d_keys), nullptr, off, nseg, n, opt, st, xf);
 }

@@ -2,7 +2,8 @@
 
 Keys are random bit patterns, so float inputs include NaNs of both signs,
 infinities, subnormals and both zeros, each of which has one place in IEEE
-754 totalOrder; integer inputs include both extremes.  Sizes cover a single
+754 totalOrder; integer inputs include both extremes.  The segmented sort is
+checked over every length bucket.  Sizes cover a single
 tile (no merge round: the tile sort applies and undoes the key transform),
 several tiles with a ragged tail, and many merge rounds.  Results are
 compared as bit patterns; values are original indices, so stability is
@@ -90,12 +91,27 @@ def test_copy_graph_and_host(ctx, name):
     assert np.array_equal(_bits(hout2.numpy()), _bits(ek))
 
 
+@pytest.mark.parametrize("name", list(TYPES))
+@pytest.mark.parametrize("pairs", [False, True])
+def test_segmented(ctx, name, pairs):
+    # every bucket: tiny, small-block, one-tile and multi-tile segments
+    lens = np.array([0, 1, 2, 31, 500, 544, 2000, 8448, 9000, 16896, 20000, 33792, 40000, 65536, 7], dtype=np.int64)
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.uint64)
+    n = int(off[-1])
+    keys = _keys(name, n, 3 + pairs)
+    vals = np.arange(n, dtype=np.uint32)
+    ek, ev = oracle.segmented_sort(keys, off, vals if pairs else None)
+    dk = _dev(keys)
+    dv = _dev(vals) if pairs else None
+    ms.msort_segmented_sort(ctx, dk, _dev(off), vals=dv)
+    ms.msort_ctx_sync(ctx)
+    assert np.array_equal(_bits(dk.cpu().numpy()), _bits(ek))
+    if pairs:
+        assert np.array_equal(dv.cpu().numpy(), ev)
+
+
 def test_other_entry_points_refuse(ctx):
     k = _dev(np.arange(1000, dtype=np.float32))
-    off = _dev(np.array([0, 500, 1000], dtype=np.uint64))
-    with pytest.raises(ms.MsortError) as e:
-        ms.msort_segmented_sort(ctx, k, off)
-    assert e.value.status == ms.MSORT_ERR_UNSUPPORTED
     with pytest.raises(ms.MsortError) as e:
         ms.msort_merge(ctx, k[:500], k[500:], torch.empty_like(k))
     assert e.value.status == ms.MSORT_ERR_UNSUPPORTED
