@@ -130,3 +130,65 @@ def test_whole_job_reductions():
     for p in procs:
         p.join(60)
     assert q.get(timeout=5) == (11.0, 200.0)
+
+
+# --- sample sort: one all-to-all exchange (the multi-GPU design) -------------
+def _oracle_sort_pairs(k, v):
+    kk, vv = oracle.sort(k.numpy(), v.numpy())
+    return torch.from_numpy(kk), torch.from_numpy(vv)
+
+
+def _oracle_merge_pairs(a, va, b, vb):
+    k, v = oracle.merge(a.numpy(), b.numpy(), None if va is None else va.numpy(),
+                        None if vb is None else vb.numpy())
+    return torch.from_numpy(k), (None if v is None else torch.from_numpy(v))
+
+
+def _sample_keys(kind, n):
+    if kind == "uniform":
+        return synth.uniform_u64(n, 5)
+    if kind == "dup16":
+        return synth.uniform_u64(n, 6) % np.uint64(16)
+    return np.full(n, 7, dtype=np.uint64)  # all equal
+
+
+def _sample_worker(rank, world, port, n, kind, q):
+    _init(rank, world, port)
+    try:
+        keys = _sample_keys(kind, n)
+        vals = np.arange(n, dtype=np.uint32)
+        # uneven chunks, one of them empty when world > 2
+        cuts = [0] + sorted({(n * (r * r + 1)) // (world * world + 1) for r in range(1, world)}) + [n]
+        if world > 2:
+            cuts[1] = cuts[0]  # rank 0 holds nothing
+        lk = torch.from_numpy(keys[cuts[rank]:cuts[rank + 1]].copy())
+        lv = torch.from_numpy(vals[cuts[rank]:cuts[rank + 1]].copy())
+        k, v = dist.sample_sort(lk, lv, local_sort=_oracle_sort_pairs, merge=_oracle_merge_pairs)
+        parts = [None] * world
+        tdist.all_gather_object(parts, (k.numpy(), v.numpy()))
+        if rank == 0:
+            gk = np.concatenate([p[0] for p in parts])
+            gv = np.concatenate([p[1] for p in parts])
+            ek, ev = oracle.sort(keys, vals)
+            sizes = [len(p[0]) for p in parts]
+            balanced = max(sizes) <= 1.5 * n / world + 64
+            q.put((bool(np.array_equal(gk, ek) and np.array_equal(gv, ev)), balanced, sizes))
+    finally:
+        tdist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 4])
+@pytest.mark.parametrize("kind", ["uniform", "dup16", "equal"])
+def test_sample_sort_cpu_ranks(world, kind):
+    ctx = tmp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_sample_worker, args=(r, world, port, 20011, kind, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+    assert all(p.exitcode == 0 for p in procs)
+    same, balanced, sizes = q.get(timeout=5)
+    assert same, sizes
+    assert balanced, sizes  # (key, position) splitters split runs of equal keys too

@@ -65,3 +65,37 @@ def test_tree_merge_sort_single_gpu_rank(ctx):
         assert np.array_equal(to_host(out), oracle.sort(keys)[0])
     finally:
         tdist.destroy_process_group()
+
+
+def test_sample_sort_gpu_pieces_and_single_rank(ctx):
+    """The sample sort's GPU building blocks (local pair sort carrying the
+    local index, stable merge with values) against the oracle, and one
+    single-rank NCCL run through the device collectives."""
+    import datetime
+    import os
+    import socket
+
+    import torch.distributed as tdist
+
+    from paper_2211_16479_gb300 import dist
+    n = 300007
+    keys = synth.uniform_u64(n, 11) % np.uint64(5000)
+    vals = np.arange(n, dtype=np.uint32)
+    k, v = dist._gpu_sort_pairs(ctx)(to_dev(keys), to_dev(vals))
+    ek, ev = oracle.sort(keys, vals)
+    assert np.array_equal(to_host(k), ek) and np.array_equal(to_host(v), ev)
+    a, b = ek[: n // 3], ek[n // 3:]
+    va, vb = ev[: n // 3], ev[n // 3:]
+    m, mv = dist._gpu_merge_pairs(ctx)(to_dev(a), to_dev(va), to_dev(b), to_dev(vb))
+    em, emv = oracle.merge(a, b, va, vb)
+    assert np.array_equal(to_host(m), em) and np.array_equal(to_host(mv), emv)
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    os.environ["MASTER_ADDR"], os.environ["MASTER_PORT"] = "127.0.0.1", str(port)
+    tdist.init_process_group("nccl", rank=0, world_size=1, timeout=datetime.timedelta(seconds=60))
+    try:
+        sk, sv = dist.sample_sort(to_dev(keys), to_dev(vals), ctx=ctx)
+        assert np.array_equal(to_host(sk), ek) and np.array_equal(to_host(sv), ev)
+    finally:
+        tdist.destroy_process_group()
