@@ -105,7 +105,8 @@ typedef struct {
 
 /* Context on CUDA device `device`.  scratch_budget_bytes caps the scratch the
  * context may hold (0 = no cap); a sort that needs more fails with
- * MSORT_ERR_OOM and enqueues nothing. */
+ * MSORT_ERR_OOM and enqueues nothing.  The host-buffer sorts instead switch to
+ * an out-of-core sort that stays within the cap (see msort_sort_host). */
 msort_status msort_ctx_create(int device, size_t scratch_budget_bytes, msort_ctx** out);
 /* Waits for the context's outstanding work, frees its scratch and itself. */
 msort_status msort_ctx_destroy(msort_ctx* ctx);
@@ -185,7 +186,20 @@ msort_status msort_merge(msort_ctx* ctx, const void* d_a, const uint32_t* d_va, 
  * the whole array each way around the sort).  Device buffers come from the
  * context: three staging slots, used by consecutive calls in turn, each
  * growing to the largest n it served, plus the sort scratch.  Synchronises on `stream`
- * before returning. */
+ * before returning.
+ *
+ * Out of core: when the context has a budget and the three staging slots
+ * plus the scratch for n elements would exceed it, the array is sorted in
+ * budget-sized chunks C whose sorted runs go to a pinned host buffer owned by
+ * the context (n keys and values, kept for later calls); every C/(2R)-th
+ * element of the R runs is sampled, and every R-th sample in (key, position)
+ * order becomes a splitter, so each block between consecutive splitters
+ * holds at most C elements; each block's slices of all runs are copied to a
+ * staging slot, sorted stably (their stable merge) and copied to their place
+ * in the output, consecutive blocks overlapping on the context's streams.
+ * MSORT_ERR_OOM if the budget does not fit a chunk of four 16896-key tiles.
+ * This path is taken by msort_sort_host_async too, and then returns with the
+ * output complete. */
 msort_status msort_sort_host(msort_ctx* ctx, const void* h_keys_in, const uint32_t* h_vals_in,
                              void* h_keys_out, uint32_t* h_vals_out, size_t n, msort_key_type kt,
                              const msort_options* opt, void* stream);

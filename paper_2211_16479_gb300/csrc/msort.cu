@@ -15,6 +15,7 @@
 #include <map>
 #include <string>
 #include <tuple>
+#include <vector>
 
 #include "ctx.h"
 #include "learned.h"
@@ -533,6 +534,10 @@ struct HostPipe {
     cudaEvent_t out_ev[kHostSlots][kHostSlices] = {};
     bool used[kHostSlots] = {};
     int next = 0;
+    // out-of-core sorts: pinned host buffer of sorted runs, kept between
+    // calls (pinning memory is slow)
+    void* runs = nullptr;
+    size_t runs_bytes = 0;
 };
 
 static msort_status host_pipe_get(msort_ctx* ctx, HostPipe** out) {
@@ -568,6 +573,7 @@ void host_pipe_destroy(msort_ctx* ctx) {
         for (cudaEvent_t ev : hp->out_ev[s])
             if (ev) cudaEventDestroy(ev);
     }
+    if (hp->runs) cudaFreeHost(hp->runs);
     if (hp->h2d) cudaStreamDestroy(hp->h2d);
     if (hp->cs) cudaStreamDestroy(hp->cs);
     if (hp->d2h) cudaStreamDestroy(hp->d2h);
@@ -747,6 +753,205 @@ static msort_status host_sort(msort_ctx* ctx, const void* h_kin_v, const uint32_
     hp->used[sl] = true;
     scratch_release(ctx, cs);
     return MSORT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Host arrays larger than the device budget: an external merge sort.  The
+// context's budget (msort_ctx_create) caps the device memory a sort may use;
+// when the pipelined host sort of n elements would exceed it, the array is
+// sorted in chunks that fit (each by the pipelined host sort, into a pinned
+// host buffer of sorted runs) and the runs are merged in blocks that fit:
+//  * regular samples, every sigma-th element of every run, sorted by
+//    (key order, position), and every R-th of them as a block splitter bound
+//    every block to at most (R + R) * sigma <= B elements (each run
+//    contributes at most (its samples in the block + 1) * sigma elements);
+//  * each block's slice of every run is copied to the device, sorted there
+//    stably (the stable sort of the slices in run order is their stable
+//    merge), and copied to its place in the output; blocks rotate through
+//    the host sort's staging slots and streams, so one block's copy-in, the
+//    previous one's sort and the one before's copy-out overlap.
+// Splitters order equal keys by position, so runs of equal keys split too
+// and the result is the stable sort of the whole array.
+// ---------------------------------------------------------------------------
+template <class K>
+static inline K host_order_key(K k, int xform) {  // the order-preserving map of the kernels
+    constexpr K sign = K(1) << (8 * sizeof(K) - 1);
+    if (xform == 1) return k ^ sign;
+    if (xform == 2) return (k & sign) ? K(~k) : K(k ^ sign);
+    return k;
+}
+
+// Device bytes the pipelined host sort of n elements may hold (three
+// staging slots and the sort scratch).
+template <class K, bool PAIRS>
+static size_t host_incore_bytes(size_t n, const Plan& pl) {
+    const size_t slot = align_up(n * sizeof(K), 256) + (PAIRS ? align_up(n * 4, 256) : 0);
+    return (size_t)kHostSlots * slot + align_up(scratch_need<K, PAIRS>(n, pl), size_t(2) << 20);  // scratch grows in 2 MiB steps
+}
+
+// Largest chunk whose in-core host sort fits the budget (0 if not even a
+// few tiles fit).  The merge blocks reuse the same staging slots.
+template <class K, bool PAIRS>
+static size_t external_chunk(size_t budget, const msort_options* opt, int xform) {
+    size_t lo = 0, hi = budget / sizeof(K) + 1;
+    while (lo + 1 < hi) {
+        const size_t mid = lo + (hi - lo) / 2;
+        Plan pl;
+        std::string why;
+        const bool ok = make_plan<K, PAIRS>(mid, opt, &pl, &why, xform);
+        if (ok && host_incore_bytes<K, PAIRS>(mid, pl) <= budget)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo >= 4 * 16896 ? lo : 0;
+}
+
+template <class K, bool PAIRS>
+static msort_status host_sort_external(msort_ctx* ctx, const K* h_kin, const uint32_t* h_vin, K* h_kout,
+                                       uint32_t* h_vout, size_t n, const msort_options* opt, cudaStream_t st,
+                                       int xform, size_t chunk) {
+    HostPipe* hp = nullptr;
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        msort_status s = host_pipe_get(ctx, &hp);
+        if (s != MSORT_OK) return s;
+        const size_t need = n * sizeof(K) + (PAIRS ? n * 4 : 0);
+        if (hp->runs_bytes < need) {
+            cudaError_t e = cudaStreamSynchronize(st);  // no copy may still use the old buffer
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+            if (hp->runs) cudaFreeHost(hp->runs);
+            hp->runs = nullptr;
+            hp->runs_bytes = 0;
+            if (cudaMallocHost(&hp->runs, need) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(MSORT_ERR_OOM, "pinned host buffer for the sorted runs");
+            }
+            hp->runs_bytes = need;
+        }
+    }
+    K* tk = static_cast<K*>(hp->runs);
+    uint32_t* tv = PAIRS ? reinterpret_cast<uint32_t*>(tk + n) : nullptr;
+    const size_t R = (n + chunk - 1) / chunk;
+
+    // 1. sorted runs, one budget-sized chunk at a time
+    for (size_t r = 0; r < R; ++r) {
+        const size_t off = r * chunk, len = std::min(chunk, n - off);
+        msort_status s = host_sort<K, PAIRS>(ctx, h_kin + off, PAIRS ? h_vin + off : nullptr, tk + off,
+                                             PAIRS ? tv + off : nullptr, len, opt, st, kSyncChunks, kSyncSlices,
+                                             xform);
+        if (s != MSORT_OK) return s;
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+
+    // 2. splitters from regular samples of the runs
+    const size_t B = chunk;
+    const size_t sigma = std::max<size_t>(1, B / (2 * R));
+    struct Smp {
+        K u;
+        size_t g;
+    };
+    auto before = [](const Smp& a, const Smp& b) { return a.u < b.u || (a.u == b.u && a.g < b.g); };
+    std::vector<Smp> smp;
+    for (size_t r = 0; r < R; ++r) {
+        const size_t off = r * chunk, len = std::min(chunk, n - off);
+        for (size_t j = 0; j < len; j += sigma) smp.push_back(Smp{host_order_key(tk[off + j], xform), off + j});
+    }
+    std::sort(smp.begin(), smp.end(), before);
+    std::vector<Smp> spl;
+    for (size_t i = R; i < smp.size(); i += R) spl.push_back(smp[i]);
+    const size_t nb = spl.size() + 1;  // blocks
+    std::vector<size_t> cut((nb + 1) * R);
+    for (size_t r = 0; r < R; ++r) {
+        const size_t off = r * chunk, len = std::min(chunk, n - off);
+        cut[r] = 0;
+        cut[nb * R + r] = len;
+        for (size_t i = 0; i < spl.size(); ++i) {  // run-r elements ordered before splitter i
+            size_t lo = 0, hi = len;
+            while (lo < hi) {
+                const size_t mid = lo + (hi - lo) / 2;
+                if (before(Smp{host_order_key(tk[off + mid], xform), off + mid}, spl[i]))
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            cut[(i + 1) * R + r] = lo;
+        }
+    }
+
+    // 3. every block: slices in, stable sort, out, pipelined through the
+    //    staging slots on the context's copy-in, compute and copy-out streams
+    const size_t kb = align_up(B * sizeof(K), 256);
+    const size_t dbytes = kb + (PAIRS ? align_up(B * 4, 256) : 0);
+    int slots[kHostSlots], ns = 0;
+    for (int i = 0; i < kHostSlots; ++i)
+        if (hp->slot_bytes[i] >= dbytes) slots[ns++] = i;
+    if (!ns) return fail(MSORT_ERR_CUDA, "no staging slot holds an out-of-core block");
+    msort_options bopt{};  // block sizes differ: no graph per block
+    if (opt) bopt = *opt;
+    bopt.use_graph = 0;
+    size_t out = 0, bi = 0;
+    int last = -1;
+    for (size_t b = 0; b < nb; ++b) {
+        size_t len = 0;
+        for (size_t r = 0; r < R; ++r) len += cut[(b + 1) * R + r] - cut[b * R + r];
+        if (!len) continue;
+        if (len > B) return fail(MSORT_ERR_CUDA, "out-of-core block larger than its bound");
+        const int sl = slots[bi++ % ns];
+        K* dk = static_cast<K*>(hp->slot[sl]);
+        uint32_t* dv = PAIRS ? reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(hp->slot[sl]) + kb) : nullptr;
+        if (hp->used[sl]) cudaStreamWaitEvent(hp->h2d, hp->done[sl], 0);  // its last block has left
+        size_t pos = 0;
+        for (size_t r = 0; r < R; ++r) {
+            const size_t off = r * chunk, lo = cut[b * R + r], cnt = cut[(b + 1) * R + r] - lo;
+            if (!cnt) continue;
+            e = cudaMemcpyAsync(dk + pos, tk + off + lo, cnt * sizeof(K), cudaMemcpyHostToDevice, hp->h2d);
+            if (e == cudaSuccess && PAIRS)
+                e = cudaMemcpyAsync(dv + pos, tv + off + lo, cnt * 4, cudaMemcpyHostToDevice, hp->h2d);
+            if (e != cudaSuccess) return cuda_fail(e, "host to device copy");
+            pos += cnt;
+        }
+        cudaEventRecord(hp->in_ev[sl][0], hp->h2d);
+        cudaStreamWaitEvent(hp->cs, hp->in_ev[sl][0], 0);
+        msort_status s = sort_entry<K, PAIRS>(ctx, dk, dv, dk, dv, len, &bopt, hp->cs, xform);
+        if (s != MSORT_OK) return s;
+        cudaEventRecord(hp->out_ev[sl][0], hp->cs);
+        cudaStreamWaitEvent(hp->d2h, hp->out_ev[sl][0], 0);
+        e = cudaMemcpyAsync(h_kout + out, dk, len * sizeof(K), cudaMemcpyDeviceToHost, hp->d2h);
+        if (e == cudaSuccess && PAIRS)
+            e = cudaMemcpyAsync(h_vout + out, dv, len * 4, cudaMemcpyDeviceToHost, hp->d2h);
+        if (e != cudaSuccess) return cuda_fail(e, "device to host copy");
+        cudaEventRecord(hp->done[sl], hp->d2h);
+        hp->used[sl] = true;
+        last = sl;
+        out += len;
+    }
+    if (last >= 0) cudaStreamWaitEvent(st, hp->done[last], 0);
+    e = cudaStreamSynchronize(st);  // the caller's host output is complete on return
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return out == n ? MSORT_OK : fail(MSORT_ERR_CUDA, "out-of-core blocks did not cover the array");
+}
+
+// Host sort of n elements: in core when it fits the budget, else external.
+template <class K, bool PAIRS>
+static msort_status host_sort_any(msort_ctx* ctx, const void* h_kin, const uint32_t* h_vin, void* h_kout,
+                                  uint32_t* h_vout, size_t n, const msort_options* opt, cudaStream_t st, int chunks,
+                                  int slices, int xform, bool* synced) {
+    *synced = false;
+    if (ctx->budget) {
+        Plan pl;
+        std::string why;
+        if (!make_plan<K, PAIRS>(n, opt, &pl, &why, xform)) return fail(MSORT_ERR_INVALID_ARG, why);
+        if (host_incore_bytes<K, PAIRS>(n, pl) > ctx->budget) {
+            const size_t chunk = external_chunk<K, PAIRS>(ctx->budget, opt, xform);
+            if (!chunk) return fail(MSORT_ERR_OOM, "the context budget is too small even for out-of-core sorting");
+            *synced = true;
+            return host_sort_external<K, PAIRS>(ctx, static_cast<const K*>(h_kin), h_vin, static_cast<K*>(h_kout),
+                                                h_vout, n, opt, st, xform, chunk);
+        }
+    }
+    return host_sort<K, PAIRS>(ctx, h_kin, h_vin, h_kout, h_vout, n, opt, st, chunks, slices, xform);
 }
 
 }  // namespace msort
@@ -938,13 +1143,16 @@ static msort_status host_sort_call(msort_ctx* ctx, const void* h_kin, const uint
     cudaStream_t st = (cudaStream_t)stream;
     const int ch = wait ? kSyncChunks : kAsyncChunks, sl = wait ? kSyncSlices : kAsyncSlices;
     const int xf = key_xform(kt);
+    bool synced = false;
     if (key_bytes(kt) == 4)
-        s = h_vin ? host_sort<uint32_t, true>(ctx, h_kin, h_vin, h_kout, h_vout, n, opt, st, ch, sl, xf)
-                  : host_sort<uint32_t, false>(ctx, h_kin, nullptr, h_kout, nullptr, n, opt, st, ch, sl, xf);
+        s = h_vin ? host_sort_any<uint32_t, true>(ctx, h_kin, h_vin, h_kout, h_vout, n, opt, st, ch, sl, xf, &synced)
+                  : host_sort_any<uint32_t, false>(ctx, h_kin, nullptr, h_kout, nullptr, n, opt, st, ch, sl, xf,
+                                                   &synced);
     else
-        s = h_vin ? host_sort<uint64_t, true>(ctx, h_kin, h_vin, h_kout, h_vout, n, opt, st, ch, sl, xf)
-                  : host_sort<uint64_t, false>(ctx, h_kin, nullptr, h_kout, nullptr, n, opt, st, ch, sl, xf);
-    if (s != MSORT_OK || !wait) return s;
+        s = h_vin ? host_sort_any<uint64_t, true>(ctx, h_kin, h_vin, h_kout, h_vout, n, opt, st, ch, sl, xf, &synced)
+                  : host_sort_any<uint64_t, false>(ctx, h_kin, nullptr, h_kout, nullptr, n, opt, st, ch, sl, xf,
+                                                   &synced);
+    if (s != MSORT_OK || !wait || synced) return s;
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     return MSORT_OK;
