@@ -17,8 +17,9 @@
  *  - Pointers named d_* are device pointers on the context's device; h_*
  *    are host pointers (pinned memory gives the fastest copies).  The caller
  *    owns every buffer it passes; the library never frees them.
- *  - Keys are unsigned 32- or 64-bit integers (msort_key_type), compared as
- *    unsigned.  Values are optional uint32 words that travel with their key.
+ *  - Keys are 32- or 64-bit unsigned or signed integers or IEEE floats
+ *    (msort_key_type, ordered as described there).  Values are optional
+ *    uint32 words that travel with their key.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *    stream).  Device work is enqueued on it and the call returns without
  *    waiting, except where a function says it synchronises.
