@@ -33,6 +33,7 @@ struct Plan {
     int W4;     // outputs per four-way merge block
     int G4;     // grid step of the four-way partition
     int xform;  // key transform: 0 unsigned keys, 1 signed integers, 2 IEEE floating point
+    int xform_out;  // transform the last round undoes: xform, or 0 to leave the keys transformed
     unsigned int* status;  // device status word of the context
 };
 

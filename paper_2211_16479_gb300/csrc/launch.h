@@ -54,6 +54,22 @@ cudaError_t launch_merge_two(const K* A, size_t na, const K* B, size_t nb, const
                              cudaStream_t st);
 template <class K, bool PAIRS>
 size_t merge_two_block();
+// One merge-tree round over sorted runs of arbitrary lengths laid end to
+// end: pair j merges [p[j], m[j]) with [m[j], p[j+1]) in place of both (in
+// the destination buffer); its output blocks of merge_two_block() outputs
+// are [c[j], c[j+1]).  Passed to the kernels by value.
+constexpr int kRunPairsMax = 32;
+struct RunPairs {
+    int np;                                  // pairs (1..kRunPairsMax)
+    unsigned long long p[kRunPairsMax + 1];  // pair starts; p[np] = end of the last pair
+    unsigned long long m[kRunPairsMax];      // start of each pair's second run (= p[j+1] if none)
+    unsigned long long c[kRunPairsMax + 1];  // first output block of each pair; c[np] = blocks
+};
+// splits: c[np] + 1 entries; xf_out: key transform the round undoes as it
+// writes (see xf_inverse).
+template <class K, bool PAIRS>
+cudaError_t launch_merge_runs(const K* src, K* dst, const uint32_t* vsrc, uint32_t* vdst, const RunPairs& rp,
+                              unsigned long long* splits, unsigned int* status, int xf_out, cudaStream_t st);
 // Resource summary of the last kernel the calling thread prepared to launch.
 const std::string& last_launch_info();
 

@@ -5,6 +5,7 @@
 
 #include "launch.h"
 #include "merge4.cuh"
+#include "merge_runs.cuh"
 #include "sort_kernels.cuh"
 
 namespace msort {
@@ -188,6 +189,29 @@ cudaError_t launch_merge_two(const K* A, size_t na, const K* B, size_t nb, const
     return cudaGetLastError();
 }
 
+template <class K, bool PAIRS>
+cudaError_t launch_merge_runs(const K* src, K* dst, const uint32_t* vsrc, uint32_t* vdst, const RunPairs& rp,
+                              unsigned long long* splits, unsigned int* status, int xf_out, cudaStream_t st) {
+    const size_t W = merge_two_block<K, PAIRS>();
+    const unsigned long long nblocks = rp.c[rp.np];
+    if (nblocks == 0) return cudaSuccess;
+    k_partition_runs<K><<<(unsigned)((nblocks + 127) / 128), 128, 0, st>>>(src, rp, W, splits);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (W == 256 * 33) {
+        auto f = k_merge_runs<K, PAIRS, 256, 33>;
+        const size_t sm = merge_block_smem<K, PAIRS, 256, 33>();
+        if ((e = prepare(f, sm)) != cudaSuccess) return e;
+        f<<<(unsigned)nblocks, 256, sm, st>>>(src, dst, vsrc, vdst, rp, splits, status, xf_out);
+    } else {
+        auto f = k_merge_runs<K, PAIRS, 256, 17>;
+        const size_t sm = merge_block_smem<K, PAIRS, 256, 17>();
+        if ((e = prepare(f, sm)) != cudaSuccess) return e;
+        f<<<(unsigned)nblocks, 256, sm, st>>>(src, dst, vsrc, vdst, rp, splits, status, xf_out);
+    }
+    return cudaGetLastError();
+}
+
 #define MSORT_INSTANTIATE(K)                                                                                    \
     template size_t tile_smem_bytes<K, false>(int);                                                             \
     template size_t tile_smem_bytes<K, true>(int);                                                              \
@@ -219,6 +243,10 @@ cudaError_t launch_merge_two(const K* A, size_t na, const K* B, size_t nb, const
                                                     unsigned int*, cudaStream_t);                               \
     template cudaError_t launch_merge_two<K, true>(const K*, size_t, const K*, size_t, const uint32_t*,          \
                                                    const uint32_t*, K*, uint32_t*, unsigned long long*,         \
-                                                   unsigned int*, cudaStream_t);
+                                                   unsigned int*, cudaStream_t);                                \
+    template cudaError_t launch_merge_runs<K, false>(const K*, K*, const uint32_t*, uint32_t*, const RunPairs&,  \
+                                                     unsigned long long*, unsigned int*, int, cudaStream_t);     \
+    template cudaError_t launch_merge_runs<K, true>(const K*, K*, const uint32_t*, uint32_t*, const RunPairs&,   \
+                                                    unsigned long long*, unsigned int*, int, cudaStream_t);
 
 }  // namespace msort

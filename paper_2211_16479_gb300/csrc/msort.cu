@@ -154,6 +154,7 @@ static bool make_plan(size_t n, const msort_options* opt, Plan* pl, std::string*
     }
     p.ways = ways;
     p.xform = xform;
+    p.xform_out = xform;
     if (xform && (p.partition_mode != 0 || ways != 2)) {
         *why = "signed and floating-point keys need partition_mode 0 and pairwise merge passes";
         return false;
@@ -225,7 +226,7 @@ static msort_status run_sort(msort_ctx* ctx, const K* kin, const uint32_t* vin, 
     int cur = ((two + four) & 1) ? 1 : 0;
     cudaError_t e;
     if (log) prof_begin(ctx, KK_TILE, st);
-    e = launch_tile<K, PAIRS>(pl, kin, vin, bk[cur], bv[cur], n, st, pl.xform, pl.passes == 0 ? pl.xform : 0);
+    e = launch_tile<K, PAIRS>(pl, kin, vin, bk[cur], bv[cur], n, st, pl.xform, pl.passes == 0 ? pl.xform_out : 0);
     if (log) prof_end(ctx, KK_TILE, st);
     ++ctx->launches;
     if (e != cudaSuccess) return cuda_fail(e, ("tile sort launch" + last_launch_info()).c_str());
@@ -241,7 +242,7 @@ static msort_status run_sort(msort_ctx* ctx, const K* kin, const uint32_t* vin, 
         ++ctx->launches;
         if (e != cudaSuccess) return cuda_fail(e, "partition launch");
         if (log) prof_begin(ctx, KK_MERGE, st);
-        const int xf_out = (p + 1 == pl.passes) ? pl.xform : 0;  // the last round writes the caller's keys
+        const int xf_out = (p + 1 == pl.passes) ? pl.xform_out : 0;  // the last round writes the caller's keys
         e = launch_merge<K, PAIRS>(pl, bk[cur], bk[cur ^ 1], bv[cur], bv[cur ^ 1], n, L, splits, st, 0, ~size_t(0),
                                    xf_out);
         if (log) prof_end(ctx, KK_MERGE, st);
@@ -585,7 +586,7 @@ void host_pipe_destroy(msort_ctx* ctx) {
 template <class K, bool PAIRS>
 static msort_status host_sort(msort_ctx* ctx, const void* h_kin_v, const uint32_t* h_vin, void* h_kout_v,
                               uint32_t* h_vout, size_t n, const msort_options* opt, cudaStream_t st, int chunks,
-                              int slices, int xform) {
+                              int slices, int xform, bool keep_xform = false) {
     const K* h_kin = static_cast<const K*>(h_kin_v);
     K* h_kout = static_cast<K*>(h_kout_v);
     msort_options tuned_opt{};
@@ -600,6 +601,7 @@ static msort_status host_sort(msort_ctx* ctx, const void* h_kin_v, const uint32_
     Plan pl;
     std::string why;
     if (!make_plan<K, PAIRS>(n, opt, &pl, &why, xform)) return fail(MSORT_ERR_INVALID_ARG, why);
+    if (keep_xform) pl.xform_out = 0;  // output keys stay in their transformed (unsigned) order
     std::lock_guard<std::mutex> g(ctx->mu);
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
@@ -697,7 +699,7 @@ static msort_status host_sort(msort_ctx* ctx, const void* h_kin_v, const uint32_
             cudaEventRecord(hp->in_ev[sl][i], hp->h2d);
             cudaStreamWaitEvent(cs, hp->in_ev[sl][i], 0);
             e = launch_tile<K, PAIRS>(pl, S + off, PAIRS ? SV + off : nullptr, bk[cur0] + off,
-                                      PAIRS ? bv[cur0] + off : nullptr, ni, cs, pl.xform, P == 0 ? pl.xform : 0);
+                                      PAIRS ? bv[cur0] + off : nullptr, ni, cs, pl.xform, P == 0 ? pl.xform_out : 0);
             ++ctx->launches;
             if (e != cudaSuccess) return cuda_fail(e, ("tile sort launch" + last_launch_info()).c_str());
             int cur = cur0;
@@ -723,7 +725,7 @@ static msort_status host_sort(msort_ctx* ctx, const void* h_kin_v, const uint32_
             for (int j = 0; j < ns; ++j) {
                 const size_t c0 = nblocks * j / ns, c1 = nblocks * (j + 1) / ns;
                 e = launch_merge<K, PAIRS>(pl, bk[cur], bk[cur ^ 1], bv[cur], bv[cur ^ 1], n, L, splits, cs, c0, c1,
-                                           p + 1 == P ? pl.xform : 0);
+                                           p + 1 == P ? pl.xform_out : 0);
                 ++ctx->launches;
                 if (e != cudaSuccess) return cuda_fail(e, ("merge pass launch" + last_launch_info()).c_str());
                 if (p + 1 == P && c1 > c0) {
@@ -765,11 +767,15 @@ static msort_status host_sort(msort_ctx* ctx, const void* h_kin_v, const uint32_
 //    (key order, position), and every R-th of them as a block splitter bound
 //    every block to at most (R + R) * sigma <= B elements (each run
 //    contributes at most (its samples in the block + 1) * sigma elements);
-//  * each block's slice of every run is copied to the device, sorted there
-//    stably (the stable sort of the slices in run order is their stable
-//    merge), and copied to its place in the output; blocks rotate through
-//    the host sort's staging slots and streams, so one block's copy-in, the
-//    previous one's sort and the one before's copy-out overlap.
+//  * each block's slice of every run is copied to the device, merged there
+//    by rounds of the pairwise merge tree over runs of unequal length (ties
+//    to the earlier run, so the result is the stable merge), and copied to
+//    its place in the output; with more runs than the merge kernels' pair
+//    table takes, the slices are instead sorted stably as one array (the
+//    stable sort of the slices in run order is also their stable merge).
+//    Blocks rotate through the host sort's staging slots and streams, so one
+//    block's copy-in, the previous one's merge and the one before's copy-out
+//    overlap.
 // Splitters order equal keys by position, so runs of equal keys split too
 // and the result is the stable sort of the whole array.
 // ---------------------------------------------------------------------------
@@ -818,7 +824,11 @@ static msort_status host_sort_external(msort_ctx* ctx, const K* h_kin, const uin
         if (s != MSORT_OK) return s;
         const size_t need = n * sizeof(K) + (PAIRS ? n * 4 : 0);
         if (hp->runs_bytes < need) {
-            cudaError_t e = cudaStreamSynchronize(st);  // no copy may still use the old buffer
+            // no copy of an earlier call (one that failed part-way included)
+            // may still use the old buffer
+            cudaError_t e = cudaStreamSynchronize(st);
+            for (cudaStream_t q : {hp->h2d, hp->cs, hp->d2h})
+                if (e == cudaSuccess) e = cudaStreamSynchronize(q);
             if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
             if (hp->runs) cudaFreeHost(hp->runs);
             hp->runs = nullptr;
@@ -833,20 +843,31 @@ static msort_status host_sort_external(msort_ctx* ctx, const K* h_kin, const uin
     K* tk = static_cast<K*>(hp->runs);
     uint32_t* tv = PAIRS ? reinterpret_cast<uint32_t*>(tk + n) : nullptr;
     const size_t R = (n + chunk - 1) / chunk;
+    // With at most 2 * kRunPairsMax runs a block's slices are merged on the
+    // device (merge-tree rounds over runs of unequal length, ping-ponging
+    // between the two halves of a staging slot, so a block is at most half a
+    // chunk); with more runs each block is sorted whole.
+    const bool merge_slices = R <= 2 * (size_t)kRunPairsMax;
+    const size_t B = merge_slices ? (chunk / 2) & ~size_t(63) : chunk;
+    if (2 * R > B) return fail(MSORT_ERR_OOM, "the context budget is too small for this many out-of-core runs");
 
-    // 1. sorted runs, one budget-sized chunk at a time
+    // 1. sorted runs, one budget-sized chunk at a time (consecutive chunks
+    //    overlap on the context's streams).  Runs that are merged later keep
+    //    their keys transformed (unsigned order); the last merge round undoes
+    //    the transform.
     for (size_t r = 0; r < R; ++r) {
         const size_t off = r * chunk, len = std::min(chunk, n - off);
         msort_status s = host_sort<K, PAIRS>(ctx, h_kin + off, PAIRS ? h_vin + off : nullptr, tk + off,
-                                             PAIRS ? tv + off : nullptr, len, opt, st, kSyncChunks, kSyncSlices,
-                                             xform);
+                                             PAIRS ? tv + off : nullptr, len, opt, st, kAsyncChunks, kAsyncSlices,
+                                             xform, merge_slices);
         if (s != MSORT_OK) return s;
     }
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
 
-    // 2. splitters from regular samples of the runs
-    const size_t B = chunk;
+    // 2. splitters from regular samples of the runs, compared by (key in
+    //    unsigned order, global position)
+    const int xf_keys = merge_slices ? 0 : xform;  // transform still to apply to the runs' keys
     const size_t sigma = std::max<size_t>(1, B / (2 * R));
     struct Smp {
         K u;
@@ -856,7 +877,7 @@ static msort_status host_sort_external(msort_ctx* ctx, const K* h_kin, const uin
     std::vector<Smp> smp;
     for (size_t r = 0; r < R; ++r) {
         const size_t off = r * chunk, len = std::min(chunk, n - off);
-        for (size_t j = 0; j < len; j += sigma) smp.push_back(Smp{host_order_key(tk[off + j], xform), off + j});
+        for (size_t j = 0; j < len; j += sigma) smp.push_back(Smp{host_order_key(tk[off + j], xf_keys), off + j});
     }
     std::sort(smp.begin(), smp.end(), before);
     std::vector<Smp> spl;
@@ -871,7 +892,7 @@ static msort_status host_sort_external(msort_ctx* ctx, const K* h_kin, const uin
             size_t lo = 0, hi = len;
             while (lo < hi) {
                 const size_t mid = lo + (hi - lo) / 2;
-                if (before(Smp{host_order_key(tk[off + mid], xform), off + mid}, spl[i]))
+                if (before(Smp{host_order_key(tk[off + mid], xf_keys), off + mid}, spl[i]))
                     lo = mid + 1;
                 else
                     hi = mid;
@@ -880,14 +901,16 @@ static msort_status host_sort_external(msort_ctx* ctx, const K* h_kin, const uin
         }
     }
 
-    // 3. every block: slices in, stable sort, out, pipelined through the
-    //    staging slots on the context's copy-in, compute and copy-out streams
-    const size_t kb = align_up(B * sizeof(K), 256);
-    const size_t dbytes = kb + (PAIRS ? align_up(B * 4, 256) : 0);
+    // 3. every block: slices in, merged (or sorted) on the device, out,
+    //    pipelined through the staging slots on the context's copy-in,
+    //    compute and copy-out streams
+    const size_t kb = align_up(B * sizeof(K), 256), vb = PAIRS ? align_up(B * 4, 256) : 0;
+    const size_t dbytes = merge_slices ? 2 * (kb + vb) : kb + vb;
     int slots[kHostSlots], ns = 0;
     for (int i = 0; i < kHostSlots; ++i)
         if (hp->slot_bytes[i] >= dbytes) slots[ns++] = i;
     if (!ns) return fail(MSORT_ERR_CUDA, "no staging slot holds an out-of-core block");
+    const size_t W = merge_two_block<K, PAIRS>();
     msort_options bopt{};  // block sizes differ: no graph per block
     if (opt) bopt = *opt;
     bopt.use_graph = 0;
@@ -899,28 +922,64 @@ static msort_status host_sort_external(msort_ctx* ctx, const K* h_kin, const uin
         if (!len) continue;
         if (len > B) return fail(MSORT_ERR_CUDA, "out-of-core block larger than its bound");
         const int sl = slots[bi++ % ns];
-        K* dk = static_cast<K*>(hp->slot[sl]);
-        uint32_t* dv = PAIRS ? reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(hp->slot[sl]) + kb) : nullptr;
+        unsigned char* base = static_cast<unsigned char*>(hp->slot[sl]);
+        K* dk[2] = {reinterpret_cast<K*>(base), reinterpret_cast<K*>(base + kb + vb)};
+        uint32_t* dv[2] = {PAIRS ? reinterpret_cast<uint32_t*>(base + kb) : nullptr,
+                           PAIRS ? reinterpret_cast<uint32_t*>(base + 2 * kb + vb) : nullptr};
         if (hp->used[sl]) cudaStreamWaitEvent(hp->h2d, hp->done[sl], 0);  // its last block has left
-        size_t pos = 0;
+        std::vector<size_t> ro(1, 0);  // boundaries of the block's non-empty slices
         for (size_t r = 0; r < R; ++r) {
             const size_t off = r * chunk, lo = cut[b * R + r], cnt = cut[(b + 1) * R + r] - lo;
             if (!cnt) continue;
-            e = cudaMemcpyAsync(dk + pos, tk + off + lo, cnt * sizeof(K), cudaMemcpyHostToDevice, hp->h2d);
+            const size_t pos = ro.back();
+            e = cudaMemcpyAsync(dk[0] + pos, tk + off + lo, cnt * sizeof(K), cudaMemcpyHostToDevice, hp->h2d);
             if (e == cudaSuccess && PAIRS)
-                e = cudaMemcpyAsync(dv + pos, tv + off + lo, cnt * 4, cudaMemcpyHostToDevice, hp->h2d);
+                e = cudaMemcpyAsync(dv[0] + pos, tv + off + lo, cnt * 4, cudaMemcpyHostToDevice, hp->h2d);
             if (e != cudaSuccess) return cuda_fail(e, "host to device copy");
-            pos += cnt;
+            ro.push_back(pos + cnt);
         }
         cudaEventRecord(hp->in_ev[sl][0], hp->h2d);
         cudaStreamWaitEvent(hp->cs, hp->in_ev[sl][0], 0);
-        msort_status s = sort_entry<K, PAIRS>(ctx, dk, dv, dk, dv, len, &bopt, hp->cs, xform);
-        if (s != MSORT_OK) return s;
+        int fin = 0;  // half of the slot that holds the block's result
+        if (merge_slices) {
+            // merge-tree rounds over the slices (at least one, which undoes
+            // the key transform)
+            const size_t runs = ro.size() - 1;
+            int rounds = 0;
+            while (((size_t)1 << rounds) < runs) ++rounds;
+            if (rounds == 0) rounds = 1;
+            std::lock_guard<std::mutex> g(ctx->mu);
+            msort_status s = ensure_scratch(ctx, (B / W + kRunPairsMax + 2) * sizeof(unsigned long long), hp->cs);
+            if (s != MSORT_OK) return s;
+            unsigned long long* splits = static_cast<unsigned long long*>(ctx->scratch);
+            for (int lv = 0; lv < rounds; ++lv) {
+                const size_t gsz = (size_t)1 << lv;
+                RunPairs rp{};
+                rp.np = (int)((runs + 2 * gsz - 1) / (2 * gsz));
+                rp.c[0] = 0;
+                for (int j = 0; j < rp.np; ++j) {
+                    rp.p[j] = ro[std::min(2 * j * gsz, runs)];
+                    rp.m[j] = ro[std::min((2 * j + 1) * gsz, runs)];
+                    rp.p[j + 1] = ro[std::min((2 * j + 2) * gsz, runs)];
+                    rp.c[j + 1] = rp.c[j] + (rp.p[j + 1] - rp.p[j] + W - 1) / W;
+                }
+                const bool lastr = lv + 1 == rounds;
+                e = launch_merge_runs<K, PAIRS>(dk[fin], dk[fin ^ 1], dv[fin], dv[fin ^ 1], rp, splits,
+                                                ctx->d_status, lastr ? xform : 0, hp->cs);
+                ctx->launches += 2;
+                if (e != cudaSuccess) return cuda_fail(e, ("run merge launch" + last_launch_info()).c_str());
+                fin ^= 1;
+            }
+            scratch_release(ctx, hp->cs);
+        } else {
+            msort_status s = sort_entry<K, PAIRS>(ctx, dk[0], dv[0], dk[0], dv[0], len, &bopt, hp->cs, xform);
+            if (s != MSORT_OK) return s;
+        }
         cudaEventRecord(hp->out_ev[sl][0], hp->cs);
         cudaStreamWaitEvent(hp->d2h, hp->out_ev[sl][0], 0);
-        e = cudaMemcpyAsync(h_kout + out, dk, len * sizeof(K), cudaMemcpyDeviceToHost, hp->d2h);
+        e = cudaMemcpyAsync(h_kout + out, dk[fin], len * sizeof(K), cudaMemcpyDeviceToHost, hp->d2h);
         if (e == cudaSuccess && PAIRS)
-            e = cudaMemcpyAsync(h_vout + out, dv, len * 4, cudaMemcpyDeviceToHost, hp->d2h);
+            e = cudaMemcpyAsync(h_vout + out, dv[fin], len * 4, cudaMemcpyDeviceToHost, hp->d2h);
         if (e != cudaSuccess) return cuda_fail(e, "device to host copy");
         cudaEventRecord(hp->done[sl], hp->d2h);
         hp->used[sl] = true;

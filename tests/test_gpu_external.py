@@ -3,9 +3,12 @@
 A context whose device budget is smaller than the in-core host sort of n
 elements sorts host arrays in budget-sized chunks (sorted runs in a
 pinned host buffer) and merges the runs in blocks bounded by sampled
-(key, position) splitters.  Checked: a couple and many runs, ragged runs,
-all-equal keys (runs of equal keys are split by position), 64-bit pairs
-(stability through the values) and floating-point keys.
+(key, position) splitters, merging each block's slices on the device.
+Checked: a couple and many runs, ragged runs, all-equal keys (runs of equal
+keys are split by position), 64-bit pairs (stability through the values),
+floating-point keys (kept transformed between the phases), presorted input
+(blocks of one slice) and more runs than the run-merge kernels take (blocks
+sorted whole).
 """
 import numpy as np
 import pytest
@@ -85,6 +88,49 @@ def test_float_keys_and_async_call():
         ms.msort_sort_host_async(c.handle, hin, out_keys=hout)
         ms.msort_ctx_sync(c.handle)
         assert np.array_equal(_bits(hout.numpy()), _bits(exp))
+    finally:
+        c.close()
+
+
+def test_many_runs_sort_whole_blocks():
+    # a 3 MiB budget gives chunks of about 2^16.4 keys, so 8e6 keys make more
+    # runs than the run-merge kernels' pair table takes: every block is then
+    # sorted whole instead of merged
+    need_gpu()
+    c = ms.Context(0, scratch_budget_bytes=3 << 20)
+    try:
+        n = 8_000_009
+        keys = synth.uniform_u32(n, 11)
+        keys[::7] = keys[3]
+        exp, _ = oracle.sort(keys)
+        hin, hout = _pinned(keys), _pinned(np.zeros_like(keys))
+        ms.msort_sort_host(c.handle, hin, out_keys=hout)
+        assert np.array_equal(hout.numpy(), exp)
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("order", ["ascending", "descending"])
+def test_presorted_float_pairs(order):
+    # ascending input puts one slice in most blocks (only the copy round,
+    # which undoes the key transform, runs); descending input spreads every
+    # block over all runs
+    c = _ctx(16)
+    try:
+        n = 3_500_017
+        rng = np.random.default_rng(8)
+        keys = np.sort(rng.standard_normal(n).astype(np.float32))
+        keys[keys == 0] = 1.0
+        keys[::11] = keys[5]  # duplicates: stability through the values
+        keys = np.sort(keys)
+        if order == "descending":
+            keys = keys[::-1].copy()
+        vals = np.arange(n, dtype=np.uint32)
+        ek, ev = oracle.sort(keys, vals)
+        hk, hv = _pinned(keys), _pinned(vals)
+        ok, ov = _pinned(np.zeros_like(keys)), _pinned(np.zeros_like(vals))
+        ms.msort_sort_host(c.handle, hk, hv, out_keys=ok, out_vals=ov)
+        assert np.array_equal(_bits(ok.numpy()), _bits(ek)) and np.array_equal(ov.numpy(), ev)
     finally:
         c.close()
 
