@@ -764,8 +764,8 @@ static msort_status host_sort(msort_ctx* ctx, const void* h_kin_v, const uint32_
 // sorted in chunks that fit (each by the pipelined host sort, into a pinned
 // host buffer of sorted runs) and the runs are merged in blocks that fit:
 //  * regular samples, every sigma-th element of every run, sorted by
-//    (key order, position), and every R-th of them as a block splitter bound
-//    every block to at most (R + R) * sigma <= B elements (each run
+//    (key order, position), and every m-th of them as a block splitter bound
+//    every block to at most (m + R) * sigma <= B elements (each run
 //    contributes at most (its samples in the block + 1) * sigma elements);
 //  * each block's slice of every run is copied to the device, merged there
 //    by rounds of the pairwise merge tree over runs of unequal length (ties
@@ -868,7 +868,14 @@ static msort_status host_sort_external(msort_ctx* ctx, const K* h_kin, const uin
     // 2. splitters from regular samples of the runs, compared by (key in
     //    unsigned order, global position)
     const int xf_keys = merge_slices ? 0 : xform;  // transform still to apply to the runs' keys
-    const size_t sigma = std::max<size_t>(1, B / (2 * R));
+    // A block from one splitter sample to the next holding m samples has at
+    // most (m + R) * sigma elements (each run adds at most one unsampled
+    // stretch of sigma - 1), so splitters every m = (k - 1) R samples with
+    // sigma = B / (k R) keep blocks within B while their expected size is
+    // (1 - 1/k) B: k = 16 when sigma stays >= 1, else 2.
+    const size_t kover = 16 * R <= B ? 16 : 2;
+    const size_t sigma = std::max<size_t>(1, B / (kover * R));
+    const size_t every = (kover - 1) * R;
     struct Smp {
         K u;
         size_t g;
@@ -881,7 +888,7 @@ static msort_status host_sort_external(msort_ctx* ctx, const K* h_kin, const uin
     }
     std::sort(smp.begin(), smp.end(), before);
     std::vector<Smp> spl;
-    for (size_t i = R; i < smp.size(); i += R) spl.push_back(smp[i]);
+    for (size_t i = every; i < smp.size(); i += every) spl.push_back(smp[i]);
     const size_t nb = spl.size() + 1;  // blocks
     std::vector<size_t> cut((nb + 1) * R);
     for (size_t r = 0; r < R; ++r) {
