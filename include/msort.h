@@ -61,7 +61,7 @@ typedef enum {
  * order.  Signed and floating-point keys are accepted by msort_sort,
  * msort_sort_pairs, msort_sort_copy, msort_sort_host(_async),
  * msort_segmented_sort, msort_scratch_bytes and the plan queries, with
- * partition_mode 0 and pairwise passes; msort_merge, msort_sort_noalloc and
+ * partition_mode 0 and pairwise passes; msort_merge, msort_merge_runs, msort_sort_noalloc and
  * the server return MSORT_ERR_UNSUPPORTED for them.  They are sorted as unsigned keys after an order-preserving bit
  * transform that the tile sort applies as it reads the input and the last
  * merge round undoes as it writes the output (no extra pass over memory). */
@@ -174,6 +174,21 @@ msort_status msort_segmented_sort(msort_ctx* ctx, void* d_keys, uint32_t* d_vals
 msort_status msort_merge(msort_ctx* ctx, const void* d_a, const uint32_t* d_va, size_t na, const void* d_b,
                          const uint32_t* d_vb, size_t nb, void* d_out, uint32_t* d_vout, msort_key_type kt,
                          void* stream);
+
+/* Stable merge of nruns sorted runs laid end to end: run i of d_keys (and
+ * d_vals) is [offsets[i], offsets[i+1]), where offsets is a host array of
+ * nruns + 1 non-decreasing element counts starting at 0; empty runs are
+ * allowed.  The merged array (equal keys in run order, values alongside)
+ * goes to d_out (and d_vout; give both value pointers or neither), which must
+ * not overlap the input.  It runs ceil(log2(non-empty runs)) rounds of the
+ * pairwise merge tree (Section "Parallel Merge Sort": one round merges runs
+ * 2j and 2j + 1 for every j), each a partition and a merge launch per 32
+ * pairs; a second buffer of offsets[nruns] elements comes from the
+ * context's scratch.  Unsigned key types only (MSORT_ERR_UNSUPPORTED for the
+ * others); MSORT_ERR_INVALID_ARG for decreasing offsets or overlapping
+ * buffers.  The runs must be sorted (not checked). */
+msort_status msort_merge_runs(msort_ctx* ctx, const void* d_keys, const uint32_t* d_vals, const uint64_t* offsets,
+                              size_t nruns, void* d_out, uint32_t* d_vout, msort_key_type kt, void* stream);
 
 /* Host-buffer sort: copies h_keys_in (and h_vals_in, nullable) to the
  * device, sorts there, and copies the result to h_keys_out (and h_vals_out;

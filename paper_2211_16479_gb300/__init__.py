@@ -58,6 +58,7 @@ _SIGS = {
     "msort_sort_host": ([_P, _P, _P, _P, _P, _SZ, _I, _OPT, _P], _ST),
     "msort_sort_host_async": ([_P, _P, _P, _P, _P, _SZ, _I, _OPT, _P], _ST),
     "msort_merge": ([_P, _P, _P, _SZ, _P, _P, _SZ, _P, _P, _I, _P], _ST),
+    "msort_merge_runs": ([_P, _P, _P, _P, _SZ, _P, _P, _I, _P], _ST),
     "msort_segmented_sort": ([_P, _P, _P, _P, _SZ, _SZ, _I, _OPT, _P], _ST),
     "msort_sort_noalloc": ([_P, _P, _P, _P, _SZ, _I, _P], _ST),
     "msort_noalloc_max_keys": ([_I, _I], _SZ),
@@ -249,6 +250,17 @@ def msort_merge(ctx, a, b, out, va=None, vb=None, vout=None, key_type=None, stre
     _check(ctx, load_library().msort_merge(ctx, _ptr(a), _ptr(va), _numel(a, None), _ptr(b), _ptr(vb),
                                            _numel(b, None), _ptr(out), _ptr(vout), _key_type(a, key_type),
                                            _stream(stream, out)))
+
+
+def msort_merge_runs(ctx, keys, offsets, out, vals=None, out_vals=None, key_type=None, stream=None) -> None:
+    """out = stable merge of the sorted runs keys[offsets[i]:offsets[i+1]]
+    laid end to end (ties in run order); offsets: host sequence of
+    nruns + 1 counts starting at 0."""
+    import numpy as np
+    offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.uint64))
+    _check(ctx, load_library().msort_merge_runs(ctx, _ptr(keys), _ptr(vals), offs.ctypes.data, max(len(offs) - 1, 0),
+                                                _ptr(out), _ptr(out_vals), _key_type(keys, key_type),
+                                                _stream(stream, out)))
 
 
 def msort_sort_host(ctx, keys, vals=None, out_keys=None, out_vals=None, n=None, key_type=None,

@@ -758,6 +758,47 @@ static msort_status host_sort(msort_ctx* ctx, const void* h_kin_v, const uint32_
 }
 
 // ---------------------------------------------------------------------------
+// One round of the merge tree over sorted runs of arbitrary lengths laid end
+// to end (boundaries ro, at least one run): runs 2j and 2j + 1 merge from src
+// into the same positions of dst, up to kRunPairsMax pairs per launch pair;
+// ro becomes the boundaries of the merged runs.  xf_out: key transform the
+// round undoes as it writes.
+// ---------------------------------------------------------------------------
+template <class K, bool PAIRS>
+static msort_status merge_runs_round(msort_ctx* ctx, const K* src, K* dst, const uint32_t* vsrc, uint32_t* vdst,
+                                     std::vector<size_t>& ro, unsigned long long* splits, int xf_out,
+                                     cudaStream_t st) {
+    const size_t W = merge_two_block<K, PAIRS>();
+    const size_t runs = ro.size() - 1;
+    const size_t np = (runs + 1) / 2;
+    for (size_t j0 = 0; j0 < np; j0 += kRunPairsMax) {
+        RunPairs rp{};
+        rp.np = (int)std::min<size_t>(kRunPairsMax, np - j0);
+        for (int j = 0; j < rp.np; ++j) {
+            const size_t a = 2 * (j0 + j);
+            rp.p[j] = ro[a];
+            rp.m[j] = ro[std::min(a + 1, runs)];
+            rp.p[j + 1] = ro[std::min(a + 2, runs)];
+            rp.c[j + 1] = rp.c[j] + (rp.p[j + 1] - rp.p[j] + W - 1) / W;
+        }
+        const cudaError_t e = launch_merge_runs<K, PAIRS>(src, dst, vsrc, vdst, rp, splits, ctx->d_status, xf_out, st);
+        ctx->launches += 2;
+        if (e != cudaSuccess) return cuda_fail(e, ("run merge launch" + last_launch_info()).c_str());
+    }
+    std::vector<size_t> next;
+    for (size_t i = 0; i < runs; i += 2) next.push_back(ro[i]);
+    next.push_back(ro[runs]);
+    ro.swap(next);
+    return MSORT_OK;
+}
+
+// Split table entries one round over `len` elements in runs may need.
+template <class K, bool PAIRS>
+static size_t merge_runs_splits(size_t len) {
+    return len / merge_two_block<K, PAIRS>() + kRunPairsMax + 2;
+}
+
+// ---------------------------------------------------------------------------
 // Host arrays larger than the device budget: an external merge sort.  The
 // context's budget (msort_ctx_create) caps the device memory a sort may use;
 // when the pipelined host sort of n elements would exceed it, the array is
@@ -770,23 +811,12 @@ static msort_status host_sort(msort_ctx* ctx, const void* h_kin_v, const uint32_
 //  * each block's slice of every run is copied to the device, merged there
 //    by rounds of the pairwise merge tree over runs of unequal length (ties
 //    to the earlier run, so the result is the stable merge), and copied to
-//    its place in the output; with more runs than the merge kernels' pair
-//    table takes, the slices are instead sorted stably as one array (the
-//    stable sort of the slices in run order is also their stable merge).
-//    Blocks rotate through the host sort's staging slots and streams, so one
+//    its place in the output.  Blocks rotate through the host sort's staging slots and streams, so one
 //    block's copy-in, the previous one's merge and the one before's copy-out
 //    overlap.
 // Splitters order equal keys by position, so runs of equal keys split too
 // and the result is the stable sort of the whole array.
 // ---------------------------------------------------------------------------
-template <class K>
-static inline K host_order_key(K k, int xform) {  // the order-preserving map of the kernels
-    constexpr K sign = K(1) << (8 * sizeof(K) - 1);
-    if (xform == 1) return k ^ sign;
-    if (xform == 2) return (k & sign) ? K(~k) : K(k ^ sign);
-    return k;
-}
-
 // Device bytes the pipelined host sort of n elements may hold (three
 // staging slots and the sort scratch).
 template <class K, bool PAIRS>
@@ -843,23 +873,20 @@ static msort_status host_sort_external(msort_ctx* ctx, const K* h_kin, const uin
     K* tk = static_cast<K*>(hp->runs);
     uint32_t* tv = PAIRS ? reinterpret_cast<uint32_t*>(tk + n) : nullptr;
     const size_t R = (n + chunk - 1) / chunk;
-    // With at most 2 * kRunPairsMax runs a block's slices are merged on the
-    // device (merge-tree rounds over runs of unequal length, ping-ponging
-    // between the two halves of a staging slot, so a block is at most half a
-    // chunk); with more runs each block is sorted whole.
-    const bool merge_slices = R <= 2 * (size_t)kRunPairsMax;
-    const size_t B = merge_slices ? (chunk / 2) & ~size_t(63) : chunk;
+    // A block is at most half a chunk: its merge rounds ping-pong between the
+    // two halves of a staging slot.
+    const size_t B = (chunk / 2) & ~size_t(63);
     if (2 * R > B) return fail(MSORT_ERR_OOM, "the context budget is too small for this many out-of-core runs");
 
     // 1. sorted runs, one budget-sized chunk at a time (consecutive chunks
-    //    overlap on the context's streams).  Runs that are merged later keep
-    //    their keys transformed (unsigned order); the last merge round undoes
-    //    the transform.
+    //    overlap on the context's streams).  The runs keep their keys
+    //    transformed (unsigned order); the last merge round undoes the
+    //    transform.
     for (size_t r = 0; r < R; ++r) {
         const size_t off = r * chunk, len = std::min(chunk, n - off);
         msort_status s = host_sort<K, PAIRS>(ctx, h_kin + off, PAIRS ? h_vin + off : nullptr, tk + off,
                                              PAIRS ? tv + off : nullptr, len, opt, st, kAsyncChunks, kAsyncSlices,
-                                             xform, merge_slices);
+                                             xform, true);
         if (s != MSORT_OK) return s;
     }
     cudaError_t e = cudaStreamSynchronize(st);
@@ -867,7 +894,6 @@ static msort_status host_sort_external(msort_ctx* ctx, const K* h_kin, const uin
 
     // 2. splitters from regular samples of the runs, compared by (key in
     //    unsigned order, global position)
-    const int xf_keys = merge_slices ? 0 : xform;  // transform still to apply to the runs' keys
     // A block from one splitter sample to the next holding m samples has at
     // most (m + R) * sigma elements (each run adds at most one unsampled
     // stretch of sigma - 1), so splitters every m = (k - 1) R samples with
@@ -884,7 +910,7 @@ static msort_status host_sort_external(msort_ctx* ctx, const K* h_kin, const uin
     std::vector<Smp> smp;
     for (size_t r = 0; r < R; ++r) {
         const size_t off = r * chunk, len = std::min(chunk, n - off);
-        for (size_t j = 0; j < len; j += sigma) smp.push_back(Smp{host_order_key(tk[off + j], xf_keys), off + j});
+        for (size_t j = 0; j < len; j += sigma) smp.push_back(Smp{tk[off + j], off + j});
     }
     std::sort(smp.begin(), smp.end(), before);
     std::vector<Smp> spl;
@@ -899,7 +925,7 @@ static msort_status host_sort_external(msort_ctx* ctx, const K* h_kin, const uin
             size_t lo = 0, hi = len;
             while (lo < hi) {
                 const size_t mid = lo + (hi - lo) / 2;
-                if (before(Smp{host_order_key(tk[off + mid], xf_keys), off + mid}, spl[i]))
+                if (before(Smp{tk[off + mid], off + mid}, spl[i]))
                     lo = mid + 1;
                 else
                     hi = mid;
@@ -908,19 +934,14 @@ static msort_status host_sort_external(msort_ctx* ctx, const K* h_kin, const uin
         }
     }
 
-    // 3. every block: slices in, merged (or sorted) on the device, out,
-    //    pipelined through the staging slots on the context's copy-in,
-    //    compute and copy-out streams
+    // 3. every block: slices in, merged on the device, out, pipelined
+    //    through the staging slots on the context's copy-in, compute and
+    //    copy-out streams
     const size_t kb = align_up(B * sizeof(K), 256), vb = PAIRS ? align_up(B * 4, 256) : 0;
-    const size_t dbytes = merge_slices ? 2 * (kb + vb) : kb + vb;
     int slots[kHostSlots], ns = 0;
     for (int i = 0; i < kHostSlots; ++i)
-        if (hp->slot_bytes[i] >= dbytes) slots[ns++] = i;
+        if (hp->slot_bytes[i] >= 2 * (kb + vb)) slots[ns++] = i;
     if (!ns) return fail(MSORT_ERR_CUDA, "no staging slot holds an out-of-core block");
-    const size_t W = merge_two_block<K, PAIRS>();
-    msort_options bopt{};  // block sizes differ: no graph per block
-    if (opt) bopt = *opt;
-    bopt.use_graph = 0;
     size_t out = 0, bi = 0;
     int last = -1;
     for (size_t b = 0; b < nb; ++b) {
@@ -947,40 +968,22 @@ static msort_status host_sort_external(msort_ctx* ctx, const K* h_kin, const uin
         }
         cudaEventRecord(hp->in_ev[sl][0], hp->h2d);
         cudaStreamWaitEvent(hp->cs, hp->in_ev[sl][0], 0);
+        // merge-tree rounds over the slices (at least one, which undoes the
+        // key transform)
         int fin = 0;  // half of the slot that holds the block's result
-        if (merge_slices) {
-            // merge-tree rounds over the slices (at least one, which undoes
-            // the key transform)
-            const size_t runs = ro.size() - 1;
-            int rounds = 0;
-            while (((size_t)1 << rounds) < runs) ++rounds;
-            if (rounds == 0) rounds = 1;
+        {
             std::lock_guard<std::mutex> g(ctx->mu);
-            msort_status s = ensure_scratch(ctx, (B / W + kRunPairsMax + 2) * sizeof(unsigned long long), hp->cs);
+            msort_status s = ensure_scratch(ctx, merge_runs_splits<K, PAIRS>(B) * sizeof(unsigned long long), hp->cs);
             if (s != MSORT_OK) return s;
             unsigned long long* splits = static_cast<unsigned long long*>(ctx->scratch);
-            for (int lv = 0; lv < rounds; ++lv) {
-                const size_t gsz = (size_t)1 << lv;
-                RunPairs rp{};
-                rp.np = (int)((runs + 2 * gsz - 1) / (2 * gsz));
-                rp.c[0] = 0;
-                for (int j = 0; j < rp.np; ++j) {
-                    rp.p[j] = ro[std::min(2 * j * gsz, runs)];
-                    rp.m[j] = ro[std::min((2 * j + 1) * gsz, runs)];
-                    rp.p[j + 1] = ro[std::min((2 * j + 2) * gsz, runs)];
-                    rp.c[j + 1] = rp.c[j] + (rp.p[j + 1] - rp.p[j] + W - 1) / W;
-                }
-                const bool lastr = lv + 1 == rounds;
-                e = launch_merge_runs<K, PAIRS>(dk[fin], dk[fin ^ 1], dv[fin], dv[fin ^ 1], rp, splits,
-                                                ctx->d_status, lastr ? xform : 0, hp->cs);
-                ctx->launches += 2;
-                if (e != cudaSuccess) return cuda_fail(e, ("run merge launch" + last_launch_info()).c_str());
+            do {
+                const bool lastr = ro.size() <= 3;
+                s = merge_runs_round<K, PAIRS>(ctx, dk[fin], dk[fin ^ 1], dv[fin], dv[fin ^ 1], ro, splits,
+                                               lastr ? xform : 0, hp->cs);
+                if (s != MSORT_OK) return s;
                 fin ^= 1;
-            }
+            } while (ro.size() > 2);
             scratch_release(ctx, hp->cs);
-        } else {
-            msort_status s = sort_entry<K, PAIRS>(ctx, dk[0], dv[0], dk[0], dv[0], len, &bopt, hp->cs, xform);
-            if (s != MSORT_OK) return s;
         }
         cudaEventRecord(hp->out_ev[sl][0], hp->cs);
         cudaStreamWaitEvent(hp->d2h, hp->out_ev[sl][0], 0);
@@ -1018,6 +1021,45 @@ static msort_status host_sort_any(msort_ctx* ctx, const void* h_kin, const uint3
         }
     }
     return host_sort<K, PAIRS>(ctx, h_kin, h_vin, h_kout, h_vout, n, opt, st, chunks, slices, xform);
+}
+
+// msort_merge_runs: rounds of the merge tree from d_in to out, the second
+// buffer in scratch; round r writes out when rounds - 1 - r is even, so the
+// last round lands in out and the input is only read.
+template <class K, bool PAIRS>
+static msort_status merge_runs_entry(msort_ctx* ctx, const K* in, const uint32_t* vin, std::vector<size_t> ro,
+                                     K* out, uint32_t* vout, cudaStream_t st) {
+    std::vector<size_t> nz(1, 0);  // drop empty runs
+    for (size_t i = 1; i < ro.size(); ++i)
+        if (ro[i] != nz.back()) nz.push_back(ro[i]);
+    ro.swap(nz);
+    const size_t n = ro.back();
+    int rounds = 0;
+    while (((size_t)1 << rounds) < ro.size() - 1) ++rounds;
+    if (rounds == 0) rounds = 1;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    const size_t kbytes = rounds > 1 ? align_up(n * sizeof(K), 256) : 0;
+    const size_t vbytes = rounds > 1 && PAIRS ? align_up(n * 4, 256) : 0;
+    msort_status s =
+        ensure_scratch(ctx, kbytes + vbytes + merge_runs_splits<K, PAIRS>(n) * sizeof(unsigned long long), st);
+    if (s != MSORT_OK) return s;
+    unsigned char* sp = static_cast<unsigned char*>(ctx->scratch);
+    K* tgt[2] = {out, reinterpret_cast<K*>(sp)};
+    uint32_t* vtgt[2] = {vout, PAIRS ? reinterpret_cast<uint32_t*>(sp + kbytes) : nullptr};
+    unsigned long long* splits = reinterpret_cast<unsigned long long*>(sp + kbytes + vbytes);
+    const K* src = in;
+    const uint32_t* vsrc = vin;
+    for (int r = 0; r < rounds; ++r) {
+        const int w = (rounds - 1 - r) & 1;
+        s = merge_runs_round<K, PAIRS>(ctx, src, tgt[w], vsrc, vtgt[w], ro, splits, 0, st);
+        if (s != MSORT_OK) break;
+        src = tgt[w];
+        vsrc = vtgt[w];
+    }
+    scratch_release(ctx, st);
+    return s;
 }
 
 }  // namespace msort
@@ -1185,6 +1227,44 @@ msort_status msort_merge(msort_ctx* ctx, const void* d_a, const uint32_t* d_va, 
     if (e != cudaSuccess) return cuda_fail(e, ("merge launch" + last_launch_info()).c_str());
     (void)ks;
     return MSORT_OK;
+}
+
+msort_status msort_merge_runs(msort_ctx* ctx, const void* d_keys, const uint32_t* d_vals, const uint64_t* offsets,
+                              size_t nruns, void* d_out, uint32_t* d_vout, msort_key_type kt, void* stream) {
+    msort_status s = check_common(ctx, kt, nullptr);
+    if (s != MSORT_OK) return s;
+    if (key_xform(kt))
+        return fail(MSORT_ERR_UNSUPPORTED, "msort_merge_runs takes unsigned keys (signed and floating-point keys: "
+                                           "the plain and host-buffer sorts)");
+    if (nruns == 0) return MSORT_OK;
+    if (!offsets) return fail(MSORT_ERR_INVALID_ARG, "offsets is NULL");
+    if (offsets[0] != 0) return fail(MSORT_ERR_INVALID_ARG, "offsets[0] must be 0");
+    std::vector<size_t> ro(nruns + 1);
+    for (size_t i = 0; i <= nruns; ++i) {
+        if (i && offsets[i] < offsets[i - 1]) return fail(MSORT_ERR_INVALID_ARG, "offsets must not decrease");
+        ro[i] = (size_t)offsets[i];
+    }
+    const size_t n = ro[nruns];
+    if (n == 0) return MSORT_OK;
+    if (!d_keys || !d_out) return fail(MSORT_ERR_INVALID_ARG, "key pointer is NULL");
+    if ((d_vals == nullptr) != (d_vout == nullptr)) return fail(MSORT_ERR_INVALID_ARG, "give both value pointers or none");
+    const size_t ks = key_bytes(kt);
+    const uintptr_t ki = reinterpret_cast<uintptr_t>(d_keys), ko = reinterpret_cast<uintptr_t>(d_out);
+    if (ki < ko + n * ks && ko < ki + n * ks) return fail(MSORT_ERR_INVALID_ARG, "d_out overlaps d_keys");
+    if (d_vals) {
+        const uintptr_t vi = reinterpret_cast<uintptr_t>(d_vals), vo = reinterpret_cast<uintptr_t>(d_vout);
+        if (vi < vo + n * 4 && vo < vi + n * 4) return fail(MSORT_ERR_INVALID_ARG, "d_vout overlaps d_vals");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (ks == 4)
+        return d_vals ? merge_runs_entry<uint32_t, true>(ctx, static_cast<const uint32_t*>(d_keys), d_vals, ro,
+                                                         static_cast<uint32_t*>(d_out), d_vout, st)
+                      : merge_runs_entry<uint32_t, false>(ctx, static_cast<const uint32_t*>(d_keys), nullptr, ro,
+                                                          static_cast<uint32_t*>(d_out), nullptr, st);
+    return d_vals ? merge_runs_entry<uint64_t, true>(ctx, static_cast<const uint64_t*>(d_keys), d_vals, ro,
+                                                     static_cast<uint64_t*>(d_out), d_vout, st)
+                  : merge_runs_entry<uint64_t, false>(ctx, static_cast<const uint64_t*>(d_keys), nullptr, ro,
+                                                      static_cast<uint64_t*>(d_out), nullptr, st);
 }
 
 msort_status msort_sort(msort_ctx* ctx, void* d_keys, size_t n, msort_key_type kt, const msort_options* opt,

@@ -159,6 +159,18 @@ def _gpu_merge_pairs(ctx):
     return merge
 
 
+def _gpu_merge_runs(ctx):
+    import paper_2211_16479_gb300 as ms
+
+    def merge_runs(k, v, offsets):
+        out = torch.empty_like(k)
+        vout = None if v is None else torch.empty_like(v)
+        if k.numel():
+            ms.msort_merge_runs(ctx, k, offsets, out, vals=v, out_vals=vout)
+        return out, vout
+    return merge_runs
+
+
 def _split_points(keys: np.ndarray, gpos: np.ndarray, sk: np.ndarray, sg: np.ndarray) -> np.ndarray:
     """For each splitter (sk[t], sg[t]), the number of local elements ordered
     before it: keys below sk[t], plus those equal to it whose global position
@@ -172,19 +184,24 @@ def _split_points(keys: np.ndarray, gpos: np.ndarray, sk: np.ndarray, sg: np.nda
 
 
 def sample_sort(local: torch.Tensor, vals: torch.Tensor | None = None, ctx=None, local_sort=None, merge=None,
-                oversample: int = 16):
+                oversample: int = 16, merge_runs=None):
     """Stable sort of the concatenation (in rank order) of every rank's
     ``local`` chunk (and ``vals`` alongside).  Returns this rank's slice
     (keys, vals): the slices, concatenated in rank order, are the sorted
     array.  ``local_sort(k, v) -> (k, v)`` sorts by key, stably, carrying
-    uint32 values; ``merge(a, va, b, vb) -> (c, vc)`` is the stable merge
-    (ties from a; va, vb may be None).  Both default to the library's GPU
-    kernels through ``ctx``.  Chunks must hold fewer than 2^31 elements."""
-    if local_sort is None or merge is None:
+    uint32 values.  The p received pieces are merged either by
+    ``merge_runs(k, v, offsets) -> (k, v)``, the stable merge of sorted runs
+    laid end to end, or, when only ``merge(a, va, b, vb) -> (c, vc)`` (the
+    stable merge of two, ties from a) is given, by a pairwise tree of it.
+    Both default to the library's GPU kernels through ``ctx``
+    (``msort_merge_runs``: every round of the tree in one launch pair).
+    Chunks must hold fewer than 2^31 elements."""
+    if local_sort is None or (merge is None and merge_runs is None):
         if ctx is None:
             raise ValueError("a msort context is needed for the GPU local sort and merges")
         local_sort = local_sort or _gpu_sort_pairs(ctx)
-        merge = merge or _gpu_merge_pairs(ctx)
+        if merge is None and merge_runs is None:
+            merge_runs = _gpu_merge_runs(ctx)
     rank, world = tdist.get_rank(), tdist.get_world_size()
     dev = local.device
     # the collectives run on the device for NCCL, on the host for gloo
@@ -241,6 +258,10 @@ def sample_sort(local: torch.Tensor, vals: torch.Tensor | None = None, ctx=None,
     got_v = None if vals is None else exchange(sv_local)
 
     # 4. p sorted pieces in source-rank order: the pairwise merge tree
+    if merge_runs is not None:
+        k = _from_wire(got_k, local).to(dev)
+        v = None if vals is None else _from_wire(got_v, vals).to(dev)
+        return merge_runs(k, v, np.concatenate([[0], np.cumsum(recv_l)]).astype(np.uint64))
     pieces, o = [], 0
     for c in recv_l:
         k = _from_wire(got_k[o:o + c], local).to(dev)

@@ -144,6 +144,17 @@ def _oracle_merge_pairs(a, va, b, vb):
     return torch.from_numpy(k), (None if v is None else torch.from_numpy(v))
 
 
+def _oracle_merge_runs(k, v, offsets):
+    # the pairwise tree of oracle merges over the runs laid end to end
+    offs = [int(x) for x in offsets]
+    pieces = [(k[a:b].numpy(), None if v is None else v[a:b].numpy()) for a, b in zip(offs, offs[1:])]
+    while len(pieces) > 1:
+        pieces = [oracle.merge(pieces[i][0], pieces[i + 1][0], pieces[i][1], pieces[i + 1][1])
+                  if i + 1 < len(pieces) else pieces[i] for i in range(0, len(pieces), 2)]
+    mk, mv = pieces[0]
+    return torch.from_numpy(mk), (None if mv is None else torch.from_numpy(mv))
+
+
 def _sample_keys(kind, n):
     if kind == "uniform":
         return synth.uniform_u64(n, 5)
@@ -152,7 +163,7 @@ def _sample_keys(kind, n):
     return np.full(n, 7, dtype=np.uint64)  # all equal
 
 
-def _sample_worker(rank, world, port, n, kind, q):
+def _sample_worker(rank, world, port, n, kind, q, runs=False):
     _init(rank, world, port)
     try:
         keys = _sample_keys(kind, n)
@@ -163,7 +174,10 @@ def _sample_worker(rank, world, port, n, kind, q):
             cuts[1] = cuts[0]  # rank 0 holds nothing
         lk = torch.from_numpy(keys[cuts[rank]:cuts[rank + 1]].copy())
         lv = torch.from_numpy(vals[cuts[rank]:cuts[rank + 1]].copy())
-        k, v = dist.sample_sort(lk, lv, local_sort=_oracle_sort_pairs, merge=_oracle_merge_pairs)
+        if runs:
+            k, v = dist.sample_sort(lk, lv, local_sort=_oracle_sort_pairs, merge_runs=_oracle_merge_runs)
+        else:
+            k, v = dist.sample_sort(lk, lv, local_sort=_oracle_sort_pairs, merge=_oracle_merge_pairs)
         parts = [None] * world
         tdist.all_gather_object(parts, (k.numpy(), v.numpy()))
         if rank == 0:
@@ -192,3 +206,20 @@ def test_sample_sort_cpu_ranks(world, kind):
     same, balanced, sizes = q.get(timeout=5)
     assert same, sizes
     assert balanced, sizes  # (key, position) splitters split runs of equal keys too
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sample_sort_cpu_ranks_merge_runs(world):
+    # the received pieces merged by one merge_runs call (the GPU default)
+    ctx = tmp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_sample_worker, args=(r, world, port, 20011, "dup16", q, True))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+    assert all(p.exitcode == 0 for p in procs)
+    same, balanced, sizes = q.get(timeout=5)
+    assert same and balanced, sizes

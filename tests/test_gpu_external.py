@@ -7,8 +7,7 @@ pinned host buffer) and merges the runs in blocks bounded by sampled
 Checked: a couple and many runs, ragged runs, all-equal keys (runs of equal
 keys are split by position), 64-bit pairs (stability through the values),
 floating-point keys (kept transformed between the phases), presorted input
-(blocks of one slice) and more runs than the run-merge kernels take (blocks
-sorted whole).
+(blocks of one slice) and more runs than one run-merge launch takes.
 """
 import numpy as np
 import pytest
@@ -92,10 +91,9 @@ def test_float_keys_and_async_call():
         c.close()
 
 
-def test_many_runs_sort_whole_blocks():
-    # a 3 MiB budget gives chunks of about 2^16.4 keys, so 8e6 keys make more
-    # runs than the run-merge kernels' pair table takes: every block is then
-    # sorted whole instead of merged
+def test_many_runs():
+    # a 3 MiB budget gives chunks of about 2^16.4 keys, so 8e6 keys make about
+    # 90 runs: more pairs per merge round than one run-merge launch takes
     need_gpu()
     c = ms.Context(0, scratch_budget_bytes=3 << 20)
     try:

@@ -1,5 +1,6 @@
-"""GPU parity of msort_merge (one round of the merge tree) and of the
-distributed tree-merge sort on one GPU rank."""
+"""GPU parity of msort_merge (one round of the merge tree), of
+msort_merge_runs (every round over runs of unequal length laid end to end)
+and of the distributed sorts on one GPU rank."""
 import numpy as np
 import pytest
 
@@ -43,6 +44,63 @@ def test_merge_two_runs(ctx, kt, pairs, na, nb):
     assert np.array_equal(to_host(out), ek)
     if pairs:
         assert np.array_equal(to_host(vout), ev)
+
+
+def _run_lengths(seed, count, hi):
+    rng = np.random.default_rng(seed)
+    lens = rng.integers(0, hi, size=count)
+    lens[::5] = 0  # empty runs
+    return [int(x) for x in lens]
+
+
+RUN_LENGTHS = [[0], [5], [0, 0, 3], [8448, 1], [4351, 0, 4353, 17], [1, 1, 1, 1, 1, 1, 1],
+               _run_lengths(1, 33, 30000), _run_lengths(2, 65, 20000), _run_lengths(3, 130, 9000),
+               [1 << 19, 3, (1 << 19) + 5, 8447, 100000, 0, 77777]]
+
+
+@pytest.mark.parametrize("kt", ["u32", "u64"])
+@pytest.mark.parametrize("pairs", [False, True])
+@pytest.mark.parametrize("lens", RUN_LENGTHS, ids=[f"runs{len(x)}_{sum(x)}" for x in RUN_LENGTHS])
+def test_merge_runs(ctx, kt, pairs, lens):
+    runs = []
+    for i, ln in enumerate(lens):
+        if kt == "u32":
+            runs.append(np.sort(synth.uniform_u32(ln, 10 + i) % np.uint32(700)))
+        else:
+            runs.append(np.sort(synth.dup_u64(ln, 10 + i, distinct=700)[0]))
+    keys = np.concatenate(runs) if runs else np.zeros(0, dtype=np.uint32)
+    n = keys.size
+    offsets = np.concatenate([[0], np.cumsum(lens)]).astype(np.uint64)
+    vals = np.arange(n, dtype=np.uint32)
+    # the stable merge of sorted runs in run order is the stable sort of
+    # their concatenation
+    ek, ev = oracle.sort(keys, vals)
+    dk = to_dev(keys)
+    out = torch.empty_like(dk)
+    dv = to_dev(vals) if pairs else None
+    vout = torch.empty_like(dv) if pairs else None
+    ms.msort_merge_runs(ctx, dk, offsets, out, vals=dv, out_vals=vout)
+    if n:
+        assert np.array_equal(to_host(out), ek)
+        assert np.array_equal(to_host(dk), keys)  # input untouched
+        if pairs:
+            assert np.array_equal(to_host(vout), ev)
+
+
+def test_merge_runs_rejects(ctx):
+    k = to_dev(np.arange(100, dtype=np.uint32))
+    out = torch.empty_like(k)
+    for offs, o, status in (([0, 60, 50, 100], out, ms.MSORT_ERR_INVALID_ARG),  # decreasing
+                            ([5, 100], out, ms.MSORT_ERR_INVALID_ARG),  # not starting at 0
+                            ([0, 50, 100], k, ms.MSORT_ERR_INVALID_ARG)):  # output overlaps input
+        with pytest.raises(ms.MsortError) as e:
+            ms.msort_merge_runs(ctx, k, offs, o)
+        assert e.value.status == status
+    f = to_dev(np.arange(100, dtype=np.float32))
+    with pytest.raises(ms.MsortError) as e:
+        ms.msort_merge_runs(ctx, f, [0, 50, 100], torch.empty_like(f))
+    assert e.value.status == ms.MSORT_ERR_UNSUPPORTED
+    ms.msort_ctx_sync(ctx)
 
 
 def test_tree_merge_sort_single_gpu_rank(ctx):
@@ -89,6 +147,13 @@ def test_sample_sort_gpu_pieces_and_single_rank(ctx):
     m, mv = dist._gpu_merge_pairs(ctx)(to_dev(a), to_dev(va), to_dev(b), to_dev(vb))
     em, emv = oracle.merge(a, b, va, vb)
     assert np.array_equal(to_host(m), em) and np.array_equal(to_host(mv), emv)
+    # the pieces a rank receives, merged in one call
+    cuts = [0, n // 7, n // 7, n // 2, n - 5, n]
+    pk = np.concatenate([np.sort(keys[c0:c1]) for c0, c1 in zip(cuts, cuts[1:])])
+    pv = np.arange(n, dtype=np.uint32)
+    rk, rv = dist._gpu_merge_runs(ctx)(to_dev(pk), to_dev(pv), np.array(cuts, dtype=np.uint64))
+    ek2, ev2 = oracle.sort(pk, pv)
+    assert np.array_equal(to_host(rk), ek2) and np.array_equal(to_host(rv), ev2)
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
         port = s.getsockname()[1]
