@@ -207,13 +207,14 @@ msort_status msort_merge_runs(msort_ctx* ctx, const void* d_keys, const uint32_t
  * Out of core: when the context has a budget and the three staging slots
  * plus the scratch for n elements would exceed it, the array is sorted in
  * budget-sized chunks C whose sorted runs go to a pinned host buffer owned by
- * the context (n keys and values, kept for later calls); every C/(2R)-th
- * element of the R runs is sampled, and every R-th sample in (key, position)
- * order becomes a splitter, so each block between consecutive splitters
- * holds at most C elements; each block's slices of all runs are copied to a
- * staging slot, sorted stably (their stable merge) and copied to their place
- * in the output, consecutive blocks overlapping on the context's streams.
- * MSORT_ERR_OOM if the budget does not fit a chunk of four 16896-key tiles.
+ * the context (n keys and values, kept for later calls).  With B = C/2,
+ * every B/(16R)-th element of the R runs is sampled, and every 15R-th sample
+ * in (key, position) order becomes a splitter (B/(2R) and R when 16R > B),
+ * so each block between consecutive splitters holds at most B elements.  Each block's slices of
+ * all runs are copied to a staging slot, merged there (msort_merge_runs'
+ * rounds; ties in run order) and copied to their place in the output,
+ * consecutive blocks overlapping on the context's streams.  MSORT_ERR_OOM if
+ * the budget does not fit a chunk of four 16896-key tiles.
  * This path is taken by msort_sort_host_async too, and then returns with the
  * output complete. */
 msort_status msort_sort_host(msort_ctx* ctx, const void* h_keys_in, const uint32_t* h_vals_in,
