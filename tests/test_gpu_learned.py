@@ -117,6 +117,24 @@ def test_guided_sorts_are_exact(ctx, mode, dist):
     assert np.array_equal(to_host(d), exp)
 
 
+@pytest.mark.parametrize("opts", [{"partition_mode": 1}, {"partition_mode": 1, "learned_passes": 64}],
+                         ids=["final_passes", "all_passes"])
+def test_full_size_learned_2_30(ctx, opts):
+    """2^30 keys of the lognormal mixture with the learned partition, as the
+    learned-partition benchmark launches it; bit-exact against the oracle
+    on every host core."""
+    import os
+    from synth import torch_gen
+    n = 1 << 30
+    src = torch_gen.lognormal3_u32(n, 1, device="cuda")
+    out = torch.empty_like(src)
+    ms.msort_sort_copy(ctx, src, out, options=opts)
+    exp, _ = oracle.par_sort(to_host(src), workers=len(os.sched_getaffinity(0)))
+    assert np.array_equal(to_host(out), exp)
+    del src, out
+    torch.cuda.empty_cache()
+
+
 def test_guided_pairs_u64_exact(ctx):
     n = (1 << 21) + 17
     keys, vals = synth.dup_u64(n, 9)

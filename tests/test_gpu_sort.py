@@ -174,6 +174,21 @@ def test_full_size_2_28(ctx, name):
     assert np.array_equal(to_host(out), exp)
 
 
+def test_full_size_pairs_2_27(ctx):
+    """2^27 (uint64 key, uint32 original index) pairs with keys from 2^20
+    distinct values, the key-value benchmark's launch configuration;
+    bit-exact (keys and values, so stability too) against the oracle."""
+    import os
+    from synth import torch_gen
+    n = 1 << 27
+    dk, dv = torch_gen.dup_u64(n, 1, device="cuda")
+    ok, ov = torch.empty_like(dk), torch.empty_like(dv)
+    ms.msort_sort_copy(ctx, dk, ok, dv, ov)
+    ek, ev = oracle.par_sort(to_host(dk), to_host(dv), workers=len(os.sched_getaffinity(0)))
+    assert np.array_equal(to_host(ok), ek)
+    assert np.array_equal(to_host(ov), ev)
+
+
 @pytest.mark.parametrize("kt", ["u32", "u64"])
 @pytest.mark.parametrize("pairs", [False, True])
 def test_graph_replay(ctx, kt, pairs):
