@@ -133,6 +133,24 @@ def test_presorted_float_pairs(order):
         c.close()
 
 
+def test_full_size_2_30():
+    """The out-of-core benchmark's configuration: 2^30 uniform uint32 keys in
+    pinned host memory, 1 GiB device budget; bit-exact against the oracle's
+    parallel sort on every host core."""
+    import os
+    from synth import torch_gen
+    c = _ctx(1024)
+    try:
+        n = 1 << 30
+        hin = torch_gen.uniform_u32(n, 1, device="cuda").cpu().pin_memory()
+        hout = torch.empty(n, dtype=torch.uint32).pin_memory()
+        ms.msort_sort_host(c.handle, hin, out_keys=hout)
+        exp, _ = oracle.par_sort(hin.numpy(), workers=len(os.sched_getaffinity(0)))
+        assert np.array_equal(hout.numpy(), exp)
+    finally:
+        c.close()
+
+
 def test_budget_too_small():
     c = _ctx(1)
     try:
