@@ -202,7 +202,9 @@ msort_status msort_merge_runs(msort_ctx* ctx, const void* d_keys, const uint32_t
  * the whole array each way around the sort).  Device buffers come from the
  * context: three staging slots, used by consecutive calls in turn, each
  * growing to the largest n it served, plus the sort scratch.  Synchronises on `stream`
- * before returning.
+ * before returning.  When the call (or msort_sort_host_async) fails after
+ * enqueuing work, it first waits for that work, so that on any error return
+ * nothing it started still uses the host buffers.
  *
  * Out of core: when the context has a budget and the three staging slots
  * plus the scratch for n elements would exceed it, the array is sorted in

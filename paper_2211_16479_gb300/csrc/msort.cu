@@ -541,6 +541,19 @@ struct HostPipe {
     size_t runs_bytes = 0;
 };
 
+void host_pipe_destroy(msort_ctx* ctx);
+
+// After a host-buffer call failed part-way: wait until nothing it enqueued
+// on the context's streams can still read or write the caller's host
+// buffers, so that the caller may free them once the call returns.
+static void host_pipe_drain(msort_ctx* ctx) {
+    HostPipe* hp = static_cast<HostPipe*>(ctx->host_pipe);
+    if (!hp) return;
+    cudaStreamSynchronize(hp->h2d);
+    cudaStreamSynchronize(hp->cs);
+    cudaStreamSynchronize(hp->d2h);
+}
+
 static msort_status host_pipe_get(msort_ctx* ctx, HostPipe** out) {
     if (ctx->host_pipe) {
         *out = static_cast<HostPipe*>(ctx->host_pipe);
@@ -557,8 +570,11 @@ static msort_status host_pipe_get(msort_ctx* ctx, HostPipe** out) {
         for (int i = 0; i < kHostSlices && e == cudaSuccess; ++i)
             e = cudaEventCreateWithFlags(&hp->out_ev[s][i], cudaEventDisableTiming);
     }
-    ctx->host_pipe = hp;  // destroyed (with whatever was created) by host_pipe_destroy
-    if (e != cudaSuccess) return cuda_fail(e, "host-sort streams/events");
+    ctx->host_pipe = hp;
+    if (e != cudaSuccess) {
+        host_pipe_destroy(ctx);  // with whatever was created; the next call tries again
+        return cuda_fail(e, "host-sort streams/events");
+    }
     *out = hp;
     return MSORT_OK;
 }
@@ -1298,7 +1314,11 @@ static msort_status host_sort_call(msort_ctx* ctx, const void* h_kin, const uint
         s = h_vin ? host_sort_any<uint64_t, true>(ctx, h_kin, h_vin, h_kout, h_vout, n, opt, st, ch, sl, xf, &synced)
                   : host_sort_any<uint64_t, false>(ctx, h_kin, nullptr, h_kout, nullptr, n, opt, st, ch, sl, xf,
                                                    &synced);
-    if (s != MSORT_OK || !wait || synced) return s;
+    if (s != MSORT_OK) {
+        host_pipe_drain(ctx);
+        return s;
+    }
+    if (!wait || synced) return s;
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     return MSORT_OK;
