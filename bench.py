@@ -786,7 +786,7 @@ def main():
     ap.add_argument("--merge-ways", type=int, default=0, help="0 = plan default, 2 = pairwise passes, 4 = four-way")
     ap.add_argument("--no-torch-sort", action="store_true", help="skip the torch.sort(stable=True) context figure")
     ap.add_argument("--graph", type=int, default=1, help="1 = replay each sort from a captured CUDA graph")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=None, help="steps of the end-to-end measurement (default: --steps)")
     ap.add_argument("--e2e-reps", type=int, default=5, help="repetitions of the end-to-end measurement (median)")
     ap.add_argument("--learned-log2n", type=int, default=30, help="size of the learned-partition workload (log2)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -795,6 +795,8 @@ def main():
     ap.add_argument("--workload", default="sort",
                     choices=["sort", "small", "float", "external", "pairs", "segmented", "learned", "serving"])
     args = ap.parse_args()
+    if args.e2e_steps is None:
+        args.e2e_steps = args.steps
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
