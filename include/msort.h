@@ -310,11 +310,13 @@ size_t msort_noalloc_max_keys(msort_key_type kt, int with_vals);
 
 /* Times every tile shape (tile size = threads x keys per thread, which also
  * fixes the merge block) of the plain sort for 32/64-bit keys, with and
- * without values, at n = 2^16, 2^20 and 2^24 (quick != 0: 2^20 only), and
+ * without values, at n = 2^16, 2^20 and 2^24 (quick != 0: 2^20 only), each
+ * with two-way and four-way merge passes for 32-bit keys without values, and
  * the segmented sort's bucket shapes for 32-bit keys; each candidate's output
  * must equal the first candidate's bit for bit or the candidate is rejected.
- * The winners are used by later calls on ctx whose options leave tile at 0
- * (size class = largest tuned class not above log2(n)).  cache_path
+ * The winners are used by later calls on ctx whose options leave tile (and,
+ * for the device-buffer sorts of unsigned keys with partition_mode 0,
+ * merge_ways) at 0 (size class = largest tuned class not above log2(n)).  cache_path
  * (nullable) receives the results as JSON.  Allocates its own test buffers
  * and synchronises the device; meant for start-up, not for a hot loop. */
 msort_status msort_tune(msort_ctx* ctx, const char* cache_path, int quick);

@@ -63,6 +63,8 @@ struct msort_ctx {
     void* plain_graphs = nullptr;
     // autotuned choices (msort_tune): (key bytes, values, log2 size class) -> tile
     std::map<std::tuple<int, int, int>, int> tuned_tile;
+    // merge fan-in (2 or 4) of the same classes; tuned for unsigned keys only
+    std::map<std::tuple<int, int, int>, int> tuned_ways;
     // segmented sort of 32-bit keys: largest on-chip bucket and large-segment tile (0 = default)
     int seg_max_small = 0;
     int seg_large_tile = 0;

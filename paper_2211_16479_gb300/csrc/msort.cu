@@ -396,11 +396,11 @@ template msort_status sort_keys_internal<uint64_t>(msort_ctx*, const uint64_t*, 
 
 // Tuned tile for (key type, values, n): the entry of the largest tuned size
 // class not above log2(n) (or the smallest class), 0 if nothing was tuned.
-static int tuned_tile_for(const msort_ctx* ctx, int key_bytes, bool pairs, size_t n) {
+static int tuned_choice(const std::map<std::tuple<int, int, int>, int>& table, int key_bytes, bool pairs, size_t n) {
     int best = 0, best_cls = -1, lowest = 0, lowest_cls = 1 << 30;
     int lg = 0;
     while (lg < 63 && (size_t(1) << (lg + 1)) <= n) ++lg;
-    for (const auto& kv : ctx->tuned_tile) {
+    for (const auto& kv : table) {
         if (std::get<0>(kv.first) != key_bytes || std::get<1>(kv.first) != (int)pairs) continue;
         const int cls = std::get<2>(kv.first);
         if (cls <= lg && cls > best_cls) {
@@ -415,6 +415,10 @@ static int tuned_tile_for(const msort_ctx* ctx, int key_bytes, bool pairs, size_
     return best ? best : lowest;
 }
 
+static int tuned_tile_for(const msort_ctx* ctx, int key_bytes, bool pairs, size_t n) {
+    return tuned_choice(ctx->tuned_tile, key_bytes, pairs, n);
+}
+
 template <class K, bool PAIRS>
 static msort_status sort_entry(msort_ctx* ctx, const void* kin, const uint32_t* vin, void* kout, uint32_t* vout,
                                size_t n, const msort_options* opt, cudaStream_t st, int xform) {
@@ -424,6 +428,16 @@ static msort_status sort_entry(msort_ctx* ctx, const void* kin, const uint32_t* 
         if (tile) {
             if (opt) tuned_opt = *opt;
             tuned_opt.tile = tile;
+            opt = &tuned_opt;
+        }
+    }
+    // tuned merge fan-in where the caller left it open (the four-way pass
+    // takes neither transformed keys nor the learned partition)
+    if (!xform && (!opt || (!opt->merge_ways && opt->partition_mode == 0))) {
+        const int ways = tuned_choice(ctx->tuned_ways, (int)sizeof(K), PAIRS, n);
+        if (ways) {
+            if (opt && opt != &tuned_opt) tuned_opt = *opt;
+            tuned_opt.merge_ways = ways;
             opt = &tuned_opt;
         }
     }

@@ -1,6 +1,7 @@
 // Autotuner: picks the tile shape (threads x keys per thread, hence tile
 // size and merge-block size) of the plain sort per key type, value presence
-// and size class, and the bucket shapes of the segmented sort of 32-bit
+// and size class, the merge fan-in (two-way or four-way passes) for 32-bit
+// keys without values, and the bucket shapes of the segmented sort of 32-bit
 // keys, by timing every candidate on this GPU.  Every candidate's output is
 // compared bit for bit with the first candidate's before its time counts;
 // a candidate that disagrees is rejected.  Results live in the context and
@@ -109,13 +110,17 @@ msort_status msort_tune(msort_ctx* ctx, const char* cache_path, int quick) {
                 else
                     k_fill<uint64_t><<<1024, 256>>>(static_cast<uint64_t*>(kin.p), static_cast<uint32_t*>(vin.p), n,
                                                     1234 + cls);
-                int best_tile = 0;
+                int best_tile = 0, best_ways = 2;
                 float best_ms = 1e30f;
                 bool have_ref = false;
                 std::string times;
-                for (int tile : kTiles) {
+                const bool four = kt == 0 && !pairs;  // four-way passes: 32-bit keys without values
+                for (int tile : kTiles)
+                for (int ways : {2, 4}) {
+                    if (ways == 4 && !four) continue;
                     msort_options o{};
                     o.tile = tile;
+                    o.merge_ways = ways;
                     if (msort_scratch_bytes(n, (msort_key_type)kt, pairs, &o) == 0) continue;  // not offered
                     auto run = [&] {
                         msort_sort_copy(ctx, kin.p, pairs ? static_cast<uint32_t*>(vin.p) : nullptr, kout.p,
@@ -134,18 +139,24 @@ msort_status msort_tune(msort_ctx* ctx, const char* cache_path, int quick) {
                              (!pairs || same_bytes(vref.p, vout.p, n * 4, d_diff));
                     }
                     char buf[64];
-                    std::snprintf(buf, sizeof buf, "%s\"%d\": %.4f", times.empty() ? "" : ", ", tile, ok ? ms : -1.f);
+                    std::snprintf(buf, sizeof buf, "%s\"%d%s\": %.4f", times.empty() ? "" : ", ", tile,
+                                  ways == 4 ? "x4" : "", ok ? ms : -1.f);
                     times += buf;
                     if (ok && ms < best_ms) {
                         best_ms = ms;
                         best_tile = tile;
+                        best_ways = ways;
                     }
                 }
-                if (best_tile) ctx->tuned_tile[std::make_tuple((int)ks, pairs, cls)] = best_tile;
-                char line[512];
+                if (best_tile) {
+                    ctx->tuned_tile[std::make_tuple((int)ks, pairs, cls)] = best_tile;
+                    if (four) ctx->tuned_ways[std::make_tuple((int)ks, pairs, cls)] = best_ways;
+                }
+                char line[640];
                 std::snprintf(line, sizeof line,
-                              "%s    {\"key_bytes\": %zu, \"values\": %d, \"log2n\": %d, \"tile\": %d, \"ms\": {%s}}",
-                              first_line ? "" : ",\n", ks, pairs, cls, best_tile, times.c_str());
+                              "%s    {\"key_bytes\": %zu, \"values\": %d, \"log2n\": %d, \"tile\": %d, \"ways\": %d, "
+                              "\"ms\": {%s}}",
+                              first_line ? "" : ",\n", ks, pairs, cls, best_tile, best_ways, times.c_str());
                 log += line;
                 first_line = false;
             }
@@ -231,12 +242,16 @@ msort_status msort_tune_load(msort_ctx* ctx, const char* cache_path) {
     char line[1024];
     int loaded = 0;
     while (std::fgets(line, sizeof line, f)) {
-        int kb = 0, v = 0, lg = 0, tile = 0;
+        int kb = 0, v = 0, lg = 0, tile = 0, ways = 0;
         const char* p = std::strstr(line, "\"key_bytes\"");
-        if (p && std::sscanf(p, "\"key_bytes\": %d, \"values\": %d, \"log2n\": %d, \"tile\": %d", &kb, &v, &lg,
-                             &tile) == 4) {
+        const int got = p ? std::sscanf(p, "\"key_bytes\": %d, \"values\": %d, \"log2n\": %d, \"tile\": %d, \"ways\": %d",
+                                        &kb, &v, &lg, &tile, &ways)
+                          : 0;
+        if (got >= 4) {
             if (tile) {
                 ctx->tuned_tile[std::make_tuple(kb, v, lg)] = tile;
+                if (got == 5 && kb == 4 && v == 0 && (ways == 2 || ways == 4))
+                    ctx->tuned_ways[std::make_tuple(kb, v, lg)] = ways;
                 ++loaded;
             }
             continue;
@@ -256,6 +271,7 @@ msort_status msort_tune_load(msort_ctx* ctx, const char* cache_path) {
 msort_status msort_tune_clear(msort_ctx* ctx) {
     if (!ctx) return fail(MSORT_ERR_INVALID_ARG, "ctx is NULL");
     ctx->tuned_tile.clear();
+    ctx->tuned_ways.clear();
     ctx->seg_max_small = 0;
     ctx->seg_large_tile = 0;
     return MSORT_OK;
