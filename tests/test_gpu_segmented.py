@@ -55,6 +55,26 @@ def test_bucket_boundaries(ctx, kt, pairs):
         assert np.array_equal(to_host(dv), ev)
 
 
+@pytest.mark.parametrize("max_small,large_tile", [(33792, 16896), (16896, 8448), (33792, 8448)])
+def test_tuned_bucket_plans(tmp_path, max_small, large_tile):
+    # the bucket plans the tuner can choose besides the default (16896-key
+    # on-chip bucket, 16896-key large-segment tile), on the boundary lengths
+    need_gpu()
+    path = tmp_path / "seg.json"
+    path.write_text('{\n  "segmented_u32": {"max_small": %d, "large_tile": %d, "ms": {}}\n}\n'
+                    % (max_small, large_tile))
+    with ms.Context(0) as c:
+        ms.msort_tune_load(c.handle, str(path))
+        rng = np.random.default_rng(3)
+        lens = np.asarray(BOUNDARY_LENS + list(rng.permutation(BOUNDARY_LENS)), dtype=np.int64)
+        off = synth.segment_offsets(lens)
+        keys = _keys("u32", int(off[-1]), 4, 1000)
+        dk = to_dev(keys)
+        ms.msort_segmented_sort(c.handle, dk, to_dev(off))
+        ms.msort_ctx_sync(c.handle)
+        assert np.array_equal(to_host(dk), oracle.segmented_sort(keys, off)[0])
+
+
 @pytest.mark.parametrize("use_graph", [False, True])
 def test_log_uniform_batch(ctx, use_graph):
     lens = synth.segment_lengths(3000, 5)
