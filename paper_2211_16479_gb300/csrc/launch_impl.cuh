@@ -87,7 +87,7 @@ cudaError_t launch_merge(const Plan& pl, const K* src, K* dst, const uint32_t* v
     cudaError_t e;
 #define MSORT_MERGE_CASE(WW, TH, IPT)                                          \
     if (pl.W == WW) {                                                          \
-        auto f = k_merge_pass<K, PAIRS, TH, IPT>;                              \
+        auto f = xf_out ? k_merge_pass<K, PAIRS, TH, IPT, true> : k_merge_pass<K, PAIRS, TH, IPT, false>; \
         if ((e = prepare(f, sm)) != cudaSuccess) return e;                     \
         f<<<(unsigned)(c1 - c0), TH, sm, st>>>(src, dst, vsrc, vdst, n, L, splits, pl.status, c0, xf_out); \
         return cudaGetLastError();                                             \
@@ -199,12 +199,12 @@ cudaError_t launch_merge_runs(const K* src, K* dst, const uint32_t* vsrc, uint32
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (W == 256 * 33) {
-        auto f = k_merge_runs<K, PAIRS, 256, 33>;
+        auto f = xf_out ? k_merge_runs<K, PAIRS, 256, 33, true> : k_merge_runs<K, PAIRS, 256, 33, false>;
         const size_t sm = merge_block_smem<K, PAIRS, 256, 33>();
         if ((e = prepare(f, sm)) != cudaSuccess) return e;
         f<<<(unsigned)nblocks, 256, sm, st>>>(src, dst, vsrc, vdst, rp, splits, status, xf_out);
     } else {
-        auto f = k_merge_runs<K, PAIRS, 256, 17>;
+        auto f = xf_out ? k_merge_runs<K, PAIRS, 256, 17, true> : k_merge_runs<K, PAIRS, 256, 17, false>;
         const size_t sm = merge_block_smem<K, PAIRS, 256, 17>();
         if ((e = prepare(f, sm)) != cudaSuccess) return e;
         f<<<(unsigned)nblocks, 256, sm, st>>>(src, dst, vsrc, vdst, rp, splits, status, xf_out);

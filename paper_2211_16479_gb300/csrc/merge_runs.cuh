@@ -37,7 +37,7 @@ __global__ void k_partition_runs(const K* __restrict__ src, const __grid_constan
 }
 
 // Block blk writes its pair's outputs [d0, min(d0 + W, pair length)).
-template <class K, bool PAIRS, int THREADS, int IPT>
+template <class K, bool PAIRS, int THREADS, int IPT, bool XF>
 __global__ void __launch_bounds__(THREADS)
 k_merge_runs(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __restrict__ vsrc,
              uint32_t* __restrict__ vdst, const __grid_constant__ RunPairs rp,
@@ -60,9 +60,9 @@ k_merge_runs(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __r
     const int nB = (int)(d1 - d0) - nA;
     const size_t oA = pb + a0, oB = pb + alen + (d0 - a0);
     uint32_t phase = 0;
-    merge_block<K, PAIRS, THREADS, IPT>(src + oA, nA, src + oB, nB, PAIRS ? vsrc + oA : nullptr,
-                                        PAIRS ? vsrc + oB : nullptr, dst + pb + d0, PAIRS ? vdst + pb + d0 : nullptr,
-                                        smem_raw, &bar, phase, status, xf_out);
+    merge_block<K, PAIRS, THREADS, IPT, XF>(src + oA, nA, src + oB, nB, PAIRS ? vsrc + oA : nullptr,
+                                            PAIRS ? vsrc + oB : nullptr, dst + pb + d0,
+                                            PAIRS ? vdst + pb + d0 : nullptr, smem_raw, &bar, phase, status, xf_out);
 }
 
 }  // namespace msort

@@ -186,11 +186,17 @@ k_seg_large(K* keys, uint32_t* vals, K* tkeys, uint32_t* tvals, const unsigned l
                     const int nA = (int)(a1 - a0);
                     const int nB = (int)(d1 - d0) - nA;
                     const size_t oA = g.pb + a0, oB = g.pb + g.alen + (d0 - a0);
-                    if (!merge_block<K, PAIRS, THREADS, IPT>(
-                            src + oA, nA, src + oB, nB, PAIRS ? bv[cur] + oA : nullptr,
-                            PAIRS ? bv[cur] + oB : nullptr, dst + out0, PAIRS ? bv[cur ^ 1] + out0 : nullptr,
-                            smem_raw, &bar, phase, status, p + 1 == passes ? xf : 0))
-                        return;
+                    const bool ok =
+                        xf && p + 1 == passes
+                            ? merge_block<K, PAIRS, THREADS, IPT, true>(
+                                  src + oA, nA, src + oB, nB, PAIRS ? bv[cur] + oA : nullptr,
+                                  PAIRS ? bv[cur] + oB : nullptr, dst + out0, PAIRS ? bv[cur ^ 1] + out0 : nullptr,
+                                  smem_raw, &bar, phase, status, xf)
+                            : merge_block<K, PAIRS, THREADS, IPT, false>(
+                                  src + oA, nA, src + oB, nB, PAIRS ? bv[cur] + oA : nullptr,
+                                  PAIRS ? bv[cur] + oB : nullptr, dst + out0, PAIRS ? bv[cur ^ 1] + out0 : nullptr,
+                                  smem_raw, &bar, phase, status, 0);
+                    if (!ok) return;
                 }
             }
             block_pass_barrier();

@@ -624,13 +624,15 @@ __host__ __device__ constexpr int merge_slots(int W, int IPT, int esize) {
 // Merge of one output block: D[0, nA + nB) = stable merge of gA[0, nA) and
 // gB[0, nB) (nA + nB <= W = THREADS * IPT), values alongside for pairs.
 // `bar` is an initialised mbarrier of this block, `phase` its next parity.
+// XF: the block undoes the key transform xf_out as it stages its output (a
+// separate instance, so the common passes keep their register budget).
 // Shared memory: merge_slots(W, IPT, sizeof(K)) keys, then for pairs
 // merge_slots(W, IPT, 4) values.  Returns false if a bounded wait gave up.
 // ---------------------------------------------------------------------------
-template <class K, bool PAIRS, int THREADS, int IPT>
+template <class K, bool PAIRS, int THREADS, int IPT, bool XF>
 __device__ __forceinline__ bool merge_block(const K* gA, int nA, const K* gB, int nB, const uint32_t* gvA,
                                             const uint32_t* gvB, K* D, uint32_t* VD, unsigned char* smem_raw,
-                                            uint64_t* bar, uint32_t& phase, unsigned int* status, int xf_out = 0) {
+                                            uint64_t* bar, uint32_t& phase, unsigned int* status, int xf_out) {
     constexpr int W = THREADS * IPT;
     constexpr int KS = (int)sizeof(K);
     constexpr int KSLOTS = merge_slots(W, IPT, KS);
@@ -728,7 +730,7 @@ __device__ __forceinline__ bool merge_block(const K* gA, int nA, const K* gB, in
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
         if (i < mine) {
-            sk[t * IPT + i] = xf_inverse(ok[i], xf_out);
+            sk[t * IPT + i] = XF ? xf_inverse(ok[i], xf_out) : ok[i];
             if (PAIRS) sv[t * IPT + i] = ov[i];
         }
     }
@@ -757,8 +759,8 @@ __host__ __device__ constexpr size_t merge_block_smem() {
 
 // Merge pass kernel: block c = c0 + blockIdx.x writes dst[c*W, min((c+1)*W,
 // pair end)) (c0 lets a pass be launched in slices).
-template <class K, bool PAIRS, int THREADS, int IPT>
-__global__ void __launch_bounds__(THREADS)
+template <class K, bool PAIRS, int THREADS, int IPT, bool XF>
+__global__ void __launch_bounds__(THREADS, (sizeof(K) == 4 && !PAIRS && IPT == 33) ? 6 : 0)
 k_merge_pass(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __restrict__ vsrc,
              uint32_t* __restrict__ vdst, size_t n, size_t L, const unsigned long long* __restrict__ splits,
              unsigned int* status, size_t c0, int xf_out) {
@@ -781,9 +783,9 @@ k_merge_pass(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __r
     const int nB = (int)(d1 - d0) - nA;
     const size_t oA = g.pb + a0, oB = g.pb + g.alen + (d0 - a0);
     uint32_t phase = 0;
-    merge_block<K, PAIRS, THREADS, IPT>(src + oA, nA, src + oB, nB, PAIRS ? vsrc + oA : nullptr,
-                                        PAIRS ? vsrc + oB : nullptr, dst + out0, PAIRS ? vdst + out0 : nullptr,
-                                        smem_raw, &bar, phase, status, xf_out);
+    merge_block<K, PAIRS, THREADS, IPT, XF>(src + oA, nA, src + oB, nB, PAIRS ? vsrc + oA : nullptr,
+                                            PAIRS ? vsrc + oB : nullptr, dst + out0, PAIRS ? vdst + out0 : nullptr,
+                                            smem_raw, &bar, phase, status, xf_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -820,8 +822,9 @@ k_merge_two(const K* __restrict__ A, size_t na, const K* __restrict__ B, size_t 
     const int nA = (int)(a1 - a0);
     const int nB = (int)(d1 - d0) - nA;
     uint32_t phase = 0;
-    merge_block<K, PAIRS, THREADS, IPT>(A + a0, nA, B + b0, nB, PAIRS ? va + a0 : nullptr, PAIRS ? vb + b0 : nullptr,
-                                        out + d0, PAIRS ? vout + d0 : nullptr, smem_raw, &bar, phase, status);
+    merge_block<K, PAIRS, THREADS, IPT, false>(A + a0, nA, B + b0, nB, PAIRS ? va + a0 : nullptr,
+                                               PAIRS ? vb + b0 : nullptr, out + d0, PAIRS ? vout + d0 : nullptr,
+                                               smem_raw, &bar, phase, status, 0);
 }
 
 }  // namespace msort
