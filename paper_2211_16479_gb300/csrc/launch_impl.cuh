@@ -66,7 +66,7 @@ cudaError_t launch_tile(const Plan& pl, const K* kin, const uint32_t* vin, K* ko
     cudaError_t e;
 #define MSORT_TILE_CASE(TILE, TH, IPT)                                         \
     if (pl.tile == TILE) {                                                     \
-        auto f = k_tile_sort<K, PAIRS, TH, IPT>;                               \
+        auto f = (xf_in || xf_out) ? k_tile_sort<K, PAIRS, TH, IPT, true> : k_tile_sort<K, PAIRS, TH, IPT, false>; \
         if ((e = prepare(f, sm)) != cudaSuccess) return e;                     \
         f<<<(unsigned)nblocks, TH, sm, st>>>(kin, vin, kout, vout, n, pl.status, xf_in, xf_out); \
         return cudaGetLastError();                                             \

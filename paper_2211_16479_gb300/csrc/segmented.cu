@@ -92,7 +92,7 @@ k_seg_small(K* keys, uint32_t* vals, const unsigned long long* __restrict__ off,
         const unsigned int s = lists[(size_t)q * nseg + w];
         const size_t b = off[s];
         const int len = (int)(off[s + 1] - b);
-        if (!tile_sort_block<K, PAIRS, THREADS, IPT>(keys + b, PAIRS ? vals + b : nullptr, keys + b,
+        if (!tile_sort_block<K, PAIRS, THREADS, IPT, true>(keys + b, PAIRS ? vals + b : nullptr, keys + b,
                                                      PAIRS ? vals + b : nullptr, len, smem_raw, &bar, phase,
                                                      status, xf, xf))
             return;
@@ -145,7 +145,7 @@ k_seg_large(K* keys, uint32_t* vals, K* tkeys, uint32_t* tvals, const unsigned l
         int cur = passes & 1;
         for (size_t j = 0; j < len; j += T) {
             const int valid = (int)(len - j < (size_t)T ? len - j : (size_t)T);
-            if (!tile_sort_block<K, PAIRS, THREADS, IPT>(keys + base + j, PAIRS ? vals + base + j : nullptr,
+            if (!tile_sort_block<K, PAIRS, THREADS, IPT, true>(keys + base + j, PAIRS ? vals + base + j : nullptr,
                                                          bk[cur] + j, PAIRS ? bv[cur] + j : nullptr, valid,
                                                          smem_raw, &bar, phase, status, xf,
                                                          passes == 0 ? xf : 0))

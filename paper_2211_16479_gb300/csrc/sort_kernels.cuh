@@ -397,10 +397,14 @@ __device__ __forceinline__ bool tile_sort_block_kv(const K* src, const uint32_t*
 // pairs.  Steps: bulk TMA load (or coalesced loads), per-thread network,
 // merge rounds in bitonic layout, bulk TMA store (or coalesced stores).
 // ---------------------------------------------------------------------------
-template <class K, bool PAIRS, int THREADS, int IPT>
+template <class K, bool PAIRS, int THREADS, int IPT, bool XF>
 __device__ __forceinline__ bool tile_sort_block(const K* src, const uint32_t* vin, K* dst, uint32_t* vout, int valid,
                                                 unsigned char* smem_raw, uint64_t* bar, uint32_t& phase,
-                                                unsigned int* status, int xf_in = 0, int xf_out = 0) {
+                                                unsigned int* status, int xf_in, int xf_out) {
+    if constexpr (!XF) {  // the instance without key transforms: their code folds away
+        xf_in = 0;
+        xf_out = 0;
+    }
     if constexpr (PAIRS && sizeof(K) == 8) {
         return tile_sort_block_kv<K, THREADS, IPT>(src, vin, dst, vout, valid, smem_raw, xf_in, xf_out);
     }
@@ -503,8 +507,9 @@ __host__ __device__ constexpr size_t tile_block_smem(int T) {
 }
 
 // Tile sort kernel: block b sorts kin[b*T, min((b+1)*T, n)) in place into
-// kout.  kin may equal kout (each block reads its whole tile first).
-template <class K, bool PAIRS, int THREADS, int IPT>
+// kout.  kin may equal kout (each block reads its whole tile first).  XF:
+// the instance that applies / undoes key transforms (signed and float keys).
+template <class K, bool PAIRS, int THREADS, int IPT, bool XF>
 __global__ void __launch_bounds__(THREADS)
 k_tile_sort(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n, unsigned int* status, int xf_in,
             int xf_out) {
@@ -518,9 +523,9 @@ k_tile_sort(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n
     const size_t base = (size_t)blockIdx.x * T;
     const int valid = (int)((n - base) < (size_t)T ? (n - base) : (size_t)T);
     uint32_t phase = 0;
-    tile_sort_block<K, PAIRS, THREADS, IPT>(kin + base, PAIRS ? vin + base : nullptr, kout + base,
-                                            PAIRS ? vout + base : nullptr, valid, smem_raw, &bar, phase, status,
-                                            xf_in, xf_out);
+    tile_sort_block<K, PAIRS, THREADS, IPT, XF>(kin + base, PAIRS ? vin + base : nullptr, kout + base,
+                                                PAIRS ? vout + base : nullptr, valid, smem_raw, &bar, phase, status,
+                                                xf_in, xf_out);
 }
 
 // ---------------------------------------------------------------------------
