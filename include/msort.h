@@ -190,6 +190,18 @@ msort_status msort_merge(msort_ctx* ctx, const void* d_a, const uint32_t* d_va, 
 msort_status msort_merge_runs(msort_ctx* ctx, const void* d_keys, const uint32_t* d_vals, const uint64_t* offsets,
                               size_t nruns, void* d_out, uint32_t* d_vout, msort_key_type kt, void* stream);
 
+/* Merge blocks the out-of-core sort (msort_sort_host) uses, computed on the
+ * host: h_runs holds n unsigned keys (kt MSORT_U32 or MSORT_U64) as
+ * R = ceil(n / chunk) sorted runs of `chunk` keys laid end to end (the last
+ * may be shorter).  Returns the number of blocks nb (0 for invalid
+ * arguments or block_max < 2R) and, when cuts_cap >= (nb + 1) * R, fills
+ * h_cuts[b * R + r] with the number of run r's keys ordered before block b
+ * (b = 0..nb), ordering keys by (value, position in h_runs): block b takes
+ * [h_cuts[b*R + r], h_cuts[(b+1)*R + r]) of every run r, and holds at most
+ * block_max keys.  Pure host code; needs no GPU. */
+size_t msort_external_plan(const void* h_runs, size_t n, msort_key_type kt, size_t chunk, size_t block_max,
+                           uint64_t* h_cuts, size_t cuts_cap);
+
 /* Host-buffer sort: copies h_keys_in (and h_vals_in, nullable) to the
  * device, sorts there, and copies the result to h_keys_out (and h_vals_out;
  * give both value pointers or neither).  Output may be the same buffer as

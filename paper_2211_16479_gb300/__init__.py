@@ -59,6 +59,7 @@ _SIGS = {
     "msort_sort_host_async": ([_P, _P, _P, _P, _P, _SZ, _I, _OPT, _P], _ST),
     "msort_merge": ([_P, _P, _P, _SZ, _P, _P, _SZ, _P, _P, _I, _P], _ST),
     "msort_merge_runs": ([_P, _P, _P, _P, _SZ, _P, _P, _I, _P], _ST),
+    "msort_external_plan": ([_P, _SZ, _I, _SZ, _SZ, _P, _SZ], _SZ),
     "msort_segmented_sort": ([_P, _P, _P, _P, _SZ, _SZ, _I, _OPT, _P], _ST),
     "msort_sort_noalloc": ([_P, _P, _P, _P, _SZ, _I, _P], _ST),
     "msort_noalloc_max_keys": ([_I, _I], _SZ),
@@ -261,6 +262,23 @@ def msort_merge_runs(ctx, keys, offsets, out, vals=None, out_vals=None, key_type
     _check(ctx, load_library().msort_merge_runs(ctx, _ptr(keys), _ptr(vals), offs.ctypes.data, max(len(offs) - 1, 0),
                                                 _ptr(out), _ptr(out_vals), _key_type(keys, key_type),
                                                 _stream(stream, out)))
+
+
+def msort_external_plan(runs, chunk: int, block_max: int):
+    """Blocks of the out-of-core sort for sorted runs of `chunk` keys laid
+    end to end in the host array `runs` (uint32 or uint64): returns the
+    (blocks + 1) x runs array of cut positions (see include/msort.h)."""
+    import numpy as np
+    runs = np.ascontiguousarray(runs)
+    kt = _key_type(runs, None)
+    lib = load_library()
+    nb = lib.msort_external_plan(runs.ctypes.data, runs.size, kt, chunk, block_max, None, 0)
+    if nb == 0:
+        raise ValueError("invalid arguments to msort_external_plan")
+    nruns = -(-runs.size // chunk)
+    cuts = np.zeros((nb + 1) * nruns, dtype=np.uint64)
+    lib.msort_external_plan(runs.ctypes.data, runs.size, kt, chunk, block_max, cuts.ctypes.data, cuts.size)
+    return cuts.reshape(nb + 1, nruns)
 
 
 def msort_sort_host(ctx, keys, vals=None, out_keys=None, out_vals=None, n=None, key_type=None,

@@ -873,6 +873,57 @@ static size_t external_chunk(size_t budget, const msort_options* opt, int xform)
     return lo >= 4 * 16896 ? lo : 0;
 }
 
+// Merge blocks of an out-of-core sort (host logic): the R = ceil(n / chunk)
+// sorted runs of `chunk` elements (the last ragged) lie end to end in
+// tk[0, n), keys in unsigned order.  Returns cut[b * R + r] = the elements of
+// run r ordered before block b, b = 0..nb, ordering by (key, global
+// position); every block holds at most B elements (B >= 2R).  Splitters are
+// regular samples: a block from one splitter sample to the next holding m
+// samples has at most (m + R) * sigma elements (each run adds at most one
+// unsampled stretch of sigma - 1), so splitters every m = (k - 1) R samples
+// with sigma = B / (k R) keep blocks within B while their expected size is
+// (1 - 1/k) B: k = 16 when sigma stays >= 1, else 2.
+template <class K>
+static std::vector<size_t> external_cuts(const K* tk, size_t n, size_t chunk, size_t B, size_t* nb_out) {
+    const size_t R = (n + chunk - 1) / chunk;
+    const size_t kover = 16 * R <= B ? 16 : 2;
+    const size_t sigma = std::max<size_t>(1, B / (kover * R));
+    const size_t every = (kover - 1) * R;
+    struct Smp {
+        K u;
+        size_t g;
+    };
+    auto before = [](const Smp& a, const Smp& b) { return a.u < b.u || (a.u == b.u && a.g < b.g); };
+    std::vector<Smp> smp;
+    for (size_t r = 0; r < R; ++r) {
+        const size_t off = r * chunk, len = std::min(chunk, n - off);
+        for (size_t j = 0; j < len; j += sigma) smp.push_back(Smp{tk[off + j], off + j});
+    }
+    std::sort(smp.begin(), smp.end(), before);
+    std::vector<Smp> spl;
+    for (size_t i = every; i < smp.size(); i += every) spl.push_back(smp[i]);
+    const size_t nb = spl.size() + 1;  // blocks
+    std::vector<size_t> cut((nb + 1) * R);
+    for (size_t r = 0; r < R; ++r) {
+        const size_t off = r * chunk, len = std::min(chunk, n - off);
+        cut[r] = 0;
+        cut[nb * R + r] = len;
+        for (size_t i = 0; i < spl.size(); ++i) {  // run-r elements ordered before splitter i
+            size_t lo = 0, hi = len;
+            while (lo < hi) {
+                const size_t mid = lo + (hi - lo) / 2;
+                if (before(Smp{tk[off + mid], off + mid}, spl[i]))
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            cut[(i + 1) * R + r] = lo;
+        }
+    }
+    *nb_out = nb;
+    return cut;
+}
+
 template <class K, bool PAIRS>
 static msort_status host_sort_external(msort_ctx* ctx, const K* h_kin, const uint32_t* h_vin, K* h_kout,
                                        uint32_t* h_vout, size_t n, const msort_options* opt, cudaStream_t st,
@@ -922,47 +973,9 @@ static msort_status host_sort_external(msort_ctx* ctx, const K* h_kin, const uin
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
 
-    // 2. splitters from regular samples of the runs, compared by (key in
-    //    unsigned order, global position)
-    // A block from one splitter sample to the next holding m samples has at
-    // most (m + R) * sigma elements (each run adds at most one unsampled
-    // stretch of sigma - 1), so splitters every m = (k - 1) R samples with
-    // sigma = B / (k R) keep blocks within B while their expected size is
-    // (1 - 1/k) B: k = 16 when sigma stays >= 1, else 2.
-    const size_t kover = 16 * R <= B ? 16 : 2;
-    const size_t sigma = std::max<size_t>(1, B / (kover * R));
-    const size_t every = (kover - 1) * R;
-    struct Smp {
-        K u;
-        size_t g;
-    };
-    auto before = [](const Smp& a, const Smp& b) { return a.u < b.u || (a.u == b.u && a.g < b.g); };
-    std::vector<Smp> smp;
-    for (size_t r = 0; r < R; ++r) {
-        const size_t off = r * chunk, len = std::min(chunk, n - off);
-        for (size_t j = 0; j < len; j += sigma) smp.push_back(Smp{tk[off + j], off + j});
-    }
-    std::sort(smp.begin(), smp.end(), before);
-    std::vector<Smp> spl;
-    for (size_t i = every; i < smp.size(); i += every) spl.push_back(smp[i]);
-    const size_t nb = spl.size() + 1;  // blocks
-    std::vector<size_t> cut((nb + 1) * R);
-    for (size_t r = 0; r < R; ++r) {
-        const size_t off = r * chunk, len = std::min(chunk, n - off);
-        cut[r] = 0;
-        cut[nb * R + r] = len;
-        for (size_t i = 0; i < spl.size(); ++i) {  // run-r elements ordered before splitter i
-            size_t lo = 0, hi = len;
-            while (lo < hi) {
-                const size_t mid = lo + (hi - lo) / 2;
-                if (before(Smp{tk[off + mid], off + mid}, spl[i]))
-                    lo = mid + 1;
-                else
-                    hi = mid;
-            }
-            cut[(i + 1) * R + r] = lo;
-        }
-    }
+    // 2. splitters from regular samples of the runs
+    size_t nb = 0;
+    const std::vector<size_t> cut = external_cuts<K>(tk, n, chunk, B, &nb);
 
     // 3. every block: slices in, merged on the device, out, pipelined
     //    through the staging slots on the context's copy-in, compute and
@@ -1257,6 +1270,22 @@ msort_status msort_merge(msort_ctx* ctx, const void* d_a, const uint32_t* d_va, 
     if (e != cudaSuccess) return cuda_fail(e, ("merge launch" + last_launch_info()).c_str());
     (void)ks;
     return MSORT_OK;
+}
+
+size_t msort_external_plan(const void* h_runs, size_t n, msort_key_type kt, size_t chunk, size_t block_max,
+                           uint64_t* h_cuts, size_t cuts_cap) {
+    if (!h_runs || n == 0 || chunk == 0 || (kt != MSORT_U32 && kt != MSORT_U64)) return 0;
+    const size_t R = (n + chunk - 1) / chunk;
+    if (2 * R > block_max) return 0;
+    size_t nb = 0;
+    const std::vector<size_t> cut = kt == MSORT_U32
+                                        ? external_cuts<uint32_t>(static_cast<const uint32_t*>(h_runs), n, chunk,
+                                                                  block_max, &nb)
+                                        : external_cuts<uint64_t>(static_cast<const uint64_t*>(h_runs), n, chunk,
+                                                                  block_max, &nb);
+    if (h_cuts && cuts_cap >= cut.size())
+        for (size_t i = 0; i < cut.size(); ++i) h_cuts[i] = cut[i];
+    return nb;
 }
 
 msort_status msort_merge_runs(msort_ctx* ctx, const void* d_keys, const uint32_t* d_vals, const uint64_t* offsets,
