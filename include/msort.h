@@ -181,8 +181,8 @@ msort_status msort_merge(msort_ctx* ctx, const void* d_a, const uint32_t* d_va, 
  * allowed.  The merged array (equal keys in run order, values alongside)
  * goes to d_out (and d_vout; give both value pointers or neither), which must
  * not overlap the input.  It runs ceil(log2(non-empty runs)) rounds of the
- * pairwise merge tree (Section "Parallel Merge Sort": one round merges runs
- * 2j and 2j + 1 for every j), each a partition and a merge launch per 32
+ * pairwise merge tree (Section "MPI Merge Sort", "Merging the subarrays",
+ * Fig. 13: one round merges runs 2j and 2j + 1 for every j), each a partition and a merge launch per 32
  * pairs; a second buffer of offsets[nruns] elements comes from the
  * context's scratch.  Unsigned key types only (MSORT_ERR_UNSUPPORTED for the
  * others); MSORT_ERR_INVALID_ARG for decreasing offsets or overlapping
