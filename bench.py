@@ -68,11 +68,29 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _kernel_source_hash():
+KERNEL_SOURCES = ("paper_2211_16479_gb300/csrc/sort_kernels.cuh", "paper_2211_16479_gb300/csrc/merge4.cuh")
+
+
+def _code_only(src: str) -> str:
+    """C++ source with comments and whitespace removed."""
+    import re
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return "".join(src.split())
+
+
+def _kernel_source_hash(read=None):
+    """16 hex digits of sha256 over the sort kernels' code (comments and
+    whitespace removed): a comment edit keeps recorded counters valid, a
+    code edit invalidates them.  read(rel) -> text overrides the files."""
     h = hashlib.sha256()
-    for rel in ("paper_2211_16479_gb300/csrc/sort_kernels.cuh", "paper_2211_16479_gb300/csrc/merge4.cuh"):
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+    for rel in KERNEL_SOURCES:
+        if read is None:
+            with open(os.path.join(ROOT, rel)) as f:
+                text = f.read()
+        else:
+            text = read(rel)
+        h.update(_code_only(text).encode())
     return h.hexdigest()[:16]
 
 

@@ -6,7 +6,7 @@
  * fixed-size chunks independently (Section "Multiprocessing Merge Sort",
  * Figs. 6-7, where each chunk of ceil(n/p) elements goes to one worker), then
  * merge sorted runs pairwise, round after round, until one run is left
- * (Section "MPI Merge Sort", Fig. 13).  Here a chunk is a tile of T keys
+ * (Section "MPI Merge Sort", Figs. 16-17).  Here a chunk is a tile of T keys
  * sorted by one thread block, and a round is one global merge pass over the
  * whole array, so ceil(log2(ceil(n / T))) passes follow the tile sort.  The
  * merge takes from the left run on ties (Section "Sequential Merge Sort"
@@ -168,7 +168,7 @@ msort_status msort_segmented_sort(msort_ctx* ctx, void* d_keys, uint32_t* d_vals
 
 /* Stable merge of two sorted arrays: d_out[0:na+nb) = merge(d_a[0:na),
  * d_b[0:nb)), equal keys taking from d_a first (one round of the paper's
- * merge tree, Section "MPI Merge Sort", Fig. 13).  d_vout non-NULL merges
+ * merge tree, Section "MPI Merge Sort", Figs. 16-17).  d_vout non-NULL merges
  * values alongside (d_va, d_vb required).  The output must not overlap the
  * inputs.  Scratch: the context's split table. */
 msort_status msort_merge(msort_ctx* ctx, const void* d_a, const uint32_t* d_va, size_t na, const void* d_b,
@@ -182,7 +182,7 @@ msort_status msort_merge(msort_ctx* ctx, const void* d_a, const uint32_t* d_va, 
  * goes to d_out (and d_vout; give both value pointers or neither), which must
  * not overlap the input.  It runs ceil(log2(non-empty runs)) rounds of the
  * pairwise merge tree (Section "MPI Merge Sort", "Merging the subarrays",
- * Fig. 13: one round merges runs 2j and 2j + 1 for every j), each a partition and a merge launch per 32
+ * Figs. 16-17: one round merges runs 2j and 2j + 1 for every j), each a partition and a merge launch per 32
  * pairs; a second buffer of offsets[nruns] elements comes from the
  * context's scratch.  Unsigned key types only (MSORT_ERR_UNSUPPORTED for the
  * others); MSORT_ERR_INVALID_ARG for decreasing offsets or overlapping

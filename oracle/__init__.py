@@ -7,7 +7,7 @@ never imports it and shares no code with it.
 ``msort_oracle.c`` holds the plain top-down merge sort of Section "Sequential
 Merge Sort" (Fig. 2, split fixed to ``right = array[mid:]``), the two-way merge
 that takes from the left run on ties, the co-rank by running that merge, the
-multiprocessing/merge-tree variant (Figs. 6-7 and Fig. 13) and the segmented
+multiprocessing/merge-tree variant (Figs. 6-7 and 16-17) and the segmented
 sort.  ``mlp.py`` holds the fp64 reference of the small CDF network used by
 the learned partitioner.  This module compiles the C file with gcc and wraps
 it with ctypes.

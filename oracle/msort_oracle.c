@@ -24,7 +24,7 @@
  *  - oracle_par_sort_*: the multiprocessing design (Section "Multiprocessing
  *    Merge Sort", Figs. 6-7: chunks of ceil(n / p) elements, one worker per
  *    chunk) followed by the pairwise merge tree of Section "MPI Merge Sort"
- *    (Fig. 13: in each round the chunk in the upper half of the remaining
+ *    (Figs. 16-17: in each round the chunk in the upper half of the remaining
  *    workers is merged into its partner in the lower half, until one run is
  *    left), with POSIX threads as workers.  It returns the same bytes as
  *    oracle_sort_*; it exists to be timed.

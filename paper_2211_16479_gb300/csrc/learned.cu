@@ -1,7 +1,7 @@
 // Learned-CDF partitioner for the final merge passes.
 //
 // The paper has no learned component: its merge tree hands each pair of
-// runs to one process (Section "MPI Merge Sort", Fig. 13) and only cites
+// runs to one process (Section "MPI Merge Sort", Figs. 16-17) and only cites
 // Merge Path partitioning (Section "Related Research").  Here the co-rank
 // search that splits every merge pass into equal output blocks starts from
 // a prediction made by a small network, F: key -> [0, 1], an estimate of the

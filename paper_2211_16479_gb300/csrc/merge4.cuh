@@ -1,5 +1,5 @@
 // Four-way merge pass: two rounds of the merge tree (Section "MPI Merge
-// Sort", Fig. 13) per round trip through HBM.  Runs A, B, C, D of length L
+// Sort", Figs. 16-17) per round trip through HBM.  Runs A, B, C, D of length L
 // become one run of length 4L equal to merge(merge(A, B), merge(C, D)) with
 // equal keys ordered A, B, C, D -- exactly what two stable pairwise rounds
 // produce.  The merge passes of the sort run at the copy bandwidth, so

@@ -1,6 +1,6 @@
 // One round of the pairwise merge tree over sorted runs of arbitrary
 // lengths laid end to end (Section "MPI Merge Sort", "Merging the
-// subarrays", Fig. 13: each round merges neighbouring runs until one is
+// subarrays", Figs. 16-17: each round merges neighbouring runs until one is
 // left; here the runs may have unequal lengths, as the out-of-core sort's
 // slices and the sample sort's received pieces do).  Pair j merges [p[j], m[j]) with
 // [m[j], p[j+1]) into the same positions of the destination; equal keys keep

@@ -2,7 +2,7 @@
 //
 // One sort = one tile-sort launch (the chunk sort of Section
 // "Multiprocessing Merge Sort", Figs. 6-7) followed by P = ceil(log2(n / T))
-// rounds of the pairwise merge tree (Section "MPI Merge Sort", Fig. 13); each
+// rounds of the pairwise merge tree (Section "MPI Merge Sort", Figs. 16-17); each
 // round is a partition launch (merge-path co-ranks of every output block) and
 // a merge launch.  Buffers ping-pong between the caller's output and the
 // context's scratch; the tile sort writes to whichever of the two makes the

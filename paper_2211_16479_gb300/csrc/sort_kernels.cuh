@@ -3,7 +3,7 @@
 // The method (arXiv 2211.16479): sort fixed-size chunks independently
 // (Section "Multiprocessing Merge Sort", Figs. 6-7), then merge sorted runs
 // pairwise, one round at a time, until a single run is left (Section "MPI
-// Merge Sort", Fig. 13).  merge() itself is left undefined in the paper; it
+// Merge Sort", Figs. 16-17).  merge() itself is left undefined in the paper; it
 // is read here as the stable two-way merge that takes from the left run while
 // left <= right.
 //

@@ -1,7 +1,7 @@
 """Multi-GPU forms of the sort over torch.distributed (one process per GPU).
 
 ``tree_merge_sort`` is the paper's message-passing merge sort (Section "MPI
-Merge Sort": scatter, local sort, then the merge tree of Fig. 13): every
+Merge Sort": scatter, local sort, then the merge tree of Figs. 16-17): every
 rank sorts its chunk, then in rounds the upper half of the still-active
 ranks sends its run to a partner in the lower half, which merges, until
 rank 0 holds the whole sorted array.  The paper needs a power-of-two rank

@@ -1,6 +1,6 @@
 """The multi-rank paths on CPU ranks (gloo, world sizes 2-4).
 
-* the paper's merge tree (Section "MPI Merge Sort", Fig. 13) through
+* the paper's merge tree (Section "MPI Merge Sort", Figs. 16-17) through
   ``dist.tree_merge_sort``: rank schedule, run exchange and merge order give
   the stable sort of the gathered array (local sort and merge are the CPU
   oracle here; on GPU ranks they are the library's kernels);
@@ -76,7 +76,7 @@ def test_tree_merge_sort_cpu_ranks(world):
 
 
 def test_schedule_matches_paper_for_powers_of_two():
-    # Fig. 13 with 8 ranks: 4..7 -> 0..3, then 2,3 -> 0,1, then 1 -> 0
+    # the process tree of Fig. 16 with 8 ranks: 4..7 -> 0..3, then 2,3 -> 0,1, then 1 -> 0
     assert dist.merge_schedule(8) == [[(0, 4), (1, 5), (2, 6), (3, 7)], [(0, 2), (1, 3)], [(0, 1)]]
     assert dist.merge_schedule(1) == []
 
