@@ -34,8 +34,8 @@
  * Keys are compared as unsigned integers (u32, u64), as signed integers
  * (i32, i64), or, for floating-point keys held as bit patterns (f32, f64),
  * by IEEE 754 totalOrder; values ride along with their key.
- * Memory: the sorts allocate an n-element temporary (Table 1: merge sort takes
- * O(n) extra space) and return -1 if malloc fails, 0 on success.
+ * Memory: the sorts allocate an n-element temporary (a two-way merge needs
+ * room for its output) and return -1 if malloc fails, 0 on success.
  */
 #include <pthread.h>
 #include <stdint.h>
