@@ -95,7 +95,9 @@ typedef struct {
     int use_graph;      /* 1 = replay the launch sequence from a CUDA graph captured on the first
                            call with the same buffers, size and plan (plain sorts with
                            partition_mode 0, and segmented sorts); removes the per-launch
-                           host cost that dominates small sorts */
+                           host cost that dominates small sorts.  A context keeps up to 64
+                           graphs of each kind; a new one evicts the least recently used,
+                           after a device synchronisation */
     int merge_ways;     /* merge rounds per pass over memory: 0 = default (2); 2 = one round
                            of the pairwise merge tree per pass; 4 = two rounds per pass (four
                            runs merged at once; keys-only sorts with partition_mode 0; half

@@ -282,14 +282,24 @@ struct PlainGraphKey {
                         o.xform);
     }
 };
+// At most kMaxPlainGraphs graphs are kept; a new one evicts the least
+// recently used after the device has finished everything in flight (so no
+// evicted graph can still be running).
+constexpr size_t kMaxPlainGraphs = 64;
 struct PlainGraphs {
-    std::map<PlainGraphKey, std::pair<cudaGraphExec_t, unsigned long long>> exec;  // graph, launches
+    struct Entry {
+        cudaGraphExec_t exec;
+        unsigned long long launches;  // kernel launches one replay stands for
+        unsigned long long used;      // tick of the last replay
+    };
+    std::map<PlainGraphKey, Entry> exec;
+    unsigned long long tick = 0;
 };
 
 void plain_graphs_destroy(msort_ctx* ctx) {
     PlainGraphs* pg = static_cast<PlainGraphs*>(ctx->plain_graphs);
     if (!pg) return;
-    for (auto& kv : pg->exec) cudaGraphExecDestroy(kv.second.first);
+    for (auto& kv : pg->exec) cudaGraphExecDestroy(kv.second.exec);
     delete pg;
     ctx->plain_graphs = nullptr;
 }
@@ -303,6 +313,15 @@ static msort_status run_sort_graph(msort_ctx* ctx, const K* kin, const uint32_t*
                             pl.tile, pl.W, pl.passes, pl.ways, pl.xform};
     auto it = pg->exec.find(key);
     if (it == pg->exec.end()) {
+        if (pg->exec.size() >= kMaxPlainGraphs) {
+            auto lru = pg->exec.begin();
+            for (auto j = pg->exec.begin(); j != pg->exec.end(); ++j)
+                if (j->second.used < lru->second.used) lru = j;
+            cudaError_t e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+            cudaGraphExecDestroy(lru->second.exec);
+            pg->exec.erase(lru);
+        }
         cudaStream_t cap;
         cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
@@ -328,11 +347,12 @@ static msort_status run_sort_graph(msort_ctx* ctx, const K* kin, const uint32_t*
         e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-        it = pg->exec.emplace(key, std::make_pair(exec, nl)).first;
+        it = pg->exec.emplace(key, PlainGraphs::Entry{exec, nl, 0}).first;
     }
-    cudaError_t e = cudaGraphLaunch(it->second.first, st);
+    it->second.used = ++pg->tick;
+    cudaError_t e = cudaGraphLaunch(it->second.exec, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
-    ctx->launches += it->second.second;
+    ctx->launches += it->second.launches;
     return MSORT_OK;
 }
 

@@ -398,8 +398,12 @@ struct SegGraphKey {
     }
 };
 
+// At most kMaxSegGraphs graphs are kept; a new one evicts the least
+// recently used after the device has finished everything in flight.
+constexpr size_t kMaxSegGraphs = 64;
 struct GraphCache {
-    std::map<SegGraphKey, cudaGraphExec_t> seg;
+    std::map<SegGraphKey, std::pair<cudaGraphExec_t, unsigned long long>> seg;  // graph, tick of last use
+    unsigned long long tick = 0;
 };
 
 }  // namespace
@@ -412,7 +416,7 @@ GraphCache* graph_cache(msort_ctx* ctx) {
 void graphs_destroy(msort_ctx* ctx) {
     if (!ctx->graphs) return;
     GraphCache* gc = static_cast<GraphCache*>(ctx->graphs);
-    for (auto& kv : gc->seg) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : gc->seg) cudaGraphExecDestroy(kv.second.first);
     delete gc;
     ctx->graphs = nullptr;
 }
@@ -434,6 +438,15 @@ msort_status seg_sort(msort_ctx* ctx, K* keys, uint32_t* vals, const unsigned lo
                               ctx->seg_max_small, ctx->seg_large_tile};
         auto it = gc->seg.find(key);
         if (it == gc->seg.end()) {
+            if (gc->seg.size() >= kMaxSegGraphs) {
+                auto lru = gc->seg.begin();
+                for (auto j = gc->seg.begin(); j != gc->seg.end(); ++j)
+                    if (j->second.second < lru->second.second) lru = j;
+                e = cudaDeviceSynchronize();
+                if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+                cudaGraphExecDestroy(lru->second.first);
+                gc->seg.erase(lru);
+            }
             cudaStream_t cap;
             e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
             if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
@@ -457,9 +470,10 @@ msort_status seg_sort(msort_ctx* ctx, K* keys, uint32_t* vals, const unsigned lo
             e = cudaGraphInstantiate(&exec, graph, 0);
             cudaGraphDestroy(graph);
             if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-            it = gc->seg.emplace(key, exec).first;
+            it = gc->seg.emplace(key, std::make_pair(exec, 0ull)).first;
         }
-        e = cudaGraphLaunch(it->second, st);
+        it->second.second = ++gc->tick;
+        e = cudaGraphLaunch(it->second.first, st);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
         ctx->launches += 1 + SegPlan<K, PAIRS>::buckets(ctx).n + 1;
     }

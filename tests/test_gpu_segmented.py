@@ -124,3 +124,18 @@ def test_full_workload_50000_segments(ctx):
     ms.msort_ctx_sync(ctx)
     exp, _ = oracle.segmented_sort(keys, off)
     assert np.array_equal(to_host(d), exp)
+
+
+def test_graph_cache_evicts(ctx):
+    # more distinct segmented launch sequences than a context keeps as graphs
+    keys_buf = torch.empty(40000, dtype=torch.uint32, device="cuda")
+    for rep in range(2):
+        for i in range(70):
+            lens = np.full(10 + i, 37 + i, dtype=np.int64)
+            off = synth.segment_offsets(lens)
+            n = int(off[-1])
+            keys = synth.uniform_u32(n, 500 + 70 * rep + i)
+            keys_buf[:n].copy_(torch.from_numpy(keys))
+            ms.msort_segmented_sort(ctx, keys_buf[:n], to_dev(off), options={"use_graph": 1})
+            ms.msort_ctx_sync(ctx)
+            assert np.array_equal(to_host(keys_buf[:n]), oracle.segmented_sort(keys, off)[0]), (rep, i)

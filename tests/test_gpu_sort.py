@@ -217,3 +217,18 @@ def test_graph_replay(ctx, kt, pairs):
             dk.copy_(torch.from_numpy(keys))
             ms.msort_sort(ctx, dk, options={"use_graph": 1})
             assert np.array_equal(to_host(dk), oracle.sort(keys)[0])
+
+
+def test_graph_cache_evicts(ctx):
+    # more distinct (buffers, size) launch sequences than a context keeps as
+    # graphs (64): every result stays exact, and the evicted ones, met again,
+    # are captured again
+    buf = torch.empty(2000, dtype=torch.uint32, device="cuda")
+    out = torch.empty_like(buf)
+    for rep in range(2):
+        for i in range(70):
+            n = 1000 + 7 * i
+            keys = synth.uniform_u32(n, 300 + 70 * rep + i)
+            buf[:n].copy_(torch.from_numpy(keys))
+            ms.msort_sort_copy(ctx, buf[:n], out[:n], options={"use_graph": 1})
+            assert np.array_equal(to_host(out[:n]), oracle.sort(keys)[0]), (rep, n)
