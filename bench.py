@@ -12,9 +12,11 @@ Printed as one JSON line on rank 0.  Also reported:
   e2e           the same sorts through the host-buffer API: pinned host keys
                 in, host keys out, every copy inside the timed region; a
                 step enqueues the five sorts with msort_sort_host_async; the
-                timed region ends when the last step's results are in host
-                memory (sync_call_value: msort_sort_host, one sort at a
-                time);
+                timed region (the same number of steps as the value) ends
+                when the last step's results are in host memory
+                (sync_call_value: msort_sort_host, one sort at a time); both
+                are the median of --e2e-reps repetitions, all reported,
+                since the host link is shared with the machine's other work;
   roofline      the merge pass (the dominant kernel; one read and one write
                 of every key per launch) against measured HBM copy
                 bandwidth, its duration from CUDA events on its stream,
