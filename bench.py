@@ -215,11 +215,12 @@ def run_reference(args):
     import synth
     m = 1 << 22
     samples = [synth.u32_distribution(d, m, 1) for d in DISTS]
-    for _ in range(args.warmup):
-        pass  # the oracle has no warm state; warm-up steps are not needed
     cores = len(os.sched_getaffinity(0))
     import oracle
     lib = oracle.load()
+    for _ in range(args.warmup):  # untimed warm-up steps
+        for a in samples:
+            oracle.sort_inplace(np.array(a, copy=True), None, workers=cores, lib=lib)
     t_total, keys = 0.0, 0
     for _ in range(args.steps):
         for a in samples:
