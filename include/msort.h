@@ -147,7 +147,9 @@ msort_status msort_sort_pairs(msort_ctx* ctx, void* d_keys, uint32_t* d_vals, si
 
 /* Out-of-place stable sort: d_keys_in (and d_vals_in) are only read, the
  * result goes to d_keys_out (and d_vals_out).  d_vals_in/d_vals_out are both
- * NULL for a keys-only sort.  Input and output must not overlap. */
+ * NULL for a keys-only sort.  Each output is either the same buffer as its
+ * input (an in-place sort, which msort_sort and msort_sort_pairs are) or
+ * does not overlap it; a partial overlap gives undefined results. */
 msort_status msort_sort_copy(msort_ctx* ctx, const void* d_keys_in, const uint32_t* d_vals_in,
                              void* d_keys_out, uint32_t* d_vals_out, size_t n, msort_key_type kt,
                              const msort_options* opt, void* stream);
