@@ -101,3 +101,18 @@ def test_signed_zero_order():
     a = np.array([0.0, -0.0, 1.0, -0.0, 0.0, -1.0], dtype=np.float32)
     k, v = oracle.sort(a, np.arange(6, dtype=np.uint32))
     assert list(v) == [5, 1, 3, 0, 4, 2]  # -1, -0 (input order), +0 (input order), 1
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.int64, np.float32, np.float64])
+def test_parallel_oracle_agrees(dtype):
+    # the chunked parallel oracle (chunks + pairwise merge tree) orders
+    # signed and float keys exactly as the sequential one, values included
+    size = np.dtype(dtype).itemsize
+    bits = RNG.integers(0, 2 ** (8 * size), size=100_003, dtype=np.uint64 if size == 8 else np.uint32)
+    keys = bits.view(dtype).copy()
+    keys[::7] = keys[3]
+    vals = np.arange(keys.size, dtype=np.uint32)
+    a, av = oracle.sort(keys, vals)
+    for workers in (1, 3, 8):
+        b, bv = oracle.par_sort(keys, vals, workers=workers)
+        assert np.array_equal(a.view(np.uint8), b.view(np.uint8)) and np.array_equal(av, bv), workers
