@@ -55,3 +55,19 @@ def test_four_way_scratch_is_small(kt, ks):
     s2 = ms.msort_scratch_bytes(n, kt, False)
     assert s2 >= n * ks and s4 > s2
     assert s4 - s2 < 0.05 * n * ks
+
+
+@pytest.mark.parametrize("kt,width", [(ms.MSORT_I32, ms.MSORT_U32), (ms.MSORT_F32, ms.MSORT_U32),
+                                      (ms.MSORT_I64, ms.MSORT_U64), (ms.MSORT_F64, ms.MSORT_U64)])
+def test_transformed_keys_plan_like_unsigned_and_refuse_other_passes(kt, width):
+    # signed and float keys sort as unsigned keys of their width after the
+    # order-preserving transform, so their plans match; four-way passes and
+    # the learned partition do not take transformed keys and are refused
+    n = (1 << 20) + 3
+    assert ms.msort_plan_info(n, kt, False) == ms.msort_plan_info(n, width, False)
+    assert ms.msort_scratch_bytes(n, kt, True) == ms.msort_scratch_bytes(n, width, True)
+    for opts in ({"merge_ways": 4}, {"partition_mode": 1}):
+        assert ms.msort_scratch_bytes(n, kt, False, opts) == 0
+        with pytest.raises(ms.MsortError) as e:
+            ms.msort_plan_passes(n, kt, False, opts)
+        assert e.value.status == ms.MSORT_ERR_INVALID_ARG
