@@ -119,9 +119,10 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, out_dir: str | None = None):
+        import tempfile
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = os.path.join(out_dir or tempfile.gettempdir(), f"msort_clocks_gpu{gpu_index}_{os.getpid()}.csv")
         self.gpu = gpu_index
 
     def start(self):
@@ -162,6 +163,16 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def _multiset_hash(t):
+    """Order-independent hash of a device key array: the sum of a 64-bit
+    mix of every key (wrapping), computed on the device."""
+    import torch
+    x = t.to(torch.int64) if t.dtype in (torch.uint32, torch.int32) else t.view(torch.int64)
+    x = x * -4658895280553007687 ^ (x >> 29 & 0x7FFFFFFFF)  # 0xBF58476D1CE4E5B9 as int64
+    x = x * -7723592293110705685  # 0x94D049BB133111EB as int64
+    return int(x.sum().item())
 
 
 def cpu_oracle_rate(sample_keys, seconds_target=12.0):
@@ -284,9 +295,11 @@ def run_ours(args):
         step()
     barrier()
 
-    # correctness guard on the last warm-up output: sorted, same multiset
+    # correctness guard on the last warm-up output: sorted, and the same
+    # multiset of keys as its input
     last = out.to(torch.int64)
     assert bool((last[1:] >= last[:-1]).all()), "output not sorted"
+    assert _multiset_hash(out) == _multiset_hash(inputs[-1]), "output is not a permutation of the input"
     del last
 
     def timed(profiled):
@@ -398,6 +411,13 @@ def run_ours(args):
                          f"merge sort + pairwise merge tree on {cores} threads",
                "context": cpu_context_rates(sample)}
 
+    # the chosen forms against the plain sort (rank 0, after the collectives)
+    chosen = None
+    if rank == 0 and not args.no_chosen:
+        if not args.no_e2e:
+            del h_in, h_out, h_outs
+        chosen = chosen_vs_plain(args, h, dev, stream)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -431,6 +451,7 @@ def run_ours(args):
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clocks,
+            "chosen_vs_plain": chosen,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -625,8 +646,120 @@ def run_pairs(args):
     ctx.close()
 
 
-def run_segmented(args):
-    """50,000 uint32 arrays with lengths log-uniform in [1, 65536]."""
+# ---------------------------------------------------------------------------
+# The chosen forms against the plain sort (learned partition, batched
+# segmented sort, continuous-batching server): each times its two arms in
+# interleaved repetitions (A, B, A, B, ...) on identical inputs and checks on
+# the device that both arms give identical output.
+# ---------------------------------------------------------------------------
+def _spread(xs):
+    xs = [float(x) for x in xs]
+    return {"min": min(xs), "median": statistics.median(xs), "max": max(xs), "samples": [round(x, 4) for x in xs]}
+
+
+def _interleaved(arms, reps, stream):
+    """arms: {name: (prepare, run)}; prepare() is untimed, run() is timed by
+    CUDA events on `stream`.  Returns {name: [ms per repetition]}."""
+    import torch
+    out = {k: [] for k in arms}
+    for _ in range(reps):
+        for name, (prep, run) in arms.items():
+            if prep is not None:
+                prep()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run()
+            e1.record(stream)
+            e1.synchronize()
+            out[name].append(e0.elapsed_time(e1))
+    return out
+
+
+def _sort_bytes(n, tile, key_bytes=4):
+    """Algorithmic bytes of one sort: a read and a write of every key per
+    pass, tile sort plus ceil(log2(n / tile)) merge passes."""
+    passes = 0
+    L = tile
+    while L < n:
+        L *= 2
+        passes += 1
+    return 2 * n * key_bytes * (1 + passes)
+
+
+def form_learned(h, dev, stream, reps, log2n, warmup):
+    """2^log2n uint32 keys of the lognormal mixture: the exact merge-path
+    partition (the plain sort) against the learned partition in its default
+    mode (the passes whose runs hold >= 2^22 keys), with the model-free
+    length-ratio start as the ablation arm."""
+    import torch
+
+    import paper_2211_16479_gb300 as ms
+    from synth import torch_gen
+    n = 1 << log2n
+    src = torch_gen.lognormal3_u32(n, 1, device=dev)
+    modes = {"exact": {}, "learned": {"partition_mode": 1}, "ratio_guess": {"partition_mode": 2}}
+    outs = {k: torch.empty_like(src) for k in modes}
+
+    def sorter(k):
+        return lambda: ms.msort_sort_copy(h, src, outs[k], options=modes[k], stream=stream)
+    for _ in range(warmup):
+        for k in modes:
+            sorter(k)()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev.index or 0)
+    sampler.start()
+    t = _interleaved({k: (None, sorter(k)) for k in modes}, reps, stream)
+    clocks = sampler.stop()
+    identical = {k: bool(torch.equal(outs[k].view(torch.int32), outs["exact"].view(torch.int32))) for k in modes}
+    del outs["ratio_guess"]
+    # partition time per pass (event pairs only, no probe counting)
+    per_pass, probes = {}, {}
+    for k in modes:
+        ms.msort_ctx_set_profiling(h, 1)
+        ms.msort_sort_copy(h, src, outs["exact"], options=modes[k], stream=stream)
+        per_pass[k] = [round(x * 1e3, 2) for x in ms.msort_ctx_kernel_log(h, ms.MSORT_KERNEL_PARTITION)]
+        ms.msort_ctx_set_profiling(h, 0)
+    # probes per search (level 2 counts them; not timed)
+    for name, o in (("exact", {"partition_mode": 3, "learned_passes": 64}),
+                    ("learned", {"partition_mode": 1, "learned_passes": 64}),
+                    ("ratio_guess", {"partition_mode": 2, "learned_passes": 64})):
+        ms.msort_ctx_set_profiling(h, 2)
+        ms.msort_sort_copy(h, src, outs["exact"], options=o, stream=stream)
+        pr, se = ms.msort_ctx_partition_stats(h)
+        ms.msort_ctx_set_profiling(h, 0)
+        probes[name] = pr / se if se else None
+    _, err = ms.msort_learned_model(h)
+    T, _, P = ms.msort_plan_info(n, ms.MSORT_U32, False)
+    first_guided = next((i for i in range(P) if (T << i) >= (1 << 22)), P)
+    med = {k: statistics.median(v) for k, v in t.items()}
+    peak, kind = _peaks()
+    alg = _sort_bytes(n, T)
+    return {"workload": f"2^{log2n} uint32 keys, lognormal mixture (0.5/0.3/0.2; ln-space mu 14/18/21; "
+                        f"sigma 1/0.5/0.3), keys only, out of place",
+            "n": n, "repetitions": reps, "order": "interleaved exact, learned, ratio_guess per repetition",
+            "plain_arm": "exact merge-path partition (partition_mode 0)",
+            "chosen_arm": "learned partition, default mode (partition_mode 1: guided search on the passes whose runs "
+                          f"hold >= 2^22 keys, passes {first_guided}..{P - 1} of {P})",
+            "ms": {k: _spread(v) for k, v in t.items()},
+            "speedup": med["exact"] / med["learned"],
+            "speedup_vs_ratio_guess": med["ratio_guess"] / med["learned"],
+            "identical_output": identical["learned"] and identical["ratio_guess"],
+            "partition_us_per_pass": per_pass,
+            "partition_us_guided_passes": {k: round(sum(v[first_guided:]), 1) for k, v in per_pass.items()},
+            "probes_per_search_all_passes": probes,
+            "model_max_sample_error": err,
+            "roofline": {"bound": "hbm", "algorithmic_bytes": alg,
+                         "frac_of_peak": {k: alg / (m * 1e-3) / 1e9 / peak for k, m in med.items()},
+                         "peak": peak, "peak_kind": kind},
+            "clocks": clocks}
+
+
+def form_segmented(h, dev, stream, reps, warmup):
+    """50,000 uint32 arrays with lengths log-uniform in [1, 65536]: the
+    batched segmented sort (one persistent launch per length bucket, CUDA
+    graph replay) against the plain sort giving the same result (one stable
+    sort of the 64-bit keys (segment index << 32 | key))."""
     import numpy as np
     import torch
 
@@ -636,129 +769,76 @@ def run_segmented(args):
     lens = synth.segment_lengths(50000, 1)
     off = synth.segment_offsets(lens)
     n = int(off[-1])
-    src = torch_gen.uniform_u32(n, 1, device="cuda")
+    src = torch_gen.uniform_u32(n, 1, device=dev)
     work = torch.empty_like(src)
-    doff = torch.from_numpy(off).cuda()
-    ctx = ms.Context(0)
-    h = ctx.handle
-    copy_ms = _events_ms(lambda: work.copy_(src), 5)
-
-    def seg(graph):
-        work.copy_(src)
-        ms.msort_segmented_sort(h, work, doff, options={"use_graph": graph})
-    res = {}
-    for graph in (0, 1):
-        for _ in range(args.warmup):
-            seg(graph)
-        res[graph] = _events_ms(lambda: seg(graph), args.steps) - copy_ms
-    ms.msort_ctx_sync(h)
-    # plain sort alternative with identical output: one global sort of
-    # (segment index << 32 | key) as 64-bit keys
-    seg_id = torch.repeat_interleave(torch.arange(len(lens), device="cuda", dtype=torch.int64),
-                                     torch.from_numpy(lens).cuda())
+    doff = torch.from_numpy(off.astype(np.int64)).to(dev)
+    seg_id = torch.repeat_interleave(torch.arange(len(lens), device=dev, dtype=torch.int64),
+                                     torch.from_numpy(lens).to(dev))
     comp = ((seg_id << 32) | src.to(torch.int64)).view(torch.uint64)
-    out = torch.empty_like(comp)
-    for _ in range(args.warmup):
-        ms.msort_sort_copy(h, comp, out)
-    plain = _events_ms(lambda: ms.msort_sort_copy(h, comp, out), args.steps)
-    same = bool(torch.equal((out.view(torch.int64) & 0xFFFFFFFF).to(torch.uint32).view(torch.int32),
-                            work.view(torch.int32)))
-    # plain sort per segment, looped, on the 500 longest segments (extrapolated by keys)
-    big = np.argsort(-lens)[:500]
-    def loop():
-        for s in big:
-            ms.msort_sort(h, work[int(off[s]):int(off[s + 1])])
-    loop_ms = _events_ms(loop, 1)
-    loop_keys = int(lens[big].sum())
-    best = min(res.values())
-    line = _base_line("Gkeys/s sorted (batched segmented sort, 50,000 uint32 arrays)", n / best / 1e6, "Gkeys/s",
-                      args, best,
-                      {"workload": "50,000 uint32 arrays, lengths log-uniform in [1, 65536], uniform keys", "n": n,
-                       "segments": 50000},
-                      dtype="u32",
-                      eager_ms=res[0], graph_ms=res[1],
-                      plain_composite_sort={"ms": plain, "gkeys_per_s": n / plain / 1e6,
-                                            "identical_output": same},
-                      plain_per_segment_loop={"segments": 500, "keys": loop_keys, "ms": loop_ms,
-                                              "gkeys_per_s": loop_keys / loop_ms / 1e6},
-                      speedup_vs_plain=plain / best)
-    print(json.dumps(line), flush=True)
-    ctx.close()
+    del seg_id
+    pout = torch.empty_like(comp)
+    opt = {"use_graph": 1}
+    arms = {"plain": (None, lambda: ms.msort_sort_copy(h, comp, pout, options=opt, stream=stream)),
+            "segmented": (lambda: work.copy_(src),
+                          lambda: ms.msort_segmented_sort(h, work, doff, options=opt, stream=stream))}
+    for _ in range(warmup):
+        for prep, run in arms.values():
+            if prep:
+                prep()
+            run()
+    ms.msort_ctx_sync(h, stream)
+    sampler = ClockSampler(dev.index or 0)
+    sampler.start()
+    t = _interleaved(arms, reps, stream)
+    clocks = sampler.stop()
+    ms.msort_ctx_sync(h, stream)
+    same = bool(torch.equal((pout.view(torch.int64) & 0xFFFFFFFF).to(torch.int32), work.view(torch.int32)))
+    med = {k: statistics.median(v) for k, v in t.items()}
+    # algorithmic bytes: on-chip segments (<= 16896 keys) move once; longer
+    # ones add ceil(log2(len / 16896)) merge passes
+    seg_bytes = sum(_sort_bytes(int(L), 16896) for L in lens if L > 1)
+    T64, _, _ = ms.msort_plan_info(n, ms.MSORT_U64, False)
+    plain_bytes = _sort_bytes(n, T64, 8)
+    peak, kind = _peaks()
+    return {"workload": "50,000 uint32 arrays, lengths log-uniform in [1, 65536], uniform keys, in place",
+            "n": n, "segments": 50000, "repetitions": reps, "order": "interleaved plain, segmented",
+            "plain_arm": "one stable plain sort of the 64-bit keys (segment << 32 | key), CUDA-graph replay",
+            "chosen_arm": "msort_segmented_sort, CUDA-graph replay",
+            "ms": {k: _spread(v) for k, v in t.items()},
+            "gkeys_per_s": {k: n / m / 1e6 for k, m in med.items()},
+            "speedup": med["plain"] / med["segmented"],
+            "identical_output": same,
+            "roofline": {"bound": "hbm", "algorithmic_bytes": {"segmented": seg_bytes, "plain": plain_bytes},
+                         "frac_of_peak": {"segmented": seg_bytes / (med["segmented"] * 1e-3) / 1e9 / peak,
+                                          "plain": plain_bytes / (med["plain"] * 1e-3) / 1e9 / peak},
+                         "peak": peak, "peak_kind": kind},
+            "clocks": clocks}
 
 
-def run_learned(args):
-    """2^30 uint32 keys from the lognormal mixture: exact vs learned partition."""
-    import torch
-
-    import paper_2211_16479_gb300 as ms
-    from synth import torch_gen
-    n = 1 << args.learned_log2n
-    src = torch_gen.lognormal3_u32(n, 1, device="cuda")
-    out = torch.empty_like(src)
-    ctx = ms.Context(0)
-    h = ctx.handle
-    modes = {"exact": {}, "learned_final_passes": {"partition_mode": 1},
-             "learned_all_passes": {"partition_mode": 1, "learned_passes": 64},
-             "ratio_guess_all_passes": {"partition_mode": 2, "learned_passes": 64}}
-    times, same = {}, {}
-    ref = None
-    for name, o in modes.items():
-        for _ in range(args.warmup):
-            ms.msort_sort_copy(h, src, out, options=o)
-        times[name] = _events_ms(lambda: ms.msort_sort_copy(h, src, out, options=o), args.steps)
-        if ref is None:
-            ref = out.clone()
-        same[name] = bool(torch.equal(out.view(torch.int32), ref.view(torch.int32)))
-    probes = {}
-    for name, o in list(modes.items()) + [("exact_counted_all_passes", {"partition_mode": 3, "learned_passes": 64})]:
-        ms.msort_ctx_set_profiling(h, True)
-        ms.msort_sort_copy(h, src, out, options=o)
-        torch.cuda.synchronize()
-        pl, pt = ms.msort_ctx_kernel_times(h, ms.MSORT_KERNEL_PARTITION)
-        pr, se = ms.msort_ctx_partition_stats(h)
-        ms.msort_ctx_set_profiling(h, False)
-        probes[name] = {"partition_ms": pt, "probes_per_search": (pr / se) if se else None}
-    _, err = ms.msort_learned_model(h)
-    best = times["learned_all_passes"]
-    line = _base_line(f"Gkeys/s sorted (2^{args.learned_log2n} uint32 lognormal mixture, learned co-rank partition)",
-                      n / best / 1e6,
-                      "Gkeys/s", args, best,
-                      {"workload": f"2^{args.learned_log2n} uint32 keys, lognormal mixture (0.5/0.3/0.2; mu 14/18/21; sigma 1/0.5/0.3)",
-                       "n": n},
-                      dtype="u32",
-                      modes_ms=times, gkeys_per_s={k: n / v / 1e6 for k, v in times.items()},
-                      speedup_vs_exact=times["exact"] / best,
-                      identical_output_to_exact=same,
-                      partition=probes, model_max_sample_error=err)
-    print(json.dumps(line), flush=True)
-    ctx.close()
-
-
-def run_serving(args):
-    """Poisson arrivals of sort requests, sizes log-uniform in [2^10, 2^24],
-    8 GB budget: continuous batching (8 slots) vs a FIFO queue alone (1 slot)."""
-    import threading
-
+def form_serving(dev, reps, count, rho):
+    """Sort requests with sizes log-uniform in [2^10, 2^24] (uniform uint32
+    keys, 8 GB device budget): continuous batching (8 slots) against the
+    same requests served one at a time in arrival order (1 slot, the plain
+    sort per request), at saturation (all submitted at once) and under
+    Poisson arrivals at `rho` x the one-slot service rate."""
     import numpy as np
     import torch
 
     import paper_2211_16479_gb300 as ms
     import synth
     from synth import torch_gen
-    count = 2000
     _, sizes = synth.poisson_requests(count, 1, rate_per_s=1.0)
     offs = np.concatenate([[0], np.cumsum(sizes)])
     total = int(offs[-1])
-    buf = torch.empty(total, dtype=torch.uint32, device="cuda")
-
-    def refill():
-        buf.copy_(torch_gen.uniform_u32(total, 7, device="cuda"))
-        torch.cuda.synchronize()
+    pristine = torch_gen.uniform_u32(total, 7, device=dev)
+    buf = torch.empty_like(pristine)
+    sort_bytes = sum(_sort_bytes(int(x), 16896) for x in sizes)
 
     def run(slots, rate):
-        refill()
-        t_arr, _ = synth.poisson_requests(count, 1, rate_per_s=rate) if rate else (np.zeros(count), None)
-        with ms.Server(0, mem_budget_bytes=8 << 30, max_slots=slots) as srv:
+        buf.copy_(pristine)
+        torch.cuda.synchronize()
+        t_arr = synth.poisson_requests(count, 1, rate_per_s=rate)[0] if rate else None
+        with ms.Server(dev.index or 0, mem_budget_bytes=8 << 30, max_slots=slots) as srv:
             ids = []
             t0 = time.perf_counter()
             for i in range(count):
@@ -770,29 +850,101 @@ def run_serving(args):
                 srv.wait(rid, 600000.0)
             wall = time.perf_counter() - t0
             st = srv.stats()
-        return {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+        return {"wall_ms": wall * 1e3, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
                 "gkeys_per_s": total / wall / 1e9, "max_inflight": st["max_inflight"],
                 "arena_high_water_gb": st["arena_high_water"] / 1e9}
 
-    # saturation: everything submitted at once
-    sat1 = run(1, 0.0)
-    sat8 = run(8, 0.0)
-    mean_keys = float(np.mean(sizes))
-    mu = sat1["gkeys_per_s"] * 1e9 / mean_keys        # plain service rate, requests/s
-    loads = {}
-    for rho in (0.3, 0.6, 0.9):
-        loads[str(rho)] = {"fifo_1_slot": run(1, rho * mu), "continuous_8_slots": run(8, rho * mu),
-                           "rate_per_s": rho * mu}
-    line = _base_line("Gkeys/s served (continuous batching of sort requests, saturation)", sat8["gkeys_per_s"],
-                      "Gkeys/s", args, 1e3 * total / (sat8["gkeys_per_s"] * 1e9),
-                      {"workload": "2000 uint32 sort requests, sizes log-uniform in [2^10, 2^24], Poisson arrivals, "
-                                   "8 GB budget", "requests": count, "keys": total},
-                      dtype="u32",
-                      saturation={"fifo_1_slot": sat1, "continuous_8_slots": sat8},
-                      speedup_vs_fifo=sat8["gkeys_per_s"] / sat1["gkeys_per_s"],
-                      poisson_load=loads, p50_ms=loads["0.6"]["continuous_8_slots"]["p50_ms"],
-                      p99_ms=loads["0.6"]["continuous_8_slots"]["p99_ms"])
-    print(json.dumps(line), flush=True)
+    run(1, 0.0)  # warm-up: the servers' first launches and buffers
+    ref = None
+    run(1, 0.0)
+    ref = buf.clone()
+    run(8, 0.0)
+    same = bool(torch.equal(buf.view(torch.int32), ref.view(torch.int32)))
+    del ref
+    mu = run(1, 0.0)["gkeys_per_s"] * 1e9 / float(np.mean(sizes))  # one-slot service rate, requests/s
+    rate = rho * mu
+    sampler = ClockSampler(dev.index or 0)
+    sampler.start()
+    res = {"saturation": {"fifo_1_slot": [], "continuous_8_slots": []},
+           "poisson": {"fifo_1_slot": [], "continuous_8_slots": []}}
+    for _ in range(reps):
+        res["saturation"]["fifo_1_slot"].append(run(1, 0.0))
+        res["saturation"]["continuous_8_slots"].append(run(8, 0.0))
+        res["poisson"]["fifo_1_slot"].append(run(1, rate))
+        res["poisson"]["continuous_8_slots"].append(run(8, rate))
+    clocks = sampler.stop()
+
+    def summary(runs):
+        return {k: _spread([r[k] for r in runs]) for k in ("wall_ms", "p50_ms", "p99_ms", "gkeys_per_s")} | \
+            {"max_inflight": max(r["max_inflight"] for r in runs),
+             "arena_high_water_gb": max(r["arena_high_water_gb"] for r in runs)}
+    out = {ph: {arm: summary(v) for arm, v in d.items()} for ph, d in res.items()}
+    sat_f = statistics.median(r["wall_ms"] for r in res["saturation"]["fifo_1_slot"])
+    sat_c = statistics.median(r["wall_ms"] for r in res["saturation"]["continuous_8_slots"])
+    p99_f = statistics.median(r["p99_ms"] for r in res["poisson"]["fifo_1_slot"])
+    p99_c = statistics.median(r["p99_ms"] for r in res["poisson"]["continuous_8_slots"])
+    p50_c = statistics.median(r["p50_ms"] for r in res["poisson"]["continuous_8_slots"])
+    peak, kind = _peaks()
+    return {"workload": f"{count} uint32 sort requests, sizes log-uniform in [2^10, 2^24], uniform keys, in place, "
+                        "8 GB device budget", "requests": count, "keys": total,
+            "repetitions": reps, "order": "interleaved per repetition: saturation 1 slot, 8 slots; Poisson 1, 8",
+            "plain_arm": "fifo_1_slot: the same requests sorted one at a time in arrival order",
+            "chosen_arm": "continuous_8_slots: up to 8 requests on the GPU at once, admitted as slots and memory free",
+            "poisson_rate_per_s": rate, "offered_load": rho,
+            "saturation": out["saturation"], "poisson": out["poisson"],
+            "speedup": sat_f / sat_c, "speedup_meaning": "saturation wall time, one slot / eight slots",
+            "p50_ms": p50_c, "p99_ms": p99_c, "p99_fifo_ms": p99_f,
+            "identical_output": same,
+            "roofline": {"bound": "hbm", "algorithmic_bytes": sort_bytes,
+                         "frac_of_peak_saturation": {"fifo_1_slot": sort_bytes / (sat_f * 1e-3) / 1e9 / peak,
+                                                     "continuous_8_slots": sort_bytes / (sat_c * 1e-3) / 1e9 / peak},
+                         "peak": peak, "peak_kind": kind},
+            "clocks": clocks}
+
+
+def chosen_vs_plain(args, h, dev, stream):
+    import torch
+    r = {}
+    r["learned"] = form_learned(h, dev, stream, args.chosen_reps, args.learned_log2n, 2)
+    torch.cuda.empty_cache()
+    r["segmented"] = form_segmented(h, dev, stream, args.chosen_reps, 2)
+    torch.cuda.empty_cache()
+    r["serving"] = form_serving(dev, args.chosen_reps, args.serving_requests, 0.9)
+    torch.cuda.empty_cache()
+    return r
+
+
+def _form_line(name, f, args):
+    med = {k: v["median"] for k, v in f["ms"].items()} if "ms" in f else None
+    if name == "serving":
+        c = f["saturation"]["continuous_8_slots"]["gkeys_per_s"]["median"]
+        return _base_line("Gkeys/s served (continuous batching of sort requests, saturation)", c, "Gkeys/s", args,
+                          f["saturation"]["continuous_8_slots"]["wall_ms"]["median"],
+                          {"workload": f["workload"], "requests": f["requests"], "keys": f["keys"]},
+                          dtype="u32", detail=f)
+    chosen = "learned" if name == "learned" else "segmented"
+    return _base_line(f"Gkeys/s sorted ({name} form vs plain sort)", f["n"] / med[chosen] / 1e6, "Gkeys/s", args,
+                      med[chosen], {"workload": f["workload"], "n": f["n"]}, dtype="u32", detail=f)
+
+
+def run_form(args):
+    import torch
+
+    import paper_2211_16479_gb300 as ms
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = ms.Context(0)
+    h = ctx.handle
+    reps = max(args.chosen_reps, 5)
+    if args.workload == "learned":
+        f = form_learned(h, dev, stream, reps, args.learned_log2n, args.warmup)
+    elif args.workload == "segmented":
+        f = form_segmented(h, dev, stream, reps, args.warmup)
+    else:
+        f = form_serving(dev, reps, args.serving_requests, 0.9)
+    print(json.dumps(_form_line(args.workload, f, args)), flush=True)
+    ctx.close()
 
 
 def main():
@@ -810,6 +962,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None, help="steps of the end-to-end measurement (default: --steps)")
     ap.add_argument("--e2e-reps", type=int, default=5, help="repetitions of the end-to-end measurement (median)")
     ap.add_argument("--learned-log2n", type=int, default=30, help="size of the learned-partition workload (log2)")
+    ap.add_argument("--chosen-reps", type=int, default=5, help="interleaved repetitions per chosen-vs-plain arm")
+    ap.add_argument("--serving-requests", type=int, default=2000, help="requests per serving run")
+    ap.add_argument("--no-chosen", action="store_true", help="skip the chosen-vs-plain comparisons")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -823,8 +978,8 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.workload != "sort":
-        fn = {"small": run_small, "float": run_float, "external": run_external, "pairs": run_pairs, "segmented": run_segmented, "learned": run_learned,
-              "serving": run_serving}
+        fn = {"small": run_small, "float": run_float, "external": run_external, "pairs": run_pairs,
+              "segmented": run_form, "learned": run_form, "serving": run_form}
         fn[args.workload](args)
         return 0
     return run_ours(args)

@@ -305,9 +305,12 @@ msort_status msort_server_destroy(msort_server* s);
  * sort as msort_sort_copy with the default plan, but takes its scratch from
  * a fixed 48 MiB array compiled into the library (held on every GPU that
  * loads the library until the process exits), and calls no allocator.
- *  - Works on the calling thread's current device.  The first call on a
- *    device looks up the array's device address (cudaGetSymbolAddress);
- *    make that first call before any stream capture.
+ *  - Works in the calling thread's current CUDA context (the current
+ *    device's primary context if none is current).  The first call under a
+ *    context looks up the array's device address there
+ *    (cudaGetSymbolAddress, which allocates nothing); make that first call
+ *    before any stream capture.  The address is kept per context id, so a
+ *    device reset or another context gets its own lookup.
  *  - n above msort_noalloc_max_keys(kt, with_vals) is rejected with
  *    MSORT_ERR_INVALID_ARG before any work is enqueued.
  *  - All calls on a device share the one array: calls whose work overlaps
@@ -315,12 +318,36 @@ msort_status msort_server_destroy(msort_server* s);
  *    wrong results.  Order them on one stream.
  *  - d_keys_out may equal d_keys_in (in place); value pointers are both
  *    NULL (keys only) or both set.  Errors a kernel detects on the device
- *    are not reported here (there is no context to carry them). */
+ *    (a bounded wait that gave up) go to a status word inside the array,
+ *    cleared at the start of every call: msort_noalloc_sync reads it. */
 msort_status msort_sort_noalloc(const void* d_keys_in, const uint32_t* d_vals_in, void* d_keys_out,
                                 uint32_t* d_vals_out, size_t n, msort_key_type kt, void* stream);
+/* Waits for `stream`, then reports what the kernels of the last
+ * msort_sort_noalloc call in the current context recorded: MSORT_OK, or
+ * MSORT_ERR_TIMEOUT for a bounded wait that gave up (the word is then
+ * cleared).  Allocates nothing; the word is shared like the array, so call
+ * it after the call it checks and before the next one is enqueued. */
+msort_status msort_noalloc_sync(void* stream);
 /* Largest n msort_sort_noalloc accepts for this key type (with or without
  * values). */
 size_t msort_noalloc_max_keys(msort_key_type kt, int with_vals);
+
+/* ---- failure detection ------------------------------------------------ */
+
+/* Self-test of the bounded device waits.  The paper's only failure remark is
+ * that a blocking Send/Recv waits forever when its peer has failed (Section
+ * "MPI Merge Sort"); here no device wait is unbounded: a block that waits
+ * for its bulk copies longer than a cycle limit (about one second in every
+ * production kernel) records MSORT_ERR_TIMEOUT in the context's status word,
+ * waits once more (bounded) for any copy of its own still in flight, and
+ * returns.  This call enqueues on `stream` one production merge block whose
+ * barrier expects one arrival more than the block makes, with the limit set
+ * to limit_cycles (1000 .. 2e9 SM cycles): the block issues no copy, gives up
+ * after about 2 x limit_cycles and writes no output.  The next
+ * msort_ctx_sync then returns MSORT_ERR_TIMEOUT and clears the word; the
+ * context stays usable.  Touches no caller memory; MSORT_ERR_INVALID_ARG for
+ * a limit outside the range. */
+msort_status msort_selftest_wait_timeout(msort_ctx* ctx, long long limit_cycles, void* stream);
 
 /* ---- autotuning ---------------------------------------------------------- */
 
@@ -372,7 +399,7 @@ msort_status msort_learned_model(msort_ctx* ctx, float* h_params, float* h_err);
  * training a fresh model per sort.  Synchronises the device. */
 msort_status msort_learned_set_model(msort_ctx* ctx, const float* h_params, float err);
 /* Probes (tests of A[a] <= B[d-1-a]) and searches made by guided partition
- * launches (modes 1-3) while profiling was on; resets the counts.
+ * launches (modes 1-3) while profiling was at level 2; resets the counts.
  * Synchronises the device. */
 msort_status msort_ctx_partition_stats(msort_ctx* ctx, uint64_t* probes, uint64_t* searches);
 
@@ -384,13 +411,20 @@ enum { MSORT_KERNEL_TILE = 0, MSORT_KERNEL_PARTITION = 1, MSORT_KERNEL_MERGE = 2
 
 /* on != 0: bracket every later launch with CUDA events on its own stream
  * (resets the event log).  Off by default; events cost a few microseconds
- * of host time per launch. */
+ * of host time per launch.  on >= 2 also makes the guided partitions
+ * (partition_mode 1-3) count their probes for msort_ctx_partition_stats,
+ * with one atomic per warp, which slows those launches: time them at
+ * level 1. */
 msort_status msort_ctx_set_profiling(msort_ctx* ctx, int on);
 /* Waits for the logged events of kernel kind `kind`, returns how many
  * launches were logged and their summed device time, and clears that log. */
 msort_status msort_ctx_kernel_times(msort_ctx* ctx, int kind, uint64_t* launches, double* total_ms);
 /* Number of kernels this context has launched since it was created. */
 unsigned long long msort_ctx_launch_count(msort_ctx* ctx);
+/* Like msort_ctx_kernel_times, launch by launch: waits for the logged events
+ * of kind `kind`, writes the first min(cap, launches) device times in launch
+ * order to h_ms (milliseconds), sets *launches and clears that log. */
+msort_status msort_ctx_kernel_log(msort_ctx* ctx, int kind, double* h_ms, size_t cap, uint64_t* launches);
 
 #ifdef __cplusplus
 }

@@ -63,6 +63,8 @@ _SIGS = {
     "msort_segmented_sort": ([_P, _P, _P, _P, _SZ, _SZ, _I, _OPT, _P], _ST),
     "msort_sort_noalloc": ([_P, _P, _P, _P, _SZ, _I, _P], _ST),
     "msort_noalloc_max_keys": ([_I, _I], _SZ),
+    "msort_noalloc_sync": ([_P], _ST),
+    "msort_selftest_wait_timeout": ([_P, ctypes.c_longlong, _P], _ST),
     "msort_tune": ([_P, ctypes.c_char_p, _I], _ST),
     "msort_tune_load": ([_P, ctypes.c_char_p], _ST),
     "msort_tune_clear": ([_P], _ST),
@@ -81,6 +83,7 @@ _SIGS = {
     "msort_ctx_set_profiling": ([_P, _I], _ST),
     "msort_ctx_kernel_times": ([_P, _I, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)], _ST),
     "msort_ctx_launch_count": ([_P], ctypes.c_ulonglong),
+    "msort_ctx_kernel_log": ([_P, _I, _P, _SZ, ctypes.POINTER(ctypes.c_uint64)], _ST),
 }
 
 _lib = None
@@ -315,8 +318,20 @@ def msort_sort_noalloc(keys_in, keys_out, vals_in=None, vals_out=None, n=None, k
                                                    _stream(stream, keys_in)))
 
 
+def msort_noalloc_sync(stream=None) -> None:
+    """Wait for `stream` and raise if the last msort_sort_noalloc call's
+    kernels recorded an error (a bounded wait that gave up)."""
+    _check(None, load_library().msort_noalloc_sync(_stream(stream)))
+
+
 def msort_noalloc_max_keys(key_type: int, with_vals: bool) -> int:
     return int(load_library().msort_noalloc_max_keys(int(key_type), int(bool(with_vals))))
+
+
+def msort_selftest_wait_timeout(ctx, limit_cycles: int = 100000, stream=None) -> None:
+    """Enqueue the bounded-wait self-test: one merge block that gives up its
+    wait after limit_cycles; the next msort_ctx_sync raises TIMEOUT."""
+    _check(ctx, load_library().msort_selftest_wait_timeout(ctx, int(limit_cycles), _stream(stream)))
 
 
 def msort_tune(ctx, cache_path=None, quick: bool = False) -> None:
@@ -367,8 +382,10 @@ def msort_ctx_partition_stats(ctx):
     return int(a.value), int(b.value)
 
 
-def msort_ctx_set_profiling(ctx, on: bool) -> None:
-    _check(ctx, load_library().msort_ctx_set_profiling(ctx, int(bool(on))))
+def msort_ctx_set_profiling(ctx, on) -> None:
+    """on: 0 off, 1 (or True) CUDA events around every launch, 2 events and
+    probe counting in guided partitions."""
+    _check(ctx, load_library().msort_ctx_set_profiling(ctx, int(on)))
 
 
 def msort_ctx_kernel_times(ctx, kind: int):
@@ -377,6 +394,15 @@ def msort_ctx_kernel_times(ctx, kind: int):
     ms = ctypes.c_double()
     _check(ctx, load_library().msort_ctx_kernel_times(ctx, int(kind), ctypes.byref(n), ctypes.byref(ms)))
     return int(n.value), float(ms.value)
+
+
+def msort_ctx_kernel_log(ctx, kind: int, cap: int = 4096):
+    """Device milliseconds of each logged launch of `kind`, in launch order
+    (at most cap of them); clears that log."""
+    buf = (ctypes.c_double * max(int(cap), 1))()
+    n = ctypes.c_uint64()
+    _check(ctx, load_library().msort_ctx_kernel_log(ctx, int(kind), buf, int(cap), ctypes.byref(n)))
+    return [float(buf[i]) for i in range(min(int(n.value), int(cap)))]
 
 
 def msort_ctx_launch_count(ctx) -> int:

@@ -51,6 +51,7 @@ struct msort_ctx {
     cudaStream_t last_stream = nullptr;
     bool scratch_pending = false;
     bool profiling = false;
+    bool count_probes = false;  // profiling level 2: guided partitions count their probes
     std::vector<msort::EventPair> prof[msort::KK_COUNT];
     size_t prof_used[msort::KK_COUNT] = {};
     unsigned long long launches = 0;

@@ -305,6 +305,7 @@ __global__ void k_partition_guided(const K* __restrict__ src, size_t n, size_t L
         for (int i = threadIdx.x; i < kNP; i += blockDim.x) p[i] = params[i];
     __syncthreads();
     const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned int live = __ballot_sync(0xffffffffu, c < nblocks);  // lanes that search (blockDim % 32 == 0)
     if (c >= nblocks) return;
     const size_t out0 = c * W;
     const PassGeom g = pass_geom(out0, n, L);
@@ -388,9 +389,12 @@ __global__ void k_partition_guided(const K* __restrict__ src, size_t n, size_t L
             hi = mid;
     }
     splits[c] = lo;
-    if (probes) {
-        atomicAdd(&probes[0], np);
-        atomicAdd(&probes[1], 1ull);
+    if (probes) {  // one atomic per warp
+        const unsigned int wp = __reduce_add_sync(live, (unsigned int)np);
+        if ((threadIdx.x & 31) == __ffs(live) - 1) {
+            atomicAdd(&probes[0], (unsigned long long)wp);
+            atomicAdd(&probes[1], (unsigned long long)__popc(live));
+        }
     }
 }
 
@@ -521,7 +525,7 @@ cudaError_t launch_guided_partition(msort_ctx* ctx, const Plan& pl, const K* src
     const unsigned th = 128;
     k_partition_guided<K><<<(unsigned)((nblocks + th - 1) / th), th, 0, st>>>(
         src, n, L, (size_t)pl.W, nblocks, splits, model ? s->params : nullptr, exact_only,
-        ctx->profiling ? s->probes : nullptr);
+        ctx->count_probes ? s->probes : nullptr);
     return cudaGetLastError();
 }
 

@@ -1402,7 +1402,28 @@ msort_status msort_ctx_set_profiling(msort_ctx* ctx, int on) {
     if (!ctx) return fail(MSORT_ERR_INVALID_ARG, "ctx is NULL");
     std::lock_guard<std::mutex> g(ctx->mu);
     ctx->profiling = on != 0;
+    ctx->count_probes = on >= 2;
     for (auto& u : ctx->prof_used) u = 0;
+    return MSORT_OK;
+}
+
+msort_status msort_ctx_kernel_log(msort_ctx* ctx, int kind, double* h_ms, size_t cap, uint64_t* launches) {
+    if (!ctx || kind < 0 || kind >= KK_COUNT || !launches || (cap && !h_ms))
+        return fail(MSORT_ERR_INVALID_ARG, "bad argument to msort_ctx_kernel_log");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    cudaSetDevice(ctx->device);
+    const size_t used = ctx->prof_used[kind];
+    for (size_t i = 0; i < used; ++i) {
+        const EventPair& p = ctx->prof[kind][i];
+        cudaError_t e = cudaEventSynchronize(p.b);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, p.a, p.b);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+        if (i < cap) h_ms[i] = ms;
+    }
+    *launches = used;
+    ctx->prof_used[kind] = 0;
     return MSORT_OK;
 }
 

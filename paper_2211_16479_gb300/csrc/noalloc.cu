@@ -11,12 +11,14 @@
 //
 // The scratch is shared by every call on a device and keeps whatever the
 // last call left in it; the status word that kernels may set is cleared at
-// the start of each call, the rest is fully rewritten before it is read.
-// Calls whose work overlaps on the GPU (different streams without ordering,
-// or several host threads) race on the scratch and give wrong results: order
-// them on one stream or serialise them.
+// the start of each call (msort_noalloc_sync reads it afterwards), the rest
+// is fully rewritten before it is read.  Calls whose work overlaps on the GPU
+// (different streams without ordering, or several host threads) race on the
+// scratch and give wrong results: order them on one stream or serialise them.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <map>
 #include <mutex>
 #include <string>
 
@@ -32,26 +34,62 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 namespace msort {
 namespace {
 
-constexpr int kMaxDevices = 64;
 constexpr int kNoAllocTile = 8448;  // 256 threads x 33 keys; valid for every key/value type
 std::mutex g_mu;
-unsigned char* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the calling thread's current
-// device, looked up once per device (the first call on a device does it).
+// Driver calls that identify the calling thread's current CUDA context,
+// reached through the runtime (the library does not link libcuda itself).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+// Scratch address per CUDA context id.  The array's address belongs to the
+// context that loaded the library's module: after a device reset, or under
+// another context, the runtime loads the module again at a new address, so
+// the cache is keyed by the context's unique id, not by the device index.
+std::map<unsigned long long, unsigned char*> g_scratch_addr;
+
+msort_status driver_entry_points() {
+    if (g_ctx_get_current && g_ctx_get_id) return MSORT_OK;
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+    void *f1 = nullptr, *f2 = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+    if (e == cudaSuccess) e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDriverEntryPointByVersion");
+    if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+        return fail(MSORT_ERR_UNSUPPORTED, "the CUDA driver lacks cuCtxGetCurrent / cuCtxGetId");
+    g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    return MSORT_OK;
+}
+
+// Device address of the scratch array in the calling thread's current
+// context, looked up once per context (the first call under a context does
+// it; cudaGetSymbolAddress allocates nothing).  With no context current yet,
+// the lookup itself makes the current device's primary context current.
 msort_status scratch_on_current_device(unsigned char** out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices) return fail(MSORT_ERR_UNSUPPORTED, "device index beyond the supported range");
     std::lock_guard<std::mutex> g(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    msort_status s = driver_entry_points();
+    if (s != MSORT_OK) return s;
+    CUcontext cu = nullptr;
+    if (g_ctx_get_current(&cu) != CUDA_SUCCESS) return fail(MSORT_ERR_CUDA, "cuCtxGetCurrent failed");
+    void* fresh = nullptr;
+    if (!cu) {
+        cudaError_t e = cudaGetSymbolAddress(&fresh, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the no-allocation scratch");
-        g_scratch_addr[dev] = static_cast<unsigned char*>(p);
+        if (g_ctx_get_current(&cu) != CUDA_SUCCESS || !cu) return fail(MSORT_ERR_CUDA, "no current CUDA context");
     }
-    *out = g_scratch_addr[dev];
+    unsigned long long id = 0;
+    if (g_ctx_get_id(cu, &id) != CUDA_SUCCESS) return fail(MSORT_ERR_CUDA, "cuCtxGetId failed");
+    auto it = g_scratch_addr.find(id);
+    if (it == g_scratch_addr.end()) {
+        if (!fresh) {
+            cudaError_t e = cudaGetSymbolAddress(&fresh, g_noalloc_scratch);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the no-allocation scratch");
+        }
+        it = g_scratch_addr.emplace(id, static_cast<unsigned char*>(fresh)).first;
+    }
+    *out = it->second;
     return MSORT_OK;
 }
 
@@ -154,6 +192,22 @@ msort_status msort_sort_noalloc(const void* d_keys_in, const uint32_t* d_vals_in
                                                     static_cast<uint64_t*>(d_keys_out), d_vals_out, n, st)
                      : noalloc_sort<uint64_t, false>(static_cast<const uint64_t*>(d_keys_in), nullptr,
                                                      static_cast<uint64_t*>(d_keys_out), nullptr, n, st);
+}
+
+msort_status msort_noalloc_sync(void* stream) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    unsigned char* base = nullptr;
+    msort_status s = scratch_on_current_device(&base);
+    if (s != MSORT_OK) return s;
+    unsigned int st = 0;
+    e = cudaMemcpy(&st, base, sizeof(st), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "no-allocation status read");
+    if (!st) return MSORT_OK;
+    e = cudaMemset(base, 0, sizeof(unsigned int));
+    if (e != cudaSuccess) return cuda_fail(e, "no-allocation status clear");
+    if (st & DEV_TIMEOUT) return fail(MSORT_ERR_TIMEOUT, "a kernel of msort_sort_noalloc gave up a bounded wait");
+    return fail(MSORT_ERR_CUDA, "a kernel of msort_sort_noalloc recorded status " + std::to_string(st));
 }
 
 size_t msort_noalloc_max_keys(msort_key_type kt, int with_vals) {

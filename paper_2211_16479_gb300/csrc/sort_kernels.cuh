@@ -632,12 +632,14 @@ __host__ __device__ constexpr int merge_slots(int W, int IPT, int esize) {
 // XF: the block undoes the key transform xf_out as it stages its output (a
 // separate instance, so the common passes keep their register budget).
 // Shared memory: merge_slots(W, IPT, sizeof(K)) keys, then for pairs
-// merge_slots(W, IPT, 4) values.  Returns false if a bounded wait gave up.
+// merge_slots(W, IPT, 4) values.  Returns false if a bounded wait gave up
+// (after wait_limit cycles; every production caller keeps the default).
 // ---------------------------------------------------------------------------
 template <class K, bool PAIRS, int THREADS, int IPT, bool XF>
 __device__ __forceinline__ bool merge_block(const K* gA, int nA, const K* gB, int nB, const uint32_t* gvA,
                                             const uint32_t* gvB, K* D, uint32_t* VD, unsigned char* smem_raw,
-                                            uint64_t* bar, uint32_t& phase, unsigned int* status, int xf_out) {
+                                            uint64_t* bar, uint32_t& phase, unsigned int* status, int xf_out,
+                                            long long wait_limit = kWaitLimitCycles) {
     constexpr int W = THREADS * IPT;
     constexpr int KS = (int)sizeof(K);
     constexpr int KSLOTS = merge_slots(W, IPT, KS);
@@ -674,11 +676,11 @@ __device__ __forceinline__ bool merge_block(const K* gA, int nA, const K* gB, in
         window_scalars(gvB, nB, vB, sv, warp, lane, 6, 0, 0u);
     }
     __syncthreads();
-    const bool ok_wait = mbar_wait_bounded(bar, phase, kWaitLimitCycles);
+    const bool ok_wait = mbar_wait_bounded(bar, phase, wait_limit);
     phase ^= 1u;
     if (!ok_wait) {
         if (t == 0) atomicOr(status, kStatusTimeout);
-        mbar_wait_bounded(bar, phase ^ 1u, kWaitLimitCycles);
+        mbar_wait_bounded(bar, phase ^ 1u, wait_limit);
         return false;
     }
 
