@@ -194,6 +194,29 @@ msort_status msort_merge(msort_ctx* ctx, const void* d_a, const uint32_t* d_va, 
 msort_status msort_merge_runs(msort_ctx* ctx, const void* d_keys, const uint32_t* d_vals, const uint64_t* offsets,
                               size_t nruns, void* d_out, uint32_t* d_vout, msort_key_type kt, void* stream);
 
+/* Cuts of one rank's sorted chunk for the one-exchange multi-GPU sort.  The
+ * paper's message-passing sort scatters the array into one subarray per
+ * process and merges the sorted subarrays up a tree (Section "MPI Merge
+ * Sort", Figs. 16-17); the one-exchange form instead sends every element
+ * once, to the rank owning its key range, with p - 1 splitters taken from
+ * regular samples of all chunks.  Elements are ordered by (key, global input
+ * position), a total order, so that splitters cut runs of equal keys and
+ * rank r receives exactly the r-th slice of the stable sort.
+ *   d_keys[0:n)     the chunk's keys, stably sorted (unsigned, kt MSORT_U32
+ *                   or MSORT_U64; others give MSORT_ERR_UNSUPPORTED)
+ *   d_idx[0:n)      each sorted key's index in the unsorted chunk (the values
+ *                   of a key-value sort whose values were 0..n-1), so its
+ *                   global position is offset + d_idx[i]
+ *   d_split_keys / d_split_pos [0:nsplit)   the splitters (key of type kt,
+ *                   uint64 global position), in any order
+ *   d_cuts[0:nsplit) (output, uint64) for each splitter, the number of chunk
+ *                   elements ordered before it: keys below it, plus equal
+ *                   keys at a smaller global position.
+ * One binary search per splitter on `stream`; n <= 2^32 - 1. */
+msort_status msort_split_points(msort_ctx* ctx, const void* d_keys, const uint32_t* d_idx, size_t n,
+                                uint64_t offset, const void* d_split_keys, const uint64_t* d_split_pos,
+                                size_t nsplit, uint64_t* d_cuts, msort_key_type kt, void* stream);
+
 /* Merge blocks the out-of-core sort (msort_sort_host) uses, computed on the
  * host: h_runs holds n unsigned keys (kt MSORT_U32 or MSORT_U64) as
  * R = ceil(n / chunk) sorted runs of `chunk` keys laid end to end (the last

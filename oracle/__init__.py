@@ -151,6 +151,22 @@ def corank(a, b, d: int, lib=None) -> int:
     return int(r)
 
 
+def split_points(keys, positions, split_keys, split_pos):
+    """For each splitter (split_keys[t], split_pos[t]): how many elements
+    come before it when elements are ordered by (key, global position), a
+    total order.  Written as the plain count over the (unsorted) elements,
+    the partition step of the one-exchange form of Section "MPI Merge Sort"'s
+    scatter-sort-merge (each rank keeps the slice between two splitters).
+    Unsigned or signed integer keys."""
+    keys = np.asarray(keys)
+    positions = np.asarray(positions, dtype=np.uint64)
+    out = np.empty(len(split_keys), dtype=np.uint64)
+    for t, (sk, sp) in enumerate(zip(np.asarray(split_keys, dtype=keys.dtype),
+                                     np.asarray(split_pos, dtype=np.uint64))):
+        out[t] = np.count_nonzero((keys < sk) | ((keys == sk) & (positions < sp)))
+    return out
+
+
 def segmented_sort(keys, offsets, vals=None, lib=None):
     lib = lib or load()
     k = np.ascontiguousarray(keys).copy()

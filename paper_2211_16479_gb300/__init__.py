@@ -60,6 +60,7 @@ _SIGS = {
     "msort_merge": ([_P, _P, _P, _SZ, _P, _P, _SZ, _P, _P, _I, _P], _ST),
     "msort_merge_runs": ([_P, _P, _P, _P, _SZ, _P, _P, _I, _P], _ST),
     "msort_external_plan": ([_P, _SZ, _I, _SZ, _SZ, _P, _SZ], _SZ),
+    "msort_split_points": ([_P, _P, _P, _SZ, ctypes.c_uint64, _P, _P, _SZ, _P, _I, _P], _ST),
     "msort_segmented_sort": ([_P, _P, _P, _P, _SZ, _SZ, _I, _OPT, _P], _ST),
     "msort_sort_noalloc": ([_P, _P, _P, _P, _SZ, _I, _P], _ST),
     "msort_noalloc_max_keys": ([_I, _I], _SZ),
@@ -265,6 +266,17 @@ def msort_merge_runs(ctx, keys, offsets, out, vals=None, out_vals=None, key_type
     _check(ctx, load_library().msort_merge_runs(ctx, _ptr(keys), _ptr(vals), offs.ctypes.data, max(len(offs) - 1, 0),
                                                 _ptr(out), _ptr(out_vals), _key_type(keys, key_type),
                                                 _stream(stream, out)))
+
+
+def msort_split_points(ctx, keys, idx, offset: int, split_keys, split_pos, cuts, key_type=None,
+                       stream=None) -> None:
+    """cuts[t] = number of elements of the sorted chunk (keys, local indices
+    idx, global position offset + idx) ordered before the splitter
+    (split_keys[t], split_pos[t]) in (key, position) order; all device
+    tensors, cuts and split_pos 64-bit."""
+    _check(ctx, load_library().msort_split_points(ctx, _ptr(keys), _ptr(idx), _numel(keys, None), int(offset),
+                                                  _ptr(split_keys), _ptr(split_pos), _numel(split_keys, None),
+                                                  _ptr(cuts), _key_type(keys, key_type), _stream(stream, keys)))
 
 
 def msort_external_plan(runs, chunk: int, block_max: int):

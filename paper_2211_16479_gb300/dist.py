@@ -115,25 +115,15 @@ def tree_merge_sort(local: torch.Tensor, ctx=None, local_sort=None, merge=None):
 # ---------------------------------------------------------------------------
 # Sample sort
 # ---------------------------------------------------------------------------
-def _to_wire(t: torch.Tensor) -> torch.Tensor:
-    """Keys or values as int64 for the collectives, bit-preserving: 64-bit
-    types by a view, 32-bit ones through their int32 view (torch has few
-    kernels for unsigned types)."""
-    return t.view(torch.int64) if t.element_size() == 8 else t.view(torch.int32).to(torch.int64)
-
-
-def _from_wire(t: torch.Tensor, like: torch.Tensor) -> torch.Tensor:
-    return t.view(like.dtype) if like.element_size() == 8 else t.to(torch.int32).view(like.dtype)
+def _wire(t: torch.Tensor) -> torch.Tensor:
+    """Keys or values for the collectives at their own width, bit-preserving:
+    a signed view of the same size (int32 or int64)."""
+    return t.view(torch.int64) if t.element_size() == 8 else t.view(torch.int32)
 
 
 def _gather(t: torch.Tensor, idx: torch.Tensor) -> torch.Tensor:
     """t[idx] through a signed view of the same width."""
-    signed = torch.int64 if t.element_size() == 8 else torch.int32
-    return t.view(signed)[idx].view(t.dtype)
-
-
-def _np(t: torch.Tensor) -> np.ndarray:
-    return t.detach().cpu().numpy()
+    return _wire(t)[idx].view(t.dtype)
 
 
 def _gpu_sort_pairs(ctx):
@@ -171,37 +161,65 @@ def _gpu_merge_runs(ctx):
     return merge_runs
 
 
-def _split_points(keys: np.ndarray, gpos: np.ndarray, sk: np.ndarray, sg: np.ndarray) -> np.ndarray:
-    """For each splitter (sk[t], sg[t]), the number of local elements ordered
-    before it: keys below sk[t], plus those equal to it whose global position
-    is below sg[t] (within equal keys the global positions increase)."""
-    lo = np.searchsorted(keys, sk, side="left")
-    hi = np.searchsorted(keys, sk, side="right")
-    out = np.empty(len(sk), dtype=np.int64)
-    for t in range(len(sk)):
-        out[t] = lo[t] + np.searchsorted(gpos[lo[t]:hi[t]], sg[t], side="left")
-    return out
+def _gpu_split_points(ctx):
+    import paper_2211_16479_gb300 as ms
+
+    def split_points(keys, idx, offset, split_keys, split_pos):
+        cuts = torch.zeros(split_keys.numel(), dtype=torch.int64, device=keys.device)
+        if split_keys.numel():
+            ms.msort_split_points(ctx, keys, idx, offset, split_keys, split_pos, cuts)
+        return cuts
+    return split_points
+
+
+def _merge_runs_by_pairs(merge):
+    """merge_runs(k, v, offsets) from a stable two-way merge(a, va, b, vb):
+    the pairwise tree over the runs laid end to end (ties in run order)."""
+    def merge_runs(k, v, offsets):
+        offs = [int(x) for x in offsets]
+        pieces = [(k[a:b], None if v is None else v[a:b]) for a, b in zip(offs, offs[1:])]
+        if not pieces:
+            return k, v
+        while len(pieces) > 1:
+            pieces = [merge(*pieces[i], *pieces[i + 1]) if i + 1 < len(pieces) else pieces[i]
+                      for i in range(0, len(pieces), 2)]
+        return pieces[0]
+    return merge_runs
 
 
 def sample_sort(local: torch.Tensor, vals: torch.Tensor | None = None, ctx=None, local_sort=None, merge=None,
-                oversample: int = 16, merge_runs=None):
+                oversample: int = 16, merge_runs=None, split_points=None):
     """Stable sort of the concatenation (in rank order) of every rank's
     ``local`` chunk (and ``vals`` alongside).  Returns this rank's slice
     (keys, vals): the slices, concatenated in rank order, are the sorted
-    array.  ``local_sort(k, v) -> (k, v)`` sorts by key, stably, carrying
-    uint32 values.  The p received pieces are merged either by
-    ``merge_runs(k, v, offsets) -> (k, v)``, the stable merge of sorted runs
-    laid end to end, or, when only ``merge(a, va, b, vb) -> (c, vc)`` (the
-    stable merge of two, ties from a) is given, by a pairwise tree of it.
-    Both default to the library's GPU kernels through ``ctx``
-    (``msort_merge_runs``: every round of the tree in one launch pair).
-    Chunks must hold fewer than 2^31 elements."""
-    if local_sort is None or (merge is None and merge_runs is None):
+    array.  Steps, all on the device for GPU ranks (only per-rank counts,
+    O(p) numbers, reach the host):
+
+    1. ``local_sort(k, v) -> (k, v)``: stable sort of the chunk by key,
+       carrying the local index 0..n-1 as the uint32 value;
+    2. ``oversample * p`` regular samples of the sorted chunk, (key, global
+       position), are all-gathered at the keys' own width; the p sample
+       runs, each sorted by (key, position) and in rank = position order,
+       are merged by ``merge_runs``; every (m / p)-th becomes a splitter;
+    3. ``split_points(keys, idx, offset, split_keys, split_pos) -> cuts``:
+       elements of the sorted chunk ordered before each splitter;
+    4. one all-to-all exchange of counts, keys and values (at their own
+       width);
+    5. ``merge_runs(k, v, offsets) -> (k, v)``: stable merge of the p
+       received pieces laid end to end in source-rank order.
+
+    ``merge_runs`` may be replaced by a two-way ``merge(a, va, b, vb)``
+    (stable, ties from a), applied as a pairwise tree.  All default to the
+    library's kernels through ``ctx`` (msort_sort_pairs, msort_merge_runs,
+    msort_split_points).  Chunks hold fewer than 2^31 elements."""
+    if merge_runs is None and merge is not None:
+        merge_runs = _merge_runs_by_pairs(merge)
+    if local_sort is None or merge_runs is None or split_points is None:
         if ctx is None:
-            raise ValueError("a msort context is needed for the GPU local sort and merges")
+            raise ValueError("a msort context is needed for the GPU local sort, merges and cuts")
         local_sort = local_sort or _gpu_sort_pairs(ctx)
-        if merge is None and merge_runs is None:
-            merge_runs = _gpu_merge_runs(ctx)
+        merge_runs = merge_runs or _gpu_merge_runs(ctx)
+        split_points = split_points or _gpu_split_points(ctx)
     rank, world = tdist.get_rank(), tdist.get_world_size()
     dev = local.device
     # the collectives run on the device for NCCL, on the host for gloo
@@ -209,66 +227,59 @@ def sample_sort(local: torch.Tensor, vals: torch.Tensor | None = None, ctx=None,
     n = local.numel()
     sizes = [torch.zeros(1, dtype=torch.int64, device=comm) for _ in range(world)]
     tdist.all_gather(sizes, torch.tensor([n], dtype=torch.int64, device=comm))
-    offset = int(sum(int(x) for x in sizes[:rank]))
+    sizes = [int(x) for x in sizes]
+    offset = sum(sizes[:rank])
 
     # 1. local stable sort; the local index rides along as the value
     idx = torch.arange(n, dtype=torch.int32, device=dev).view(torch.uint32)
-    sk_local, si = local_sort(local.contiguous(), idx)
-    si64 = si.view(torch.int32).to(torch.int64)
-    sv_local = None if vals is None else _gather(vals.contiguous(), si64)
-    keys_np = _np(sk_local)
-    gpos_np = _np(si64) + offset  # global input position of every sorted element
+    sk, si = local_sort(local.contiguous(), idx)
+    si_long = si.view(torch.int32).to(torch.int64)
+    sv = None if vals is None else _gather(vals.contiguous(), si_long)
 
-    # 2. regular samples (s per rank) -> p - 1 splitters, as (key, position)
+    # 2. regular samples (key, global position) -> sorted by the library's
+    # merge of the p sample runs -> p - 1 splitters
     s = max(1, oversample * world)
-    smp_k = torch.zeros(s, dtype=torch.int64)
-    smp_g = torch.full((s,), -1, dtype=torch.int64)
+    smp_k = torch.zeros(s, dtype=_wire(sk).dtype, device=dev)
+    smp_p = torch.zeros(s, dtype=torch.int64, device=dev)
     if n:
-        pick = (np.arange(s, dtype=np.int64) * 2 + 1) * n // (2 * s)
-        smp_k[:] = _to_wire(torch.from_numpy(np.ascontiguousarray(keys_np[pick])))
-        smp_g[:] = torch.from_numpy(gpos_np[pick])
-    all_k = [torch.zeros(s, dtype=torch.int64, device=comm) for _ in range(world)]
-    all_g = [torch.zeros(s, dtype=torch.int64, device=comm) for _ in range(world)]
+        pick = torch.div((torch.arange(s, dtype=torch.int64, device=dev) * 2 + 1) * n, 2 * s, rounding_mode="floor")
+        smp_k = _wire(sk)[pick]
+        smp_p = si_long[pick] + offset
+    all_k = [torch.zeros(s, dtype=smp_k.dtype, device=comm) for _ in range(world)]
+    all_p = [torch.zeros(s, dtype=torch.int64, device=comm) for _ in range(world)]
     tdist.all_gather(all_k, smp_k.to(comm))
-    tdist.all_gather(all_g, smp_g.to(comm))
-    gk = _np(_from_wire(torch.cat(all_k).cpu(), local.cpu()))
-    gg = _np(torch.cat(all_g).cpu())
-    keep = gg >= 0
-    gk, gg = gk[keep], gg[keep]
-    order = np.lexsort((gg, gk))  # by key, then by global position
-    gk, gg = gk[order], gg[order]
-    m = len(gk)
-    at = (np.arange(1, world) * m) // world
-    cuts = _split_points(keys_np, gpos_np, gk[at], gg[at]) if m else np.zeros(world - 1, dtype=np.int64)
-    bounds = np.concatenate([[0], cuts, [n]]).astype(np.int64)
-    send = torch.from_numpy(np.diff(bounds)).to(comm)
+    tdist.all_gather(all_p, smp_p.to(comm))
+    counts = [s if sizes[r] else 0 for r in range(world)]
+    gk = torch.cat([all_k[r][:counts[r]] for r in range(world)]).to(dev).view(sk.dtype)
+    gp = torch.cat([all_p[r][:counts[r]] for r in range(world)]).to(dev)
+    m = gk.numel()
+    run_offsets = np.concatenate([[0], np.cumsum(counts)]).astype(np.uint64)
+    order = torch.arange(m, dtype=torch.int32, device=dev).view(torch.uint32)
+    mk, mo = merge_runs(gk, order, run_offsets)
+    at = torch.tensor([(j * m) // world for j in range(1, world)], dtype=torch.int64, device=dev)
+    if m:
+        spl_k = _gather(mk, at)
+        spl_p = gp[mo.view(torch.int32).to(torch.int64)[at]]
+        cuts = split_points(sk, si, offset, spl_k, spl_p)
+        cuts = [int(x) for x in cuts.tolist()]
+    else:
+        cuts = [0] * (world - 1)
+    bounds = [0] + cuts + [n]
+    send = torch.tensor([bounds[r + 1] - bounds[r] for r in range(world)], dtype=torch.int64, device=comm)
 
-    # 3. one exchange: counts, then keys (and values)
+    # 3. one exchange: counts, then keys (and values) at their own width
     recv = torch.zeros(world, dtype=torch.int64, device=comm)
     tdist.all_to_all_single(recv, send)
     send_l, recv_l = send.tolist(), recv.tolist()
     total = int(sum(recv_l))
 
     def exchange(t):
-        wire = _to_wire(t).to(comm) if n else torch.zeros(0, dtype=torch.int64, device=comm)
-        got = torch.zeros(total, dtype=torch.int64, device=comm)
-        tdist.all_to_all_single(got, wire, output_split_sizes=recv_l, input_split_sizes=send_l)
-        return got
-    got_k = exchange(sk_local)
-    got_v = None if vals is None else exchange(sv_local)
+        w = _wire(t).to(comm)
+        got = torch.zeros(total, dtype=w.dtype, device=comm)
+        tdist.all_to_all_single(got, w, output_split_sizes=recv_l, input_split_sizes=send_l)
+        return got.to(dev).view(t.dtype)
+    got_k = exchange(sk)
+    got_v = None if vals is None else exchange(sv)
 
-    # 4. p sorted pieces in source-rank order: the pairwise merge tree
-    if merge_runs is not None:
-        k = _from_wire(got_k, local).to(dev)
-        v = None if vals is None else _from_wire(got_v, vals).to(dev)
-        return merge_runs(k, v, np.concatenate([[0], np.cumsum(recv_l)]).astype(np.uint64))
-    pieces, o = [], 0
-    for c in recv_l:
-        k = _from_wire(got_k[o:o + c], local).to(dev)
-        v = None if vals is None else _from_wire(got_v[o:o + c], vals).to(dev)
-        pieces.append((k, v))
-        o += c
-    while len(pieces) > 1:
-        pieces = [merge(*pieces[i], *pieces[i + 1]) if i + 1 < len(pieces) else pieces[i]
-                  for i in range(0, len(pieces), 2)]
-    return pieces[0]
+    # 4. the p sorted pieces, end to end in source-rank order: one stable merge
+    return merge_runs(got_k, got_v, np.concatenate([[0], np.cumsum(recv_l)]).astype(np.uint64))

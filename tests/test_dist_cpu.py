@@ -155,6 +155,12 @@ def _oracle_merge_runs(k, v, offsets):
     return torch.from_numpy(mk), (None if mv is None else torch.from_numpy(mv))
 
 
+def _oracle_split_points(keys, idx, offset, split_keys, split_pos):
+    pos = idx.numpy().astype(np.uint64) + np.uint64(offset)
+    return torch.from_numpy(oracle.split_points(keys.numpy(), pos, split_keys.numpy(), split_pos.numpy())
+                            .astype(np.int64))
+
+
 def _sample_keys(kind, n):
     if kind == "uniform":
         return synth.uniform_u64(n, 5)
@@ -175,9 +181,11 @@ def _sample_worker(rank, world, port, n, kind, q, runs=False):
         lk = torch.from_numpy(keys[cuts[rank]:cuts[rank + 1]].copy())
         lv = torch.from_numpy(vals[cuts[rank]:cuts[rank + 1]].copy())
         if runs:
-            k, v = dist.sample_sort(lk, lv, local_sort=_oracle_sort_pairs, merge_runs=_oracle_merge_runs)
+            k, v = dist.sample_sort(lk, lv, local_sort=_oracle_sort_pairs, merge_runs=_oracle_merge_runs,
+                                    split_points=_oracle_split_points)
         else:
-            k, v = dist.sample_sort(lk, lv, local_sort=_oracle_sort_pairs, merge=_oracle_merge_pairs)
+            k, v = dist.sample_sort(lk, lv, local_sort=_oracle_sort_pairs, merge=_oracle_merge_pairs,
+                                    split_points=_oracle_split_points)
         parts = [None] * world
         tdist.all_gather_object(parts, (k.numpy(), v.numpy()))
         if rank == 0:

@@ -164,3 +164,27 @@ def test_sample_sort_gpu_pieces_and_single_rank(ctx):
         assert np.array_equal(to_host(sk), ek) and np.array_equal(to_host(sv), ev)
     finally:
         tdist.destroy_process_group()
+
+
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+def test_split_points_match_oracle(ctx, dtype):
+    """msort_split_points: cuts of a stably sorted chunk at (key, global
+    position) splitters, against the oracle's plain count; splitters equal to
+    elements, between positions, below and above every key, and all-equal
+    chunks."""
+    rng = np.random.default_rng(17)
+    for n, hi in ((0, 10), (1, 3), (1000, 4), (300007, 5000), (65536, 1)):
+        keys = rng.integers(0, hi, size=n).astype(dtype)
+        idx = np.arange(n, dtype=np.uint32)
+        sk, si = oracle.sort(keys, idx)
+        offset = 123456789012
+        pos = si.astype(np.uint64) + np.uint64(offset)
+        m = 257
+        pick = rng.integers(0, max(n, 1), size=m)
+        spl_k = np.concatenate([sk[pick] if n else np.zeros(m, dtype), [0, np.iinfo(dtype).max]]).astype(dtype)
+        spl_p = np.concatenate([pos[pick] + rng.integers(0, 2, size=m).astype(np.uint64) if n
+                                else np.zeros(m, np.uint64), [0, 1 << 62]]).astype(np.uint64)
+        cuts = torch.zeros(len(spl_k), dtype=torch.int64, device="cuda")
+        ms.msort_split_points(ctx, to_dev(sk), to_dev(si), offset, to_dev(spl_k), to_dev(spl_p), cuts)
+        exp = oracle.split_points(keys, np.arange(n, dtype=np.uint64) + np.uint64(offset), spl_k, spl_p)
+        assert np.array_equal(to_host(cuts).astype(np.uint64), exp), n

@@ -202,3 +202,29 @@ def test_planted_mistakes_are_caught(tmp_path):
         lib = oracle.load(m, outdir=str(tmp_path))
         assert lib.oracle_mutant_id() == m
         assert not _pins_pass(lib), f"mutant {m} slipped through the pins"
+
+
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+def test_split_points_is_the_rank_in_the_stable_sort(oracle_lib, dtype):
+    """oracle.split_points against the oracle's stable sort: a splitter equal
+    to element e (its key and position) has exactly as many elements before
+    it as e's index in the stably sorted array; a splitter between two
+    positions falls between their ranks."""
+    rng = np.random.default_rng(13)
+    for trial in range(60):
+        n = int(rng.integers(0, 40))
+        keys = rng.integers(0, [2, 5, 1000][trial % 3], size=n).astype(dtype)
+        offset = int(rng.integers(0, 1 << 40))
+        pos = np.arange(n, dtype=np.uint64) + np.uint64(offset)
+        _, order = oracle.sort(keys, np.arange(n, dtype=np.uint32), lib=oracle_lib)
+        rank = np.empty(n, dtype=np.int64)
+        rank[order] = np.arange(n)
+        cuts = oracle.split_points(keys, pos, keys, pos)
+        assert np.array_equal(cuts.astype(np.int64), rank)
+        if n:
+            # (key, position - 0.5): just before e; (key, beyond every position): after all equal keys
+            two = np.uint64(2)
+            below = oracle.split_points(keys, pos * two + np.uint64(1), keys, pos * two)
+            assert np.array_equal(below.astype(np.int64), rank)
+            after = oracle.split_points(keys, pos, keys, np.full(n, offset + n, dtype=np.uint64))
+            assert np.array_equal(after.astype(np.int64), [np.count_nonzero(keys <= k) for k in keys])
