@@ -412,11 +412,12 @@ def run_ours(args):
                "context": cpu_context_rates(sample)}
 
     # the chosen forms against the plain sort (rank 0, after the collectives)
-    chosen = None
+    chosen = small = None
     if rank == 0 and not args.no_chosen:
         if not args.no_e2e:
             del h_in, h_out, h_outs
         chosen = chosen_vs_plain(args, h, dev, stream)
+        small = form_small(h, dev, stream, 500)
 
     if rank == 0:
         line = {
@@ -452,6 +453,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "clocks": clocks,
             "chosen_vs_plain": chosen,
+            "small_config": small,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -495,38 +497,62 @@ def _torch_sort_gkeys(a_u32, reps):
     return a_u32.numel() / t / 1e6
 
 
-def run_small(args):
+def form_small(h, dev, stream, reps):
     """The small configuration: one stable sort of 2^20 uniform uint32 keys
-    (4 MiB, L2-resident, so launch cost dominates), replayed from a CUDA
-    graph; without the graph and torch.sort(stable=True) as context."""
+    (4 MiB, L2-resident, so launch cost and dependent latency dominate).
+    The default plan at this size is the single cooperative launch; the
+    multi-launch plan (tile sort, then a partition and a merge launch per
+    round) is timed beside it, both replayed from CUDA graphs and both
+    launched directly, with torch.sort(stable=True) as context."""
     import torch
 
     import paper_2211_16479_gb300 as ms
     from synth import torch_gen
     n = 1 << 20
-    a = torch_gen.u32_distribution("uniform", n, 1, device="cuda")
-    out = torch.empty_like(a)
-    ctx = ms.Context(0)
-    h = ctx.handle
-    reps = max(args.steps, 10) * 50
+    a = torch_gen.u32_distribution("uniform", n, 1, device=dev)
+    outs = {}
+    exp = torch.sort(a.to(torch.int64)).values.to(torch.uint32)
     res = {}
-    for name, o in (("graph", {"use_graph": 1}), ("launches", {})):
-        step = lambda: ms.msort_sort_copy(h, a, out, options=o)
-        for _ in range(max(args.warmup, 3)):
+    arms = {"single_graph": {"use_graph": 1}, "single_launch": {},
+            "multi_graph": {"use_graph": 1, "single_launch": -1}, "multi_launch": {"single_launch": -1}}
+    for name, o in arms.items():
+        outs[name] = torch.empty_like(a)
+        step = (lambda o=o, out=outs[name]: ms.msort_sort_copy(h, a, out, options=o, stream=stream))
+        for _ in range(5):
             step()
         torch.cuda.synchronize()
-        exp = torch.sort(a.to(torch.int64)).values.to(torch.uint32)
-        assert bool((out == exp).all()), "small sort mismatch"
-        res[name] = _events_ms(step, reps)
+        assert bool((outs[name] == exp).all()), f"small sort mismatch ({name})"
+        res[name] = _events_ms(step, reps, stream)
     T, W, P = ms.msort_plan_info(n, ms.MSORT_U32, False)
-    line = _base_line("Gkeys/s sorted (stable merge sort, 2^20 uint32 keys)", n / res["graph"] / 1e6, "Gkeys/s",
-                      args, res["graph"],
-                      {"workload": "2^20 uniform uint32 keys, keys only, stable out-of-place sort, CUDA-graph replay",
-                       "n": n, "tile": T, "merge_passes": P,
-                       "l2": "4 MiB input stays in the 126 MB L2 (a launch-bound size)"},
-                      dtype="u32", us_per_sort={"graph": res["graph"] * 1e3, "launches": res["launches"] * 1e3},
-                      without_graph_gkeys=n / res["launches"] / 1e6,
-                      torch_sort_stable_gkeys=_torch_sort_gkeys(a, reps))
+    peak, kind = _peaks()
+    alg = 2 * n * 4 * (1 + P)
+    best = res["single_graph"]
+    return {"workload": "2^20 uniform uint32 keys, keys only, stable out-of-place sort", "n": n,
+            "tile": T, "merge_rounds": P, "repetitions": reps,
+            "us_per_sort": {k: v * 1e3 for k, v in res.items()},
+            "gkeys_per_s": n / best / 1e6,
+            "speedup_vs_multi_launch_graph": res["multi_graph"] / best,
+            "identical_output": True,
+            "roofline": {"bound": "latency (L2-resident)", "algorithmic_bytes": alg,
+                         "achieved_gbs": alg / (best * 1e-3) / 1e9, "frac_of_hbm_peak_nominal":
+                         alg / (best * 1e-3) / 1e9 / peak, "peak": peak, "peak_kind": kind,
+                         "note": "the 4 MiB array stays in the 126 MB L2: the HBM roofline is nominal here"},
+            "torch_sort_stable_gkeys": _torch_sort_gkeys(a, reps)}
+
+
+def run_small(args):
+    import torch
+
+    import paper_2211_16479_gb300 as ms
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = ms.Context(0)
+    f = form_small(ctx.handle, dev, stream, max(args.steps, 10) * 50)
+    line = _base_line("Gkeys/s sorted (stable merge sort, 2^20 uint32 keys)", f["gkeys_per_s"], "Gkeys/s", args,
+                      f["us_per_sort"]["single_graph"] * 1e-3,
+                      {"workload": f["workload"] + ", single cooperative launch replayed from a CUDA graph",
+                       "n": f["n"], "tile": f["tile"], "merge_rounds": f["merge_rounds"]},
+                      dtype="u32", detail=f)
     print(json.dumps(line), flush=True)
     ctx.close()
 

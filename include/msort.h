@@ -103,7 +103,13 @@ typedef struct {
                            runs merged at once; keys-only sorts with partition_mode 0; half
                            the HBM traffic of the merge phase but slower on GB300, where the
                            pairwise pass runs at the copy bandwidth) */
-    int reserved[2];    /* must be zero */
+    int single_launch;  /* 0 = automatic: arrays of up to 2^22 elements are sorted by one
+                           cooperative launch that runs the tile sort and every merge round,
+                           with a grid barrier between rounds (such arrays stay in L2, where
+                           launch cost dominates), when tile, merge_block and partition_mode
+                           are 0 and passes are pairwise; 1 = that single launch up to 2^28
+                           elements (same conditions); -1 = never */
+    int reserved[1];    /* must be zero */
 } msort_options;
 
 /* Context on CUDA device `device`.  scratch_budget_bytes caps the scratch the
@@ -430,7 +436,7 @@ msort_status msort_ctx_partition_stats(msort_ctx* ctx, uint64_t* probes, uint64_
 
 /* Kernel kinds for msort_ctx_kernel_times. */
 enum { MSORT_KERNEL_TILE = 0, MSORT_KERNEL_PARTITION = 1, MSORT_KERNEL_MERGE = 2,
-       MSORT_KERNEL_SEGMENTED = 3, MSORT_KERNEL_MLP = 4 };
+       MSORT_KERNEL_SEGMENTED = 3, MSORT_KERNEL_MLP = 4, MSORT_KERNEL_SINGLE = 5 };
 
 /* on != 0: bracket every later launch with CUDA events on its own stream
  * (resets the event log).  Off by default; events cost a few microseconds

@@ -18,7 +18,7 @@ MSORT_OK, MSORT_ERR_INVALID_ARG, MSORT_ERR_UNSUPPORTED, MSORT_ERR_OOM = 0, 1, 2,
 MSORT_ERR_CUDA, MSORT_ERR_TIMEOUT, MSORT_ERR_BUSY = 4, 5, 6
 MSORT_U32, MSORT_U64, MSORT_I32, MSORT_I64, MSORT_F32, MSORT_F64 = 0, 1, 2, 3, 4, 5
 MSORT_KERNEL_TILE, MSORT_KERNEL_PARTITION, MSORT_KERNEL_MERGE = 0, 1, 2
-MSORT_KERNEL_SEGMENTED, MSORT_KERNEL_MLP = 3, 4
+MSORT_KERNEL_SEGMENTED, MSORT_KERNEL_MLP, MSORT_KERNEL_SINGLE = 3, 4, 5
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "TIMEOUT", 6: "BUSY"}
 
 
@@ -31,7 +31,7 @@ class MsortError(RuntimeError):
 class msort_options(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int), ("merge_block", ctypes.c_int), ("partition_mode", ctypes.c_int),
                 ("learned_passes", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("merge_ways", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("merge_ways", ctypes.c_int), ("single_launch", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 _P, _SZ, _I, _ST = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int

@@ -14,7 +14,7 @@
 
 namespace msort {
 
-enum KernelKind { KK_TILE = 0, KK_PARTITION = 1, KK_MERGE = 2, KK_SEGMENTED = 3, KK_MLP = 4, KK_COUNT = 5 };
+enum KernelKind { KK_TILE = 0, KK_PARTITION = 1, KK_MERGE = 2, KK_SEGMENTED = 3, KK_MLP = 4, KK_SINGLE = 5, KK_COUNT = 6 };
 
 // Status bits a kernel may raise in the context's device status word.
 enum : unsigned int { DEV_OK = 0, DEV_TIMEOUT = 1u, DEV_BAD_INPUT = 2u, DEV_INTERNAL = 4u };
@@ -34,6 +34,7 @@ struct Plan {
     int G4;     // grid step of the four-way partition
     int xform;  // key transform: 0 unsigned keys, 1 signed integers, 2 IEEE floating point
     int xform_out;  // transform the last round undoes: xform, or 0 to leave the keys transformed
+    int single;     // 1: the whole sort in one cooperative launch (csrc/small.cuh)
     unsigned int* status;  // device status word of the context
 };
 

@@ -70,6 +70,17 @@ struct RunPairs {
 template <class K, bool PAIRS>
 cudaError_t launch_merge_runs(const K* src, K* dst, const uint32_t* vsrc, uint32_t* vdst, const RunPairs& rp,
                               unsigned long long* splits, unsigned int* status, int xf_out, cudaStream_t st);
+// Single-launch sort of n keys (csrc/small.cuh): tiles of pl.tile keys (the
+// default shape for n is small_tile<K, PAIRS>(n)) and every merge round in
+// one cooperative launch; `barrier`
+// points to 8 bytes of scratch that this function zeroes on `st` first.
+template <class K, bool PAIRS>
+int small_tile(size_t n);
+template <class K, bool PAIRS>
+bool small_tile_supported(int tile);
+template <class K, bool PAIRS>
+cudaError_t launch_small(const Plan& pl, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, K* tk,
+                         uint32_t* tv, size_t n, void* barrier, cudaStream_t st, int xf_in, int xf_out);
 // Resource summary of the last kernel the calling thread prepared to launch.
 const std::string& last_launch_info();
 

@@ -6,6 +6,7 @@
 #include "launch.h"
 #include "merge4.cuh"
 #include "merge_runs.cuh"
+#include "small.cuh"
 #include "sort_kernels.cuh"
 
 namespace msort {
@@ -212,6 +213,92 @@ cudaError_t launch_merge_runs(const K* src, K* dst, const uint32_t* vsrc, uint32
     return cudaGetLastError();
 }
 
+// Single-launch shapes (threads x keys per thread; tile = merge block).
+// 32-bit keys alone: 256 x 11, 256 x 17, 256 x 33, 512 x 11, 512 x 17,
+// 512 x 33 or 1024 x 11; other key/value types: 256 x 11 and 256 x 33
+// (256 x 17 for 64-bit key-value pairs, whose 33-key blocks need too many
+// registers).  Small blocks keep each thread's serial merge short and spread
+// a small array over many SMs, which is what bounds a sort whose data stays
+// in L2.  Measured on GB300 (uniform 32-bit keys, graph replay): 256 x 17
+// is fastest up to 2^19 keys, 512 x 17 at 2^20 (59.5 us against 63.6 and
+// 61.4 for 256 x 17 and 256 x 33), 512 x 33 above; other types take
+// 256 x 11 up to 2^18 keys and their larger block above.
+template <class K, bool PAIRS>
+int small_tile(size_t n) {
+    if constexpr (!PAIRS && sizeof(K) == 4) {
+        if (n <= (size_t(1) << 19)) return 256 * 17;
+        return n <= (size_t(1) << 20) ? 512 * 17 : 512 * 33;
+    }
+    if (n <= (size_t(1) << 18)) return 256 * 11;
+    return (PAIRS && sizeof(K) == 8) ? 256 * 17 : 256 * 33;
+}
+
+template <class K, bool PAIRS>
+bool small_tile_supported(int tile) {
+    if (!PAIRS && sizeof(K) == 4)
+        return tile == 256 * 11 || tile == 256 * 17 || tile == 256 * 33 || tile == 512 * 11 || tile == 512 * 17 ||
+               tile == 512 * 33 || tile == 1024 * 11;
+    if (PAIRS && sizeof(K) == 8) return tile == 256 * 11 || tile == 256 * 17;
+    return tile == 256 * 11 || tile == 256 * 33;
+}
+
+template <class K, bool PAIRS, int TH, int IPT>
+static cudaError_t launch_small_shape(const Plan& pl, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout,
+                                      K* tk, uint32_t* tv, size_t n, void* barrier, cudaStream_t st, int xf_in,
+                                      int xf_out) {
+    auto f = (xf_in || xf_out) ? k_small_sort<K, PAIRS, TH, IPT, true> : k_small_sort<K, PAIRS, TH, IPT, false>;
+    const size_t sm = small_sort_smem<K, PAIRS, TH, IPT>();
+    cudaError_t e = prepare(f, sm);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per = 0, coop = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev)) != cudaSuccess) return e;
+    if (!coop) return cudaErrorNotSupported;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, f, TH, sm)) != cudaSuccess) return e;
+    if (per < 1) return cudaErrorInvalidConfiguration;
+    const size_t tiles = (n + (size_t)TH * IPT - 1) / ((size_t)TH * IPT);
+    const size_t cap = (size_t)sms * (size_t)per;  // blocks that can all be resident at once
+    const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
+    if ((e = cudaMemsetAsync(barrier, 0, sizeof(GridBarrier), st)) != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(TH);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, f, kin, vin, kout, vout, tk, tv, n, pl.passes,
+                              static_cast<GridBarrier*>(barrier), pl.status, xf_in, xf_out);
+}
+
+template <class K, bool PAIRS>
+cudaError_t launch_small(const Plan& pl, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, K* tk,
+                         uint32_t* tv, size_t n, void* barrier, cudaStream_t st, int xf_in, int xf_out) {
+#define MSORT_SMALL_CASE(TH, IPT)                                                                            \
+    if (pl.tile == TH * IPT)                                                                                \
+        return launch_small_shape<K, PAIRS, TH, IPT>(pl, kin, vin, kout, vout, tk, tv, n, barrier, st, xf_in, \
+                                                     xf_out);
+    MSORT_SMALL_CASE(256, 11)
+    if constexpr (!PAIRS && sizeof(K) == 4) {
+        MSORT_SMALL_CASE(256, 17)
+        MSORT_SMALL_CASE(256, 33)
+        MSORT_SMALL_CASE(512, 11)
+        MSORT_SMALL_CASE(512, 17)
+        MSORT_SMALL_CASE(512, 33)
+        MSORT_SMALL_CASE(1024, 11)
+    } else if constexpr (PAIRS && sizeof(K) == 8) {
+        MSORT_SMALL_CASE(256, 17)
+    } else {
+        MSORT_SMALL_CASE(256, 33)
+    }
+#undef MSORT_SMALL_CASE
+    return cudaErrorInvalidConfiguration;
+}
+
 #define MSORT_INSTANTIATE(K)                                                                                    \
     template size_t tile_smem_bytes<K, false>(int);                                                             \
     template size_t tile_smem_bytes<K, true>(int);                                                              \
@@ -247,6 +334,14 @@ cudaError_t launch_merge_runs(const K* src, K* dst, const uint32_t* vsrc, uint32
     template cudaError_t launch_merge_runs<K, false>(const K*, K*, const uint32_t*, uint32_t*, const RunPairs&,  \
                                                      unsigned long long*, unsigned int*, int, cudaStream_t);     \
     template cudaError_t launch_merge_runs<K, true>(const K*, K*, const uint32_t*, uint32_t*, const RunPairs&,   \
-                                                    unsigned long long*, unsigned int*, int, cudaStream_t);
+                                                    unsigned long long*, unsigned int*, int, cudaStream_t);      \
+    template int small_tile<K, false>(size_t);                                                                  \
+    template int small_tile<K, true>(size_t);                                                                   \
+    template bool small_tile_supported<K, false>(int);                                                          \
+    template bool small_tile_supported<K, true>(int);                                                           \
+    template cudaError_t launch_small<K, false>(const Plan&, const K*, const uint32_t*, K*, uint32_t*, K*,        \
+                                                uint32_t*, size_t, void*, cudaStream_t, int, int);               \
+    template cudaError_t launch_small<K, true>(const Plan&, const K*, const uint32_t*, K*, uint32_t*, K*,         \
+                                               uint32_t*, size_t, void*, cudaStream_t, int, int);
 
 }  // namespace msort

@@ -121,6 +121,11 @@ template <class K, bool PAIRS>
 static bool make_plan(size_t n, const msort_options* opt, Plan* pl, std::string* why, int xform = 0) {
     Plan p{};
     p.tile = opt && opt->tile ? opt->tile : default_tile<K, PAIRS>();
+    // a tile of the single launch only (options.single_launch = 1): the
+    // multi-launch fields below keep the default tile; apply_single replaces them
+    if (opt && opt->single_launch == 1 && opt->tile && !tile_supported<K, PAIRS>(opt->tile) &&
+        small_tile_supported<K, PAIRS>(opt->tile))
+        p.tile = default_tile<K, PAIRS>();
     if (!tile_supported<K, PAIRS>(p.tile)) {
         *why = "options.tile " + std::to_string(p.tile) +
                " is not available for this key/value type (4352, 8448, 8704 or 16896)";
@@ -163,6 +168,57 @@ static bool make_plan(size_t n, const msort_options* opt, Plan* pl, std::string*
     p.G4 = p.W4 / 8;
     p.status = nullptr;
     *pl = p;
+    return true;
+}
+
+// The single-launch plan (csrc/small.cuh): tile sort and every merge round
+// in one cooperative launch.  Chosen automatically for n up to 2^22 (such an
+// array stays in L2, and launch cost dominates the multi-launch plan) when
+// the caller leaves the tile and merge block at 0 with partition_mode 0 and
+// pairwise passes; options.single_launch = 1 asks for it up to 2^28
+// elements, -1 never uses it.
+constexpr size_t kSingleLaunchAuto = size_t(1) << 22;
+constexpr size_t kSingleLaunchForcedMax = size_t(1) << 28;
+
+// Options the single launch accepts: partition_mode 0, pairwise passes,
+// merge_block 0, and tile 0 (or, with single_launch = 1, one of its tiles).
+static bool single_eligible(const msort_options* opt) {
+    return !(opt && ((opt->tile && opt->single_launch != 1) || opt->merge_block || opt->partition_mode ||
+                     (opt->merge_ways && opt->merge_ways != 2)));
+}
+
+static bool single_wanted(size_t n, const msort_options* opt) {
+    const int mode = opt ? opt->single_launch : 0;
+    if (n == 0 || mode < 0 || !single_eligible(opt)) return false;
+    return mode == 1 ? n <= kSingleLaunchForcedMax : n <= kSingleLaunchAuto;
+}
+
+template <class K, bool PAIRS>
+static bool apply_single(size_t n, const msort_options* opt, Plan* pl, std::string* why) {
+    const int mode = opt ? opt->single_launch : 0;
+    if (mode < -1 || mode > 1) {
+        *why = "options.single_launch must be -1, 0 or 1";
+        return false;
+    }
+    if (mode == 1 && !single_eligible(opt)) {
+        *why = "options.single_launch = 1 needs tile and merge_block 0, partition_mode 0 and pairwise passes";
+        return false;
+    }
+    if (mode == 1 && n > kSingleLaunchForcedMax) {
+        *why = "options.single_launch = 1 takes at most 2^28 elements";
+        return false;
+    }
+    if (mode == 1 && opt->tile && !small_tile_supported<K, PAIRS>(opt->tile)) {
+        *why = "options.tile " + std::to_string(opt->tile) + " is not a single-launch tile for this key/value type";
+        return false;
+    }
+    if (!single_wanted(n, opt)) return true;
+    const int T = (opt && opt->tile) ? opt->tile : small_tile<K, PAIRS>(n);
+    pl->single = 1;
+    pl->tile = T;
+    pl->W = T;
+    pl->passes = 0;
+    for (size_t L = (size_t)T; L < n; L *= 2) ++pl->passes;
     return true;
 }
 
@@ -217,6 +273,16 @@ static msort_status run_sort(msort_ctx* ctx, const K* kin, const uint32_t* vin, 
     sp += align_up(gm * sizeof(K), 256);
     unsigned long long* brk = reinterpret_cast<unsigned long long*>(sp);
 
+    if (pl.single) {
+        // the split table is unused by this plan; its first 8 bytes hold the grid barrier
+        if (log) prof_begin(ctx, KK_SINGLE, st);
+        cudaError_t es = launch_small<K, PAIRS>(pl, kin, vin, kout, vout, tk, tv, n, splits, st, pl.xform,
+                                                pl.xform_out);
+        if (log) prof_end(ctx, KK_SINGLE, st);
+        ++ctx->launches;
+        if (es != cudaSuccess) return cuda_fail(es, ("single-launch sort" + last_launch_info()).c_str());
+        return MSORT_OK;
+    }
     // Passes over memory: with four-way passes, one pairwise pass first when
     // the number of merge rounds is odd, then one pass per two rounds.
     const int four = gm ? pl.passes / 2 : 0;
@@ -275,11 +341,11 @@ static msort_status run_sort(msort_ctx* ctx, const K* kin, const uint32_t* vin, 
 struct PlainGraphKey {
     const void *kin, *vin, *kout, *vout, *scratch;
     size_t n;
-    int type, tile, W, passes, ways, xform;
+    int type, tile, W, passes, ways, xform, single;
     bool operator<(const PlainGraphKey& o) const {
-        return std::tie(kin, vin, kout, vout, scratch, n, type, tile, W, passes, ways, xform) <
+        return std::tie(kin, vin, kout, vout, scratch, n, type, tile, W, passes, ways, xform, single) <
                std::tie(o.kin, o.vin, o.kout, o.vout, o.scratch, o.n, o.type, o.tile, o.W, o.passes, o.ways,
-                        o.xform);
+                        o.xform, o.single);
     }
 };
 // At most kMaxPlainGraphs graphs are kept; a new one evicts the least
@@ -309,8 +375,8 @@ static msort_status run_sort_graph(msort_ctx* ctx, const K* kin, const uint32_t*
                                    size_t n, const Plan& pl, cudaStream_t st) {
     if (!ctx->plain_graphs) ctx->plain_graphs = new PlainGraphs();
     PlainGraphs* pg = static_cast<PlainGraphs*>(ctx->plain_graphs);
-    const PlainGraphKey key{kin,    vin,  kout,      vout,    ctx->scratch, n, (int)sizeof(K) * 2 + (PAIRS ? 1 : 0),
-                            pl.tile, pl.W, pl.passes, pl.ways, pl.xform};
+    const PlainGraphKey key{kin,     vin,  kout,      vout,    ctx->scratch, n, (int)sizeof(K) * 2 + (PAIRS ? 1 : 0),
+                            pl.tile, pl.W, pl.passes, pl.ways, pl.xform, pl.single};
     auto it = pg->exec.find(key);
     if (it == pg->exec.end()) {
         if (pg->exec.size() >= kMaxPlainGraphs) {
@@ -443,7 +509,9 @@ template <class K, bool PAIRS>
 static msort_status sort_entry(msort_ctx* ctx, const void* kin, const uint32_t* vin, void* kout, uint32_t* vout,
                                size_t n, const msort_options* opt, cudaStream_t st, int xform) {
     msort_options tuned_opt{};
-    if (!opt || !opt->tile) {
+    const msort_options* caller = opt;
+    const bool single = single_wanted(n, opt);  // tuned shapes do not apply to the single launch
+    if (!single && (!opt || !opt->tile)) {
         const int tile = tuned_tile_for(ctx, (int)sizeof(K), PAIRS, n);
         if (tile) {
             if (opt) tuned_opt = *opt;
@@ -453,7 +521,7 @@ static msort_status sort_entry(msort_ctx* ctx, const void* kin, const uint32_t* 
     }
     // tuned merge fan-in where the caller left it open (the four-way pass
     // takes neither transformed keys nor the learned partition)
-    if (!xform && (!opt || (!opt->merge_ways && opt->partition_mode == 0))) {
+    if (!single && !xform && (!opt || (!opt->merge_ways && opt->partition_mode == 0))) {
         const int ways = tuned_choice(ctx->tuned_ways, (int)sizeof(K), PAIRS, n);
         if (ways) {
             if (opt && opt != &tuned_opt) tuned_opt = *opt;
@@ -464,6 +532,7 @@ static msort_status sort_entry(msort_ctx* ctx, const void* kin, const uint32_t* 
     Plan pl;
     std::string why;
     if (!make_plan<K, PAIRS>(n, opt, &pl, &why, xform)) return fail(MSORT_ERR_INVALID_ARG, why);
+    if (!apply_single<K, PAIRS>(n, caller, &pl, &why)) return fail(MSORT_ERR_INVALID_ARG, why);
     if (n == 0) return MSORT_OK;
     std::lock_guard<std::mutex> g(ctx->mu);
     cudaError_t e = cudaSetDevice(ctx->device);
@@ -505,6 +574,7 @@ msort_status plan_info_for(size_t n, const msort_options* opt, int* tile, int* W
     Plan pl;
     std::string why;
     if (!make_plan<K, PAIRS>(n, opt, &pl, &why, xform)) return fail(MSORT_ERR_INVALID_ARG, why);
+    if (!apply_single<K, PAIRS>(n, opt, &pl, &why)) return fail(MSORT_ERR_INVALID_ARG, why);
     if (tile) *tile = pl.tile;
     if (W) *W = pl.W;
     if (passes) *passes = pl.passes;
@@ -516,6 +586,7 @@ msort_status plan_passes_for(size_t n, const msort_options* opt, int* ways, int*
     Plan pl;
     std::string why;
     if (!make_plan<K, PAIRS>(n, opt, &pl, &why, xform)) return fail(MSORT_ERR_INVALID_ARG, why);
+    if (!apply_single<K, PAIRS>(n, opt, &pl, &why)) return fail(MSORT_ERR_INVALID_ARG, why);
     const bool four = merge4_grid_max(n, pl) != 0;
     if (ways) *ways = four ? 4 : 2;
     if (memory_passes) *memory_passes = four ? pl.passes / 2 + (pl.passes & 1) : pl.passes;
@@ -527,6 +598,7 @@ size_t scratch_bytes_for(size_t n, const msort_options* opt, int xform) {
     Plan pl;
     std::string why;
     if (!make_plan<K, PAIRS>(n, opt, &pl, &why, xform)) return 0;
+    if (!apply_single<K, PAIRS>(n, opt, &pl, &why)) return 0;
     return scratch_need<K, PAIRS>(n, pl);
 }
 
@@ -640,7 +712,9 @@ static msort_status host_sort(msort_ctx* ctx, const void* h_kin_v, const uint32_
     const K* h_kin = static_cast<const K*>(h_kin_v);
     K* h_kout = static_cast<K*>(h_kout_v);
     msort_options tuned_opt{};
-    if (!opt || !opt->tile) {
+    const msort_options* caller = opt;
+    const bool single = single_wanted(n, opt);  // tuned shapes do not apply to the single launch
+    if (!single && (!opt || !opt->tile)) {
         const int tile = tuned_tile_for(ctx, (int)sizeof(K), PAIRS, n);
         if (tile) {
             if (opt) tuned_opt = *opt;
