@@ -377,6 +377,17 @@ size_t msort_noalloc_max_keys(msort_key_type kt, int with_vals);
  * context stays usable.  Touches no caller memory; MSORT_ERR_INVALID_ARG for
  * a limit outside the range. */
 msort_status msort_selftest_wait_timeout(msort_ctx* ctx, long long limit_cycles, void* stream);
+/* The same for the grid barriers of the single-launch sort (options.single_launch):
+ * enqueues that sort of the n uint32 keys at d_keys (n spanning at least two
+ * of its tiles, so that there is a barrier; up to 2^28) with every barrier
+ * wait limited to limit_cycles and the first barrier expecting one arrival
+ * more than the grid makes.  Every block completes its stores, gives up at
+ * that barrier after about limit_cycles, records MSORT_ERR_TIMEOUT and leaves;
+ * no copy is in flight.  The keys are left in an unspecified order.  Uses
+ * the context's scratch like a sort; MSORT_ERR_INVALID_ARG for a limit
+ * outside [1000, 2e9] or too small an n. */
+msort_status msort_selftest_grid_timeout(msort_ctx* ctx, void* d_keys, size_t n, long long limit_cycles,
+                                         void* stream);
 
 /* ---- autotuning ---------------------------------------------------------- */
 

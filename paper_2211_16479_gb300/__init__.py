@@ -66,6 +66,7 @@ _SIGS = {
     "msort_noalloc_max_keys": ([_I, _I], _SZ),
     "msort_noalloc_sync": ([_P], _ST),
     "msort_selftest_wait_timeout": ([_P, ctypes.c_longlong, _P], _ST),
+    "msort_selftest_grid_timeout": ([_P, _P, _SZ, ctypes.c_longlong, _P], _ST),
     "msort_tune": ([_P, ctypes.c_char_p, _I], _ST),
     "msort_tune_load": ([_P, ctypes.c_char_p], _ST),
     "msort_tune_clear": ([_P], _ST),
@@ -344,6 +345,14 @@ def msort_selftest_wait_timeout(ctx, limit_cycles: int = 100000, stream=None) ->
     """Enqueue the bounded-wait self-test: one merge block that gives up its
     wait after limit_cycles; the next msort_ctx_sync raises TIMEOUT."""
     _check(ctx, load_library().msort_selftest_wait_timeout(ctx, int(limit_cycles), _stream(stream)))
+
+
+def msort_selftest_grid_timeout(ctx, keys, limit_cycles: int = 100000, n=None, stream=None) -> None:
+    """Enqueue the grid-barrier self-test of the single-launch sort on the
+    uint32 device tensor `keys` (left unordered); the next msort_ctx_sync
+    raises TIMEOUT."""
+    _check(ctx, load_library().msort_selftest_grid_timeout(ctx, _ptr(keys), _numel(keys, n), int(limit_cycles),
+                                                           _stream(stream, keys)))
 
 
 def msort_tune(ctx, cache_path=None, quick: bool = False) -> None:

@@ -78,9 +78,12 @@ template <class K, bool PAIRS>
 int small_tile(size_t n);
 template <class K, bool PAIRS>
 bool small_tile_supported(int tile);
+// wait_limit: cycle limit of every grid-barrier wait; extra_arrivals: 0
+// (the self-test raises it so that the first barrier never completes).
 template <class K, bool PAIRS>
 cudaError_t launch_small(const Plan& pl, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, K* tk,
-                         uint32_t* tv, size_t n, void* barrier, cudaStream_t st, int xf_in, int xf_out);
+                         uint32_t* tv, size_t n, void* barrier, cudaStream_t st, int xf_in, int xf_out,
+                         long long wait_limit = 2000000000ll, unsigned int extra_arrivals = 0);
 // Resource summary of the last kernel the calling thread prepared to launch.
 const std::string& last_launch_info();
 

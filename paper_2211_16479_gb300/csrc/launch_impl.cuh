@@ -245,7 +245,7 @@ bool small_tile_supported(int tile) {
 template <class K, bool PAIRS, int TH, int IPT>
 static cudaError_t launch_small_shape(const Plan& pl, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout,
                                       K* tk, uint32_t* tv, size_t n, void* barrier, cudaStream_t st, int xf_in,
-                                      int xf_out) {
+                                      int xf_out, long long wait_limit, unsigned int extra_arrivals) {
     auto f = (xf_in || xf_out) ? k_small_sort<K, PAIRS, TH, IPT, true> : k_small_sort<K, PAIRS, TH, IPT, false>;
     const size_t sm = small_sort_smem<K, PAIRS, TH, IPT>();
     cudaError_t e = prepare(f, sm);
@@ -272,16 +272,18 @@ static cudaError_t launch_small_shape(const Plan& pl, const K* kin, const uint32
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, f, kin, vin, kout, vout, tk, tv, n, pl.passes,
-                              static_cast<GridBarrier*>(barrier), pl.status, xf_in, xf_out);
+                              static_cast<GridBarrier*>(barrier), pl.status, xf_in, xf_out, wait_limit,
+                              extra_arrivals);
 }
 
 template <class K, bool PAIRS>
 cudaError_t launch_small(const Plan& pl, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, K* tk,
-                         uint32_t* tv, size_t n, void* barrier, cudaStream_t st, int xf_in, int xf_out) {
+                         uint32_t* tv, size_t n, void* barrier, cudaStream_t st, int xf_in, int xf_out,
+                         long long wait_limit, unsigned int extra_arrivals) {
 #define MSORT_SMALL_CASE(TH, IPT)                                                                            \
     if (pl.tile == TH * IPT)                                                                                \
         return launch_small_shape<K, PAIRS, TH, IPT>(pl, kin, vin, kout, vout, tk, tv, n, barrier, st, xf_in, \
-                                                     xf_out);
+                                                     xf_out, wait_limit, extra_arrivals);
     MSORT_SMALL_CASE(256, 11)
     if constexpr (!PAIRS && sizeof(K) == 4) {
         MSORT_SMALL_CASE(256, 17)
@@ -340,8 +342,10 @@ cudaError_t launch_small(const Plan& pl, const K* kin, const uint32_t* vin, K* k
     template bool small_tile_supported<K, false>(int);                                                          \
     template bool small_tile_supported<K, true>(int);                                                           \
     template cudaError_t launch_small<K, false>(const Plan&, const K*, const uint32_t*, K*, uint32_t*, K*,        \
-                                                uint32_t*, size_t, void*, cudaStream_t, int, int);               \
+                                                uint32_t*, size_t, void*, cudaStream_t, int, int, long long,     \
+                                                unsigned int);                                                   \
     template cudaError_t launch_small<K, true>(const Plan&, const K*, const uint32_t*, K*, uint32_t*, K*,         \
-                                               uint32_t*, size_t, void*, cudaStream_t, int, int);
+                                               uint32_t*, size_t, void*, cudaStream_t, int, int, long long,      \
+                                               unsigned int);
 
 }  // namespace msort

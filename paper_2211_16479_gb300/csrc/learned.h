@@ -35,4 +35,8 @@ msort_status sort_with_scratch(msort_ctx* ctx, const K* kin, const uint32_t* vin
                                void* scratch, cudaStream_t st);
 size_t sort_scratch_need(size_t n, int key_bytes, bool pairs);
 
+// Grid-barrier self-test of the single launch (msort.cu).
+msort_status selftest_single_timeout(msort_ctx* ctx, void* d_keys, size_t n, long long limit_cycles,
+                                     cudaStream_t st);
+
 }  // namespace msort

@@ -422,6 +422,38 @@ static msort_status run_sort_graph(msort_ctx* ctx, const K* kin, const uint32_t*
     return MSORT_OK;
 }
 
+// Self-test of the single launch's grid barriers (msort_selftest_grid_timeout):
+// the single-launch sort of the n uint32 keys at d_keys, launched so that its
+// first grid barrier expects one arrival more than the grid makes, with
+// every wait limited to limit_cycles.  All blocks give up there, record the
+// timeout in the context's status word and leave; the keys are left in an
+// unspecified order.
+msort_status selftest_single_timeout(msort_ctx* ctx, void* d_keys, size_t n, long long limit_cycles,
+                                     cudaStream_t st) {
+    msort_options o{};
+    o.single_launch = 1;
+    Plan pl;
+    std::string why;
+    if (!make_plan<uint32_t, false>(n, &o, &pl, &why) || !apply_single<uint32_t, false>(n, &o, &pl, &why))
+        return fail(MSORT_ERR_INVALID_ARG, why);
+    if (!pl.single || pl.passes < 1) return fail(MSORT_ERR_INVALID_ARG, "n must span at least two single-launch tiles");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    pl.status = ctx->d_status;
+    msort_status s = ensure_scratch(ctx, scratch_need<uint32_t, false>(n, pl), st);
+    if (s != MSORT_OK) return s;
+    unsigned char* sp = static_cast<unsigned char*>(ctx->scratch);
+    uint32_t* tk = reinterpret_cast<uint32_t*>(sp);
+    void* barrier = sp + align_up(n * sizeof(uint32_t), 256);  // the split table (unused by this plan)
+    uint32_t* keys = static_cast<uint32_t*>(d_keys);
+    e = launch_small<uint32_t, false>(pl, keys, nullptr, keys, nullptr, tk, nullptr, n, barrier, st, 0, 0,
+                                      limit_cycles, 1u);
+    ++ctx->launches;
+    scratch_release(ctx, st);
+    return e == cudaSuccess ? MSORT_OK : cuda_fail(e, ("single-launch self-test" + last_launch_info()).c_str());
+}
+
 template <class K>
 size_t sort_keys_scratch(size_t n) {
     Plan pl;

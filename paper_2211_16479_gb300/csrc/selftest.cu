@@ -8,11 +8,13 @@
 // one arrival more than the block makes, with a short limit, so that this
 // path runs without any fault, trap or unbounded wait: the block's windows
 // are too short for a bulk copy (no copy is ever in flight) and its output
-// is never written.
+// is never written.  A second self-test does the same to the grid barrier
+// of the single-launch sort (msort.cu, selftest_single_timeout).
 #include <cuda_runtime.h>
 
 #include "ctx.h"
 #include "launch.h"
+#include "learned.h"
 #include "sort_kernels.cuh"
 
 namespace msort {
@@ -60,6 +62,15 @@ msort_status msort_selftest_wait_timeout(msort_ctx* ctx, long long limit_cycles,
     ++ctx->launches;
     e = cudaGetLastError();
     return e == cudaSuccess ? MSORT_OK : cuda_fail(e, "self-test launch");
+}
+
+msort_status msort_selftest_grid_timeout(msort_ctx* ctx, void* d_keys, size_t n, long long limit_cycles,
+                                         void* stream) {
+    if (!ctx) return fail(MSORT_ERR_INVALID_ARG, "ctx is NULL");
+    if (!d_keys) return fail(MSORT_ERR_INVALID_ARG, "d_keys is NULL");
+    if (limit_cycles < 1000 || limit_cycles > kWaitLimitCycles)
+        return fail(MSORT_ERR_INVALID_ARG, "limit_cycles must be in [1000, 2e9]");
+    return selftest_single_timeout(ctx, d_keys, n, limit_cycles, (cudaStream_t)stream);
 }
 
 }  // extern "C"

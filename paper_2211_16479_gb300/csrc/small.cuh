@@ -107,11 +107,13 @@ __device__ __forceinline__ size_t corank_warp(const K* A, size_t alen, const K* 
 // merge rounds with output blocks of W = T, ping-pong between (kout, vout)
 // and (tk, tv) starting where the last round lands in kout.  XF: the tile
 // sort applies xf_in and the last round (or, with no round, the tile sort)
-// undoes xf_out.
+// undoes xf_out.  wait_limit bounds every grid-barrier wait (production:
+// kWaitLimitCycles).
 template <class K, bool PAIRS, int THREADS, int IPT, bool XF>
 __global__ void __launch_bounds__(THREADS)
 k_small_sort(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, K* tk, uint32_t* tv, size_t n, int passes,
-             GridBarrier* gb, unsigned int* status, int xf_in, int xf_out) {
+             GridBarrier* gb, unsigned int* status, int xf_in, int xf_out, long long wait_limit,
+             unsigned int extra_arrivals) {
     constexpr int T = THREADS * IPT;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
@@ -136,10 +138,12 @@ k_small_sort(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, K* tk, 
                                                          phase, status, xf_in, passes == 0 ? xf_out : 0))
             return;
     }
-    unsigned int target = 0;  // arrivals that end the current barrier
+    // arrivals that end the current barrier (extra_arrivals is 0 except in the
+    // self-test, where the first barrier then never completes)
+    unsigned int target = extra_arrivals;
     for (int p = 0; p < passes; ++p) {
         target += G;
-        if (!grid_sync(gb, target, status, kWaitLimitCycles)) return;
+        if (!grid_sync(gb, target, status, wait_limit)) return;
         const size_t L = (size_t)T << p;
         const K* src = bk[cur];
         K* dst = bk[cur ^ 1];

@@ -57,3 +57,32 @@ def test_selftest_rejects_limits_out_of_range():
                 ms.msort_selftest_wait_timeout(ctx.handle, bad)
             assert e.value.status == ms.MSORT_ERR_INVALID_ARG
         ms.msort_ctx_sync(ctx.handle)
+
+
+@pytest.mark.parametrize("n", [2 * 4352, 3 * 4352 + 5, (1 << 20) + 3])
+def test_grid_barrier_expiry_reports_timeout(n):
+    """The single launch's grid barrier: the first barrier expects one block
+    more than the grid has; every block gives up after the short limit."""
+    need_gpu()
+    with ms.Context(0) as ctx:
+        d = to_dev(synth.uniform_u32(n, 6))
+        ms.msort_selftest_grid_timeout(ctx.handle, d, 20000)
+        with pytest.raises(ms.MsortError) as e:
+            ms.msort_ctx_sync(ctx.handle)
+        assert e.value.status == ms.MSORT_ERR_TIMEOUT
+        ms.msort_ctx_sync(ctx.handle)
+        keys = synth.uniform_u32(n, 7)
+        d = to_dev(keys)
+        ms.msort_sort(ctx.handle, d)  # the single launch itself still works
+        ms.msort_ctx_sync(ctx.handle)
+        assert np.array_equal(to_host(d), oracle.sort(keys)[0])
+
+
+def test_grid_selftest_rejects_bad_arguments():
+    need_gpu()
+    with ms.Context(0) as ctx:
+        d = to_dev(synth.uniform_u32(4352, 1))
+        for n, limit in ((4352, 20000), (8704, 10), (8704, 2000000001)):
+            with pytest.raises(ms.MsortError) as e:
+                ms.msort_selftest_grid_timeout(ctx.handle, d, limit, n=n)
+            assert e.value.status == ms.MSORT_ERR_INVALID_ARG
