@@ -12,12 +12,17 @@ def _rounds(n, tile):
     return r
 
 
+MULTI = {"single_launch": -1}  # the multi-launch plan (tile sort + a partition and a merge per round)
+
+
 @pytest.mark.parametrize("n", [1, 16896, 16897, 2 * 16896 + 1, 4 * 16896 + 1, 1 << 20, 1 << 28, (1 << 28) + 1])
 def test_pass_mapping(n):
-    T, W, rounds = ms.msort_plan_info(n, ms.MSORT_U32, False)
+    T, W, rounds = ms.msort_plan_info(n, ms.MSORT_U32, False, MULTI)
     assert T == 16896 and rounds == _rounds(n, T)
-    ways, mem = ms.msort_plan_passes(n, ms.MSORT_U32, False)
+    ways, mem = ms.msort_plan_passes(n, ms.MSORT_U32, False, MULTI)
     assert ways == 2 and mem == rounds  # default: one merge round per pass
+    if n > 1 << 22:  # beyond the single launch the default is this plan
+        assert ms.msort_plan_info(n, ms.MSORT_U32, False) == (T, W, rounds)
     ways, mem = ms.msort_plan_passes(n, ms.MSORT_U32, False, {"merge_ways": 4})
     if rounds >= 2:
         assert ways == 4 and mem == rounds // 2 + rounds % 2
@@ -71,3 +76,36 @@ def test_transformed_keys_plan_like_unsigned_and_refuse_other_passes(kt, width):
         with pytest.raises(ms.MsortError) as e:
             ms.msort_plan_passes(n, kt, False, opts)
         assert e.value.status == ms.MSORT_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("n,tile", [(1, 4352), (1 << 16, 4352), (1 << 19, 4352), ((1 << 19) + 1, 8704),
+                                    (1 << 20, 8704), ((1 << 20) + 1, 16896), (1 << 22, 16896)])
+def test_single_launch_plan_by_size(n, tile):
+    # up to 2^22 keys the default plan is one cooperative launch whose tile
+    # (= merge block) depends on n; its rounds still map to one pass each
+    T, W, rounds = ms.msort_plan_info(n, ms.MSORT_U32, False)
+    assert (T, W) == (tile, tile) and rounds == _rounds(n, tile)
+    assert ms.msort_plan_passes(n, ms.MSORT_U32, False) == (2, rounds)
+    # the scratch holds the ping-pong copy and the split table, whose first
+    # 8 bytes carry the grid barrier
+    assert ms.msort_scratch_bytes(n, ms.MSORT_U32, False) >= n * 4 + 8
+
+
+def test_single_launch_options():
+    n = 1 << 20
+    assert ms.msort_plan_info(n, ms.MSORT_U64, True)[0] == 4352
+    assert ms.msort_plan_info(1 << 16, ms.MSORT_U64, False)[0] == 2816
+    assert ms.msort_plan_info(n, ms.MSORT_U64, False)[0] == 8448
+    # forced beyond the automatic limit, with a chosen single-launch tile
+    assert ms.msort_plan_info(1 << 24, ms.MSORT_U32, False, {"single_launch": 1, "tile": 5632})[0] == 5632
+    # options the single launch does not take fall back to the multi-launch plan ...
+    assert ms.msort_plan_info(n, ms.MSORT_U32, False, {"tile": 8448})[0] == 8448
+    assert ms.msort_plan_passes(n, ms.MSORT_U32, False, {"merge_ways": 4})[0] == 4
+    # ... or are refused when the single launch is forced
+    for bad in ({"single_launch": 3}, {"single_launch": 1, "tile": 33792}, {"single_launch": 1, "partition_mode": 2},
+                {"single_launch": 1, "merge_ways": 4}, {"single_launch": 1, "merge_block": 8448}):
+        with pytest.raises(ms.MsortError) as e:
+            ms.msort_plan_info(n, ms.MSORT_U32, False, bad)
+        assert e.value.status == ms.MSORT_ERR_INVALID_ARG
+    with pytest.raises(ms.MsortError):
+        ms.msort_plan_info((1 << 28) + 1, ms.MSORT_U32, False, {"single_launch": 1})
