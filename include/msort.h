@@ -438,6 +438,21 @@ msort_status msort_learned_model(msort_ctx* ctx, float* h_params, float* h_err);
  * poor model costs probes, never correctness.  h_params == NULL returns to
  * training a fresh model per sort.  Synchronises the device. */
 msort_status msort_learned_set_model(msort_ctx* ctx, const float* h_params, float err);
+/* One merge pass's partition, as a call (to check every co-rank the sort
+ * uses): d_keys[0:n) holds sorted runs of run_length keys laid end to end
+ * (the last may be shorter), merged pairwise (runs 2j and 2j + 1) into
+ * output blocks of `block` keys (block divides 2 * run_length).  For every
+ * output block c, d_splits[c] = the stable co-rank of its first output c *
+ * block within its pair: how many of the pair's first-run keys come before
+ * it (Merge Path, cited in the paper's Section "Related Research").  mode:
+ * 0 the exact binary search of the plain sort, 1 the learned network's
+ * guided search (needs a model: a partition_mode 1 sort trained one on ctx,
+ * or msort_learned_set_model installed one), 2 the ratio-guess guided
+ * search, 3 the guided kernel's plain binary search.  Every mode returns the
+ * same exact co-ranks.  d_splits holds ceil(n / block) uint64 entries;
+ * unsigned key types only. */
+msort_status msort_partition_splits(msort_ctx* ctx, const void* d_keys, size_t n, size_t run_length,
+                                    size_t block, int mode, uint64_t* d_splits, msort_key_type kt, void* stream);
 /* Probes (tests of A[a] <= B[d-1-a]) and searches made by guided partition
  * launches (modes 1-3) while profiling was at level 2; resets the counts.
  * Synchronises the device. */

@@ -75,6 +75,7 @@ _SIGS = {
     "msort_learned_model": ([_P, _P, _P], _ST),
     "msort_learned_set_model": ([_P, _P, ctypes.c_float], _ST),
     "msort_ctx_partition_stats": ([_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)], _ST),
+    "msort_partition_splits": ([_P, _P, _SZ, _SZ, _SZ, _I, _P, _I, _P], _ST),
     "msort_server_create": ([_I, _SZ, _I, ctypes.POINTER(_P)], _ST),
     "msort_server_submit": ([_P, _P, _P, _SZ, _I, ctypes.POINTER(ctypes.c_uint64)], _ST),
     "msort_server_poll": ([_P, ctypes.c_uint64, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)], _ST),
@@ -394,6 +395,17 @@ def msort_learned_set_model(ctx, params, err: float = 0.0) -> None:
         return
     arr = (ctypes.c_float * 97)(*[float(v) for v in params])
     _check(ctx, load_library().msort_learned_set_model(ctx, arr, float(err)))
+
+
+def msort_partition_splits(ctx, keys, run_length: int, block: int, mode: int, splits, key_type=None,
+                           stream=None) -> None:
+    """splits[c] = co-rank of output block c of the pairwise merge of the
+    sorted runs of run_length keys in `keys` (mode 0 exact, 1 learned, 2
+    ratio guess, 3 counted exact); splits: int64/uint64 device tensor of
+    ceil(n / block) entries."""
+    _check(ctx, load_library().msort_partition_splits(ctx, _ptr(keys), _numel(keys, None), int(run_length),
+                                                      int(block), int(mode), _ptr(splits), _key_type(keys, key_type),
+                                                      _stream(stream, keys)))
 
 
 def msort_ctx_partition_stats(ctx):

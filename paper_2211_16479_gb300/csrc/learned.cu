@@ -613,6 +613,42 @@ msort_status msort_learned_set_model(msort_ctx* ctx, const float* h_params, floa
     return MSORT_OK;
 }
 
+msort_status msort_partition_splits(msort_ctx* ctx, const void* d_keys, size_t n, size_t run_length,
+                                    size_t block, int mode, uint64_t* d_splits, msort_key_type kt, void* stream) {
+    if (!ctx) return fail(MSORT_ERR_INVALID_ARG, "ctx is NULL");
+    if (kt != MSORT_U32 && kt != MSORT_U64) return fail(MSORT_ERR_UNSUPPORTED, "unsigned keys only");
+    if (mode < 0 || mode > 3) return fail(MSORT_ERR_INVALID_ARG, "mode must be 0, 1, 2 or 3");
+    if (n == 0) return MSORT_OK;
+    if (!d_keys || !d_splits) return fail(MSORT_ERR_INVALID_ARG, "NULL pointer");
+    if (block == 0 || block > (size_t)1 << 30 || run_length == 0 || (2 * run_length) % block)
+        return fail(MSORT_ERR_INVALID_ARG, "block must divide 2 * run_length");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    if (mode != 0) {
+        msort_status rs = ensure_state(ctx);
+        if (rs != MSORT_OK) return rs;
+        if (mode == 1 && !state(ctx)->trained)
+            return fail(MSORT_ERR_INVALID_ARG, "mode 1 needs a model: run a partition_mode 1 sort or install one first");
+    }
+    Plan pl{};
+    pl.W = (int)block;
+    pl.partition_mode = mode;
+    pl.status = ctx->d_status;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long* splits = reinterpret_cast<unsigned long long*>(d_splits);
+    if (kt == MSORT_U32)
+        e = mode == 0 ? launch_partition<uint32_t>(pl, static_cast<const uint32_t*>(d_keys), n, run_length, splits, st)
+                      : launch_guided_partition<uint32_t>(ctx, pl, static_cast<const uint32_t*>(d_keys), n,
+                                                          run_length, splits, st);
+    else
+        e = mode == 0 ? launch_partition<uint64_t>(pl, static_cast<const uint64_t*>(d_keys), n, run_length, splits, st)
+                      : launch_guided_partition<uint64_t>(ctx, pl, static_cast<const uint64_t*>(d_keys), n,
+                                                          run_length, splits, st);
+    ++ctx->launches;
+    return e == cudaSuccess ? MSORT_OK : cuda_fail(e, "partition launch");
+}
+
 msort_status msort_ctx_partition_stats(msort_ctx* ctx, uint64_t* probes, uint64_t* searches) {
     if (!ctx || !probes || !searches) return fail(MSORT_ERR_INVALID_ARG, "NULL argument");
     std::lock_guard<std::mutex> g(ctx->mu);

@@ -8,6 +8,7 @@
 // context's scratch; the tile sort writes to whichever of the two makes the
 // last round land in the caller's buffer, so no final copy is needed.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cstdio>
@@ -35,8 +36,14 @@ msort_status cuda_fail(cudaError_t e, const char* what) {
     return MSORT_ERR_CUDA;
 }
 
+// Names of the kernel kinds in NVTX ranges (profilers show each logged
+// launch as a named range on the host timeline).
+static const char* const kKindName[KK_COUNT] = {"msort tile sort", "msort partition", "msort merge pass",
+                                                "msort segmented", "msort mlp", "msort single launch"};
+
 void prof_begin(msort_ctx* ctx, int k, cudaStream_t st) {
     if (!ctx->profiling) return;
+    nvtxRangePushA(kKindName[k]);
     auto& v = ctx->prof[k];
     size_t& u = ctx->prof_used[k];
     if (u == v.size()) {
@@ -52,6 +59,7 @@ void prof_end(msort_ctx* ctx, int k, cudaStream_t st) {
     if (!ctx->profiling) return;
     cudaEventRecord(ctx->prof[k][ctx->prof_used[k]].b, st);
     ++ctx->prof_used[k];
+    nvtxRangePop();
 }
 
 msort_status ensure_scratch(msort_ctx* ctx, size_t bytes, cudaStream_t st) {

@@ -190,3 +190,60 @@ def test_ablation_model_cuts_probes(ctx):
         assert learned < ratio, report
     # on pre-sorted runs the positional ratio guess is far off; the CDF is not
     assert report["sorted"][2] < report["sorted"][1], report
+
+
+def _expected_splits(runs, L, W):
+    n = len(runs)
+    out = []
+    for c in range((n + W - 1) // W):
+        out0 = c * W
+        pb = (out0 // (2 * L)) * 2 * L
+        alen = min(L, n - pb)
+        blen = min(L, n - pb - alen)
+        out.append(oracle.corank(runs[pb:pb + alen], runs[pb + alen:pb + alen + blen], out0 - pb))
+    return np.array(out, dtype=np.uint64)
+
+
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+def test_every_partition_is_the_exact_corank(ctx, dtype):
+    """Each mode's split table for one merge pass (exact binary search, the
+    learned network's guided search, the ratio guess, the counted exact
+    search) against the oracle's co-rank of every output block, on runs of
+    two lengths with a ragged last run; then with a zeroed and a random
+    installed model."""
+    n = 300007
+    if dtype == np.uint32:
+        keys = synth.lognormal3_u32(n, 21)
+    else:
+        keys, _ = synth.dup_u64(n, 21, distinct=1 << 10)
+    d = to_dev(keys)
+    out = torch.empty_like(d)
+    ms.msort_sort_copy(ctx, d, out, options={"partition_mode": 1, "learned_passes": 64})  # trains a model
+    ms.msort_ctx_sync(ctx)
+    W = 8448
+    rng = np.random.default_rng(3)
+    models = [None, np.zeros(mlp.NPARAM), rng.normal(size=mlp.NPARAM) * 5]
+    try:
+        for L in (16896, 4 * 16896):
+            runs = np.concatenate([oracle.sort(keys[i:i + L])[0] for i in range(0, n, L)])
+            exp = _expected_splits(runs, L, W)
+            druns = to_dev(runs)
+            for model in models:
+                if model is not None:
+                    ms.msort_learned_set_model(ctx, model, 0.0)
+                for mode in (0, 1, 2, 3):
+                    splits = torch.full((len(exp),), -1, dtype=torch.int64, device="cuda")
+                    ms.msort_partition_splits(ctx, druns, L, W, mode, splits)
+                    ms.msort_ctx_sync(ctx)
+                    assert np.array_equal(to_host(splits).astype(np.uint64), exp), (L, mode, model is None)
+    finally:
+        ms.msort_learned_set_model(ctx, None)
+
+
+def test_partition_splits_argument_checks(ctx):
+    d = torch.zeros(1000, dtype=torch.uint32, device="cuda")
+    s = torch.zeros(10, dtype=torch.int64, device="cuda")
+    for L, W, mode in ((100, 300, 0), (100, 200, 4), (0, 100, 0)):
+        with pytest.raises(ms.MsortError) as e:
+            ms.msort_partition_splits(ctx, d, L, W, mode, s)
+        assert e.value.status == ms.MSORT_ERR_INVALID_ARG
