@@ -244,7 +244,10 @@ template <class K, bool PAIRS>
 static size_t scratch_need(size_t n, const Plan& pl) {
     size_t b = align_up(n * sizeof(K), 256);
     if (PAIRS) b += align_up(n * sizeof(uint32_t), 256);
-    size_t nblocks = (n + pl.W - 1) / pl.W;
+    // the single launch keeps a split table big enough for the multi-launch
+    // plan it falls back to (merge blocks of at least 4352 outputs)
+    const size_t Wt = pl.single ? std::min<size_t>((size_t)pl.W, 4352) : (size_t)pl.W;
+    size_t nblocks = (n + Wt - 1) / Wt;
     b += align_up((nblocks + 1) * sizeof(unsigned long long), 256);
     const size_t gm = merge4_grid_max(n, pl);
     if (gm) {
@@ -287,6 +290,19 @@ static msort_status run_sort(msort_ctx* ctx, const K* kin, const uint32_t* vin, 
         cudaError_t es = launch_small<K, PAIRS>(pl, kin, vin, kout, vout, tk, tv, n, splits, st, pl.xform,
                                                 pl.xform_out);
         if (log) prof_end(ctx, KK_SINGLE, st);
+        if (es == cudaErrorCooperativeLaunchTooLarge || es == cudaErrorNotSupported) {
+            // the device refused a grid that must be resident at once (for
+            // example under a limit on the SMs this process may use): sort
+            // with the multi-launch plan instead (its split table fits, see
+            // scratch_need)
+            cudaGetLastError();
+            Plan mp;
+            std::string why;
+            if (!make_plan<K, PAIRS>(n, nullptr, &mp, &why, pl.xform)) return fail(MSORT_ERR_INVALID_ARG, why);
+            mp.status = pl.status;
+            mp.xform_out = pl.xform_out;
+            return run_sort<K, PAIRS>(ctx, kin, vin, kout, vout, n, mp, scratch, log, st);
+        }
         ++ctx->launches;
         if (es != cudaSuccess) return cuda_fail(es, ("single-launch sort" + last_launch_info()).c_str());
         return MSORT_OK;
