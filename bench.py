@@ -192,7 +192,7 @@ def cpu_oracle_rate(sample_keys, seconds_target=12.0):
             total_t += time.perf_counter() - t0
             total_keys += len(a)
         reps += 1
-        if reps >= 50:
+        if reps >= 400:
             break
     return total_keys / total_t / 1e9, cores, reps
 
