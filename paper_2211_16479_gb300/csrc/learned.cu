@@ -24,7 +24,11 @@
 // ratio a0 = d |A| / (|A| + |B|), then take two secant steps in F-space:
 // the model's values at the two probed keys, scaled by each run's density
 // in F-space (from the model's values at the run's first and last keys);
-// each probe also narrows the bracket by its exact comparison.
+// each probe also narrows the bracket by its exact comparison.  The step
+// is computed without cancellation: F(kb) - F(ka) unit by unit from the
+// exact integer key difference, and the new position in 64-bit integers
+// (in fp32, positions near 2^29 and differences of nearby outputs resolve
+// only tens of elements).
 // Verification: an exponential search outward from the prediction (probes
 // at distance 1, 2, 4, ... until the split is bracketed; J. L. Bentley and
 // A. C. Yao, "An almost optimal algorithm for unbounded searching", 1976),
@@ -85,6 +89,8 @@ __device__ __forceinline__ float mlp_f(const float* p, float x) {
 
 __device__ __forceinline__ float clamp01(float v) { return fminf(fmaxf(v, 0.f), 1.f); }
 
+
+
 template <class K>
 __device__ __forceinline__ float key_to_x(K k);
 template <>
@@ -94,6 +100,35 @@ __device__ __forceinline__ float key_to_x<uint32_t>(uint32_t k) {
 template <>
 __device__ __forceinline__ float key_to_x<uint64_t>(uint64_t k) {
     return __ull2float_rn(k) * 5.421010862427522e-20f;  // k / 2^64, rounded to fp32
+}
+
+// (kb - ka) in the network's input units, from the exact integer difference
+template <class K>
+__device__ __forceinline__ float key_diff_x(K ka, K kb);
+template <>
+__device__ __forceinline__ float key_diff_x<uint32_t>(uint32_t ka, uint32_t kb) {
+    return (float)((long long)kb - (long long)ka) * 2.3283064365386963e-10f;
+}
+template <>
+__device__ __forceinline__ float key_diff_x<uint64_t>(uint64_t ka, uint64_t kb) {
+    const double d = kb >= ka ? (double)(kb - ka) : -(double)(ka - kb);
+    return (float)(d * 5.421010862427522e-20);
+}
+
+// F(kb) - F(ka) without the cancellation of subtracting two nearby outputs:
+// per hidden unit, the difference of its two ReLU values, taken from the
+// exact key difference where the unit is active at both keys.
+template <class K>
+__device__ __forceinline__ float mlp_diff(const float* p, K ka, K kb) {
+    const float xa = key_to_x<K>(ka), xb = key_to_x<K>(kb), dx = key_diff_x<K>(ka, kb);
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < kH; ++j) {
+        const float ua = fmaf(p[j], xa, p[kH + j]), ub = fmaf(p[j], xb, p[kH + j]);
+        const float dh = (ua > 0.f && ub > 0.f) ? p[j] * dx : fmaxf(ub, 0.f) - fmaxf(ua, 0.f);
+        s = fmaf(p[2 * kH + j], dh, s);
+    }
+    return s;
 }
 
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
@@ -340,9 +375,10 @@ __global__ void k_partition_guided(const K* __restrict__ src, size_t n, size_t L
                 else
                     hi = ahat;
                 if (lo >= hi) break;
-                const float delta = (mlp_f(p, key_to_x<K>(kb)) - mlp_f(p, key_to_x<K>(ka))) * inv;
-                const float cand = (float)ahat + rintf(delta);
-                ahat = cand <= (float)lo ? lo : (cand >= (float)hi ? hi : (size_t)cand);
+                const float delta = mlp_diff<K>(p, ka, kb) * inv;  // positions to move
+                const long long step = (long long)rintf(fminf(fmaxf(delta, -4.0e18f), 4.0e18f));
+                const long long cand = (long long)ahat + step;
+                ahat = cand <= (long long)lo ? lo : (cand >= (long long)hi ? hi : (size_t)cand);
             }
         }
         // Exponential search outward from the prediction; f(a) = A[a] <=
