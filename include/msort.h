@@ -103,12 +103,20 @@ typedef struct {
                            runs merged at once; keys-only sorts with partition_mode 0; half
                            the HBM traffic of the merge phase but slower on GB300, where the
                            pairwise pass runs at the copy bandwidth) */
-    int single_launch;  /* 0 = automatic: arrays of up to 2^22 elements are sorted by one
-                           cooperative launch that runs the tile sort and every merge round,
-                           with a grid barrier between rounds (such arrays stay in L2, where
-                           launch cost dominates), when tile, merge_block and partition_mode
-                           are 0 and passes are pairwise; 1 = that single launch up to 2^28
-                           elements (same conditions); -1 = never */
+    int single_launch;  /* 0 = automatic: msort_sort, msort_sort_pairs and msort_sort_copy
+                           sort arrays of up to 2^22 elements by one cooperative launch that
+                           runs the tile sort and every merge round, with a grid barrier
+                           between rounds (such arrays stay in L2, where launch cost
+                           dominates), when tile, merge_block and partition_mode are 0 and
+                           passes are pairwise; its tile (= merge block) follows n: 4352,
+                           8704 or 16896 for 32-bit keys alone, 2816 then 8448 (4352 for
+                           64-bit key-value pairs) otherwise.  1 = that single launch up to
+                           2^28 elements (same conditions, except that tile may name one of
+                           its shapes: 2816, 4352, 5632, 8448, 8704, 11264 or 16896 for 32-bit
+                           keys alone, 2816 and 8448 (4352 for 64-bit pairs) otherwise).
+                           -1 = never.  If the device refuses the cooperative grid, the sort
+                           runs the multi-launch plan instead (same result).  The host-buffer,
+                           segmented and serving paths always use the multi-launch plan */
     int reserved[1];    /* must be zero */
 } msort_options;
 
