@@ -164,3 +164,31 @@ def test_concurrent_single_launches_on_several_streams():
     finally:
         for c in ctxs:
             c.close()
+
+
+EDGE_SIZES = [0, 31, 32, 33] + [s for k in (10, 13, 15, 17, 19, 21, 22) for s in ((1 << k), (1 << k) + 1)]
+
+
+@pytest.mark.parametrize("n", EDGE_SIZES)
+@pytest.mark.parametrize("dtype,pairs", [(np.uint32, False), (np.uint64, True)])
+def test_single_launch_edge_sizes(ctx, n, dtype, pairs):
+    """The sizes of the survey's list (0, 31, 32, 33, 2^k, 2^k + 1) with
+    default options, up to the automatic limit 2^22 + 1 (the first size that
+    takes the multi-launch plan)."""
+    keys = _keys("uniform", n, n % 997 + 1, dtype)
+    vals = np.arange(n, dtype=np.uint32) if pairs else None
+    _sort_and_check(ctx, keys, vals, None)
+
+
+def test_single_launch_unaligned_pairs(ctx):
+    # views one element into larger buffers: the windows take scalar heads and tails
+    n = 70001
+    keys = _keys("few", n + 2, 4, np.uint64)
+    vals = np.arange(n + 2, dtype=np.uint32)
+    dk, dv = to_dev(keys), to_dev(vals)
+    ok = torch.empty(n + 2, dtype=dk.dtype, device="cuda")
+    ov = torch.empty(n + 2, dtype=dv.dtype, device="cuda")
+    ms.msort_sort_copy(ctx, dk[1:1 + n], ok[1:1 + n], dv[1:1 + n], ov[1:1 + n])
+    ms.msort_ctx_sync(ctx)
+    ek, ev = oracle.sort(keys[1:1 + n], vals[1:1 + n])
+    assert np.array_equal(to_host(ok)[1:1 + n], ek) and np.array_equal(to_host(ov)[1:1 + n], ev)
