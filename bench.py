@@ -25,7 +25,15 @@ Printed as one JSON line on rank 0.  Also reported:
                 without those events, the sorts replayed from CUDA graphs);
   cpu_baseline  the CPU oracle (chunked merge sort with a pairwise merge tree
                 on every host core) on a bounded sample of the same inputs;
-  clocks        nvidia-smi samples taken during the timed region.
+  clocks        nvidia-smi samples taken during the timed region;
+  chosen_vs_plain  the forms the method was extended with, each against the
+                plain sort on identical inputs in interleaved repetitions, with
+                identical output checked on the device: the learned partition
+                (2^30 lognormal-mixture keys; the model-free ratio start as the
+                ablation), the batched segmented sort (50,000 arrays) and the
+                continuous-batching server (2,000 requests; p50/p99);
+  small_config  the 2^20-key configuration (L2-resident): the single
+                cooperative launch against the multi-launch plan.
 
 --impl reference times the CPU oracle itself on the same metric (there is no
 GPU reference implementation of this method).
