@@ -85,7 +85,11 @@ typedef struct {
     int merge_block;    /* outputs per merge block: 0, or the value the tile implies
                            (4352 for tiles of 17 keys per thread, 8448 for 33) */
     int partition_mode; /* 0 = exact merge-path binary search; 1 = learned CDF predictor
-                           (window verified, exact search inside, so the result is the same);
+                           (window verified, exact search inside, so the result is the same;
+                           the network is trained on a key sample on a second stream while the
+                           sort runs, and partitions that start before its training has finished
+                           use the ratio guess of mode 2 instead of waiting; at profiling level 2
+                           they wait for it);
                            2 = ratio guess d*|A|/(|A|+|B|) with the same verification
                            (the learned mode without its model, for comparison);
                            3 = exact binary search in the guided kernel (diagnostics: its

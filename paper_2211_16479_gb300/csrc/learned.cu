@@ -59,15 +59,15 @@ struct LearnedState {
     uint64_t* sorted = nullptr;
     void* sort_scratch = nullptr;
     float* x = nullptr;
-    float* dy = nullptr;
     float* params = nullptr;
-    float* m1 = nullptr;
-    float* m2 = nullptr;
-    float* grad = nullptr;
+    void* train = nullptr;  // TrainState of the round kernels
     float* err = nullptr;
     unsigned long long* probes = nullptr;  // [0] probes, [1] searches
+    unsigned int* ready = nullptr;         // epoch of the last model whose training has finished
+    unsigned int epoch = 0;                // epoch of the model the current sort trains
     cudaStream_t side = nullptr;
-    cudaEvent_t input_ready = nullptr, model_ready = nullptr;
+    cudaEvent_t input_ready = nullptr, model_ready = nullptr, sampled = nullptr;
+    cudaGraphExec_t train_exec = nullptr;  // the training rounds of a sort, captured once
     bool pending = false;
     bool trained = false;
     bool frozen = false;  // a caller-installed model: skip sampling and training
@@ -156,7 +156,7 @@ __global__ void k_keys_to_x(const K* __restrict__ sorted, int m, int stride, flo
 // Knot initialisation from sorted x (one block of kH threads): unit j is
 // relu(x - q_j) with q_j the sample quantile at (j + 1/2) / H; output
 // weights are the slope changes between consecutive knots.
-__global__ void k_knot_init(const float* __restrict__ x, int m, float* __restrict__ p, float* m1, float* m2) {
+__global__ void k_knot_init(const float* __restrict__ x, int m, float* __restrict__ p) {
     __shared__ float q[kH], slope[kH];
     const int j = threadIdx.x;
     const float rank_j = (j + 0.5f) / kH;
@@ -174,143 +174,204 @@ __global__ void k_knot_init(const float* __restrict__ x, int m, float* __restric
     p[kH + j] = -q[j];
     p[2 * kH + j] = slope[j] - (j > 0 ? slope[j - 1] : 0.f);
     if (j == 0) p[3 * kH] = 0.5f / kH;
-    for (int i = j; i < kNP; i += kH) {
-        m1[i] = 0.f;
-        m2[i] = 0.f;
-    }
 }
 
-// The whole safeguarded training in one block of 512 threads (one launch,
-// one SM, so it runs beside the sort without taking the GPU from it).
-// Per round: forward over all samples (dy to `dy`, loss by a fixed tree),
-// the guard (accept: save and update; reject: restore, halve the rate,
-// restart the moments), and on accept the backward pass with each warp
-// owning two hidden units (lane-strided sums, then a fixed xor-shuffle tree;
-// the warp of unit 0 also sums dy for b2) followed by Adam.  grad_only != 0: one forward and
-// backward at the given parameters, gradient to grad_out, no update.
-constexpr int kTrainThreads = 512;
-constexpr int kUnitsPerWarp = kH / (kTrainThreads / 32);
-__global__ void __launch_bounds__(kTrainThreads)
-k_mlp_train_fused(const float* __restrict__ x, int m, float* __restrict__ params, int steps, float lr0,
-                  float* __restrict__ dy, float* __restrict__ grad_out, int grad_only) {
-    __shared__ float p[kNP], g[kNP], m1[kNP], m2[kNP], saved[kNP];
-    __shared__ float red[kTrainThreads];
-    __shared__ float lr, best, pw1, pw2;  // pw1 = 0.9^k, pw2 = 0.999^k for the bias corrections
-    __shared__ int seen, accept;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int i = tid; i < kNP; i += kTrainThreads) {
-        p[i] = params[i];
-        m1[i] = 0.f;
-        m2[i] = 0.f;
-    }
-    if (tid == 0) {
-        lr = lr0;
-        best = 0.f;
-        pw1 = 1.f;
-        pw2 = 1.f;
-        seen = 0;
-    }
-    __syncthreads();
+// Training, one launch per round, spread over kTrainBlocks blocks.  Each
+// round evaluates the loss at the current parameters and (when an update
+// may follow) the full-batch gradient there: block b takes the points
+// [b m / B, (b + 1) m / B) in chunks of kChunk (x and dy of a chunk in
+// shared memory), sums its squared residuals by a fixed tree and its
+// gradient with each warp owning four hidden units (lane-strided sums over
+// the chunks, then a fixed xor-shuffle tree), and writes the 98 partial sums
+// to its own row.  Few blocks: a round is bound by its fixed latency (launch,
+// the L2 round trips of the reduction), not by its arithmetic, and every
+// block it holds is an SM slot the concurrent sort does not get.  The last block to finish (a
+// counter taken after a release fence) adds the rows in block order, so the
+// totals do not depend on which blocks ran first, and applies the guard and
+// the Adam update to the state the next round starts from:
+//   accept (first round, or loss <= best): best = loss; save the parameters;
+//     in the final round stop there, else take one Adam step;
+//   reject: restore the saved parameters, halve the rate, restart the moments.
+// A final round that is rejected needs one more forward evaluation (of the
+// restored parameters, which is then accepted), so the host launches
+// steps + 2 rounds and a round that finds the training finished returns at
+// once.  grad_only: one round that writes the summed gradient to grad_out.
+constexpr int kTrainBlocks = 8;
+constexpr int kRoundThreads = 256;
+constexpr int kUnitsPerWarp = kH / (kRoundThreads / 32);
+constexpr int kChunk = 2048;
+constexpr int kPartStride = 100;  // 97 gradient sums, the squared-residual sum, padding
+
+struct TrainState {
+    float saved[128], m1[128], m2[128];
+    float lr, best, pw1, pw2;  // pw1 = 0.9^k, pw2 = 0.999^k for the bias corrections
+    int seen, finished;
+    unsigned int arrived;      // blocks of the current round done
+    unsigned int pad;
+    float part[kTrainBlocks][kPartStride];
+};
+
+__global__ void __launch_bounds__(kRoundThreads)
+k_mlp_round(const float* __restrict__ x, int m, float* __restrict__ params, TrainState* __restrict__ ts, int first,
+            int need_grad, int final_round, float lr0, float* __restrict__ grad_out) {
+    __shared__ float p[kNP], xs[kChunk], dys[kChunk], red[kRoundThreads], tot[kPartStride];
+    __shared__ int is_last, accept;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, b = blockIdx.x;
+    if (!first && !grad_out && ts->finished) return;  // uniform: every block reads the same flag
+    for (int i = tid; i < kNP; i += kRoundThreads) p[i] = params[i];
+    const int r0 = (int)(((long long)b * m) / kTrainBlocks), r1 = (int)(((long long)(b + 1) * m) / kTrainBlocks);
+    const int cnt = r1 - r0;
     const float inv_m = 1.f / (float)m;
-    for (int round = 0;; ++round) {
-        float e2 = 0.f;
-        for (int r = tid; r < m; r += kTrainThreads) {
-            const float res = mlp_f(p, x[r]) - (r + 0.5f) * inv_m;
-            dy[r] = 2.f * res * inv_m;
+    float w1[kUnitsPerWarp], b1[kUnitsPerWarp], w2[kUnitsPerWarp];
+    float a0[kUnitsPerWarp], a1[kUnitsPerWarp], a2[kUnitsPerWarp];
+    float ab = 0.f, e2 = 0.f;
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kUnitsPerWarp; ++u) {
+        const int j = warp * kUnitsPerWarp + u;
+        w1[u] = p[j];
+        b1[u] = p[kH + j];
+        w2[u] = p[2 * kH + j];
+        a0[u] = a1[u] = a2[u] = 0.f;
+    }
+    for (int c0 = 0; c0 < cnt; c0 += kChunk) {
+        const int cc = cnt - c0 < kChunk ? cnt - c0 : kChunk;
+        for (int i = tid; i < cc; i += kRoundThreads) {
+            const int r = r0 + c0 + i;
+            const float xr = x[r];
+            const float res = mlp_f(p, xr) - (r + 0.5f) * inv_m;
+            xs[i] = xr;
+            dys[i] = 2.f * res * inv_m;
             e2 += res * res;
         }
-        red[tid] = e2;
         __syncthreads();
-        for (int w = kTrainThreads / 2; w > 0; w >>= 1) {
-            if (tid < w) red[tid] += red[tid + w];
-            __syncthreads();
-        }
-        const bool last = grad_only || round >= steps;  // a rejected final round re-checks once more
-        if (tid == 0) {
-            const float loss = red[0] * inv_m;
-            accept = grad_only || !seen || loss <= best;
-            if (accept) {
-                best = loss;
-                seen = 1;
-            } else {
-                lr *= 0.5f;
-                pw1 = 1.f;
-                pw2 = 1.f;
-            }
-        }
-        __syncthreads();
-        if (!accept) {
-            for (int i = tid; i < kNP; i += kTrainThreads) {
-                p[i] = saved[i];
-                m1[i] = 0.f;
-                m2[i] = 0.f;
-            }
-            __syncthreads();
-            continue;
-        }
-        if (!grad_only)
-            for (int i = tid; i < kNP; i += kTrainThreads) saved[i] = p[i];
-        if (last && !grad_only) break;
-        // backward: warp w -> units w * kUnitsPerWarp + u
+        if (need_grad) {
+            for (int i = lane; i < cc; i += 32) {
+                const float xr = xs[i], d = dys[i];
 #pragma unroll
-        for (int u = 0; u < kUnitsPerWarp; ++u) {
-            const int j = warp * kUnitsPerWarp + u;
-            const float w1 = p[j], b1 = p[kH + j], w2 = p[2 * kH + j];
-            float a0 = 0.f, a1 = 0.f, a2 = 0.f, ab = 0.f;
-            for (int r = lane; r < m; r += 32) {
-                const float xr = x[r], d = dy[r];
-                const float pre = fmaf(w1, xr, b1);
-                const bool act = pre > 0.f;
-                const float h = act ? pre : 0.f;
-                const float gp = act ? d * w2 : 0.f;
-                a0 = fmaf(gp, xr, a0);
-                a1 += gp;
-                a2 = fmaf(d, h, a2);
-                if (j == 0) ab += d;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-                a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-                a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-                ab += __shfl_xor_sync(0xffffffffu, ab, o);
-            }
-            if (lane == 0) {
-                g[j] = a0;
-                g[kH + j] = a1;
-                g[2 * kH + j] = a2;
-                if (j == 0) g[3 * kH] = ab;
+                for (int u = 0; u < kUnitsPerWarp; ++u) {
+                    const float pre = fmaf(w1[u], xr, b1[u]);
+                    const bool act = pre > 0.f;
+                    const float h = act ? pre : 0.f;
+                    const float gp = act ? d * w2[u] : 0.f;
+                    a0[u] = fmaf(gp, xr, a0[u]);
+                    a1[u] += gp;
+                    a2[u] = fmaf(d, h, a2[u]);
+                }
+                ab += d;
             }
         }
-        __syncthreads();
-        if (grad_only) {
-            for (int i = tid; i < kNP; i += kTrainThreads) grad_out[i] = g[i];
-            return;
-        }
-        if (tid < kNP) {
-            const float b1c = 0.9f, b2c = 0.999f, eps = 1e-8f;
-            const float c1 = 1.f - pw1 * b1c, c2 = 1.f - pw2 * b2c;  // 1 - beta^(k+1)
-            const float gi = g[tid];
-            const float a = b1c * m1[tid] + (1.f - b1c) * gi;
-            const float v = b2c * m2[tid] + (1.f - b2c) * gi * gi;
-            m1[tid] = a;
-            m2[tid] = v;
-            p[tid] -= lr * (a / c1) / (sqrtf(v / c2) + eps);
-        }
-        __syncthreads();
-        if (tid == 0) {
-            pw1 *= 0.9f;
-            pw2 *= 0.999f;
-        }
+        __syncthreads();  // the chunk buffers are reused
+    }
+    red[tid] = e2;
+    __syncthreads();
+    for (int w = kRoundThreads / 2; w > 0; w >>= 1) {
+        if (tid < w) red[tid] += red[tid + w];
         __syncthreads();
     }
+    float* row = ts->part[b];
+    if (tid == 0) row[kNP] = red[0];
+    if (need_grad) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int u = 0; u < kUnitsPerWarp; ++u) {
+                a0[u] += __shfl_xor_sync(0xffffffffu, a0[u], o);
+                a1[u] += __shfl_xor_sync(0xffffffffu, a1[u], o);
+                a2[u] += __shfl_xor_sync(0xffffffffu, a2[u], o);
+            }
+            ab += __shfl_xor_sync(0xffffffffu, ab, o);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int u = 0; u < kUnitsPerWarp; ++u) {
+                const int j = warp * kUnitsPerWarp + u;
+                row[j] = a0[u];
+                row[kH + j] = a1[u];
+                row[2 * kH + j] = a2[u];
+            }
+            if (warp == 0) row[3 * kH] = ab;
+        }
+    }
     __syncthreads();
-    for (int i = tid; i < kNP; i += kTrainThreads) params[i] = saved[i];
+    if (tid == 0) {
+        __threadfence();  // release this block's row before counting it
+        is_last = atomicAdd(&ts->arrived, 1u) == (unsigned)(kTrainBlocks - 1);
+        if (is_last) __threadfence();  // acquire: every row is visible below
+    }
+    __syncthreads();
+    if (!is_last) return;
+
+    // the last block: totals in block order, then the guard and the update
+    if (tid <= kNP) {
+        float s = 0.f;
+        for (int q = 0; q < kTrainBlocks; ++q) s += __ldcg(&ts->part[q][tid]);
+        tot[tid] = s;
+    }
+    __syncthreads();
+    if (grad_out) {
+        for (int i = tid; i < kNP; i += kRoundThreads) grad_out[i] = tot[i];
+        if (tid == 0) ts->arrived = 0;
+        return;
+    }
+    if (tid == 0) {
+        if (first) {
+            ts->lr = lr0;
+            ts->best = 0.f;
+            ts->pw1 = 1.f;
+            ts->pw2 = 1.f;
+            ts->seen = 0;
+        }
+        const float loss = tot[kNP] * inv_m;
+        accept = !ts->seen || loss <= ts->best;
+        if (accept) {
+            ts->best = loss;
+            ts->seen = 1;
+        } else {
+            ts->lr *= 0.5f;
+            ts->pw1 = 1.f;
+            ts->pw2 = 1.f;
+        }
+    }
+    __syncthreads();
+    if (tid < kNP) {
+        float m1 = first ? 0.f : ts->m1[tid], m2 = first ? 0.f : ts->m2[tid];
+        float pi = p[tid];
+        if (!accept) {
+            pi = ts->saved[tid];
+            m1 = 0.f;
+            m2 = 0.f;
+        } else {
+            ts->saved[tid] = pi;
+            if (!final_round) {
+                const float b1c = 0.9f, b2c = 0.999f, eps = 1e-8f;
+                const float c1 = 1.f - ts->pw1 * b1c, c2 = 1.f - ts->pw2 * b2c;  // 1 - beta^(k+1)
+                const float gi = tot[tid];
+                m1 = b1c * m1 + (1.f - b1c) * gi;
+                m2 = b2c * m2 + (1.f - b2c) * gi * gi;
+                pi -= ts->lr * (m1 / c1) / (sqrtf(m2 / c2) + eps);
+            }
+        }
+        ts->m1[tid] = m1;
+        ts->m2[tid] = m2;
+        params[tid] = pi;  // accepted final round: pi is the saved (best) value
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (accept && !final_round) {
+            ts->pw1 *= 0.9f;
+            ts->pw2 *= 0.999f;
+        }
+        ts->finished = accept && final_round;
+        ts->arrived = 0;
+    }
 }
 
 // err[0] = max_r |clamp(F(x_r)) - t_r| (one block, fixed reduction).
+// Also publishes the model: after err is written, *ready = epoch (release),
+// which the guided partitions of the sort poll once per block.
 __global__ void k_model_error(const float* __restrict__ x, int m, const float* __restrict__ params,
-                              float* __restrict__ err) {
+                              float* __restrict__ err, unsigned int* ready, unsigned int epoch) {
     constexpr int TH = 256;
     __shared__ float p[kNP];
     __shared__ float s[TH];
@@ -324,20 +385,36 @@ __global__ void k_model_error(const float* __restrict__ x, int m, const float* _
         if (threadIdx.x < w) s[threadIdx.x] = fmaxf(s[threadIdx.x], s[threadIdx.x + w]);
         __syncthreads();
     }
-    if (threadIdx.x == 0) err[0] = s[0];
+    if (threadIdx.x == 0) {
+        err[0] = s[0];
+        __threadfence();  // the parameters (earlier kernels of this stream) and err before the flag
+        atomicExch(ready, epoch);
+    }
 }
 
 // Co-rank with a guided start.  params == nullptr: ratio guess (mode 2);
 // exact_only: no guess at all (plain binary search, mode 3, used to count
 // its probes).  Counts probes (one probe = one test of A[a] <= B[d-1-a]).
+// A model trained beside the sort is used once its training has finished:
+// each block reads *ready (acquire) once and takes the model if it holds
+// this sort's epoch, else starts from the ratio guess.  The split is the
+// exact co-rank either way; the sort never waits for its model.  ready ==
+// nullptr: the parameters are a fixed, installed model.
 template <class K>
 __global__ void k_partition_guided(const K* __restrict__ src, size_t n, size_t L, size_t W, size_t nblocks,
                                    unsigned long long* __restrict__ splits, const float* __restrict__ params,
-                                   int exact_only,
+                                   const unsigned int* ready, unsigned int epoch, int exact_only,
                                    unsigned long long* probes) {
     __shared__ float p[kNP];
-    if (params)
-        for (int i = threadIdx.x; i < kNP; i += blockDim.x) p[i] = params[i];
+    __shared__ int use_model;
+    if (threadIdx.x == 0) {
+        unsigned int v = epoch;
+        if (params && ready) asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ready) : "memory");
+        use_model = params != nullptr && v == epoch;
+    }
+    __syncthreads();
+    if (use_model)  // L2 loads: the parameters were written by another stream's kernels
+        for (int i = threadIdx.x; i < kNP; i += blockDim.x) p[i] = __ldcg(params + i);
     __syncthreads();
     const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned int live = __ballot_sync(0xffffffffu, c < nblocks);  // lanes that search (blockDim % 32 == 0)
@@ -353,7 +430,7 @@ __global__ void k_partition_guided(const K* __restrict__ src, size_t n, size_t L
     if (lo < hi && !exact_only) {
         size_t ahat = (size_t)((double)d * (double)alen / (double)(alen + blen));
         ahat = ahat < lo ? lo : (ahat > hi ? hi : ahat);
-        if (params) {
+        if (use_model) {
             // Secant steps in F-space.  A run's keys cover [F(first), F(last)]
             // (the whole CDF for random-order runs, a sliver for presorted
             // ones), so moving a by D shifts F(A[a]) by about D * sA and
@@ -443,7 +520,8 @@ static msort_status ensure_state(msort_ctx* ctx) {
     if (ctx->learned) return MSORT_OK;
     LearnedState* s = new LearnedState();
     const size_t ssz = align_up(sort_keys_scratch<uint64_t>(kSample), 256);
-    const size_t bytes = 2 * (size_t)kSample * 8 + ssz + 2 * (size_t)kSample * 4 + 8 * 512 + 1024 + 256;
+    const size_t tsz = align_up(sizeof(TrainState), 256);
+    const size_t bytes = 2 * (size_t)kSample * 8 + ssz + (size_t)kSample * 4 + tsz + 3 * 512 + 256;
     if (cudaMalloc(&s->block, bytes) != cudaSuccess) {
         cudaGetLastError();
         delete s;
@@ -458,20 +536,16 @@ static msort_status ensure_state(msort_ctx* ctx) {
     q += ssz;
     s->x = reinterpret_cast<float*>(q);
     q += (size_t)kSample * 4;
-    s->dy = reinterpret_cast<float*>(q);
-    q += (size_t)kSample * 4;
+    s->train = q;
+    q += tsz;
     s->params = reinterpret_cast<float*>(q);
-    q += 512;
-    s->m1 = reinterpret_cast<float*>(q);
-    q += 512;
-    s->m2 = reinterpret_cast<float*>(q);
-    q += 512;
-    s->grad = reinterpret_cast<float*>(q);
     q += 512;
     s->err = reinterpret_cast<float*>(q);
     q += 512;
     s->probes = reinterpret_cast<unsigned long long*>(q);
-    cudaMemset(s->probes, 0, 16);
+    s->ready = reinterpret_cast<unsigned int*>(q + 16);
+    cudaMemset(s->train, 0, sizeof(TrainState));  // the round counter starts at zero
+    cudaMemset(s->probes, 0, 16 + sizeof(unsigned int));
     cudaMemset(s->err, 0, 4);
     int lo_prio = 0, hi_prio = 0;
     cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
@@ -480,6 +554,7 @@ static msort_status ensure_state(msort_ctx* ctx) {
     cudaStreamCreateWithPriority(&s->side, cudaStreamNonBlocking, hi_prio);
     cudaEventCreateWithFlags(&s->input_ready, cudaEventDisableTiming);
     cudaEventCreateWithFlags(&s->model_ready, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&s->sampled, cudaEventDisableTiming);
     ctx->learned = s;
     return MSORT_OK;
 }
@@ -491,8 +566,10 @@ void learned_destroy(msort_ctx* ctx) {
         cudaStreamSynchronize(s->side);
         cudaStreamDestroy(s->side);
     }
+    if (s->train_exec) cudaGraphExecDestroy(s->train_exec);
     if (s->input_ready) cudaEventDestroy(s->input_ready);
     if (s->model_ready) cudaEventDestroy(s->model_ready);
+    if (s->sampled) cudaEventDestroy(s->sampled);
     cudaFree(s->block);
     delete s;
     ctx->learned = nullptr;
@@ -505,19 +582,57 @@ int learned_first_pass(const Plan& pl, size_t) {
     return p;
 }
 
+// steps + 2 rounds (the last one returns at once unless the final round was
+// rejected); each round's launch waits for the previous one on the stream.
 static cudaError_t train_on(msort_ctx* ctx, LearnedState* s, const float* x, int m, float* params, int steps,
                             float lr, cudaStream_t st) {
-    k_mlp_train_fused<<<1, kTrainThreads, 0, st>>>(x, m, params, steps, lr, s->dy, nullptr, 0);
-    ++ctx->launches;
+    TrainState* ts = static_cast<TrainState*>(s->train);
+    for (int r = 0; r <= steps + 1; ++r) {
+        k_mlp_round<<<kTrainBlocks, kRoundThreads, 0, st>>>(x, m, params, ts, r == 0, r < steps, r >= steps, lr,
+                                                            nullptr);
+        ++ctx->launches;
+    }
     return cudaGetLastError();
 }
 
+// The training of a sort (kTrainSteps steps on the fixed sample buffers)
+// replayed from a CUDA graph: one host call instead of one per round, so
+// the host does not hold back the sort's own launches.  Captured on a
+// stream of its own the first time.
+static cudaError_t train_sample(msort_ctx* ctx, LearnedState* s, int m) {
+    if (!s->train_exec) {
+        cudaStream_t cs = nullptr;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const unsigned long long before = ctx->launches;
+            const cudaError_t le = train_on(ctx, s, s->x, m, s->params, kTrainSteps, kLr, cs);
+            ctx->launches = before;
+            e = cudaStreamEndCapture(cs, &g);
+            if (e == cudaSuccess) e = le;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&s->train_exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) {
+            s->train_exec = nullptr;
+            return e;
+        }
+    }
+    ctx->launches += kTrainSteps + 2;
+    return cudaGraphLaunch(s->train_exec, s->side);
+}
+
 template <class K>
-msort_status learned_prepare(msort_ctx* ctx, const Plan& pl, const K* keys, size_t n, cudaStream_t st) {
+msort_status learned_prepare(msort_ctx* ctx, const Plan& pl, const K* keys, size_t n, cudaStream_t st,
+                             bool keys_overwritten) {
     msort_status rs = ensure_state(ctx);
     if (rs != MSORT_OK) return rs;
     LearnedState* s = state(ctx);
     if (s->frozen) return MSORT_OK;
+    if (++s->epoch == 0) s->epoch = 1;  // 0 is the flag's value before any model
     cudaError_t e = cudaEventRecord(s->input_ready, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s->side, s->input_ready, 0);
     if (e != cudaSuccess) return cuda_fail(e, "learned partitioner stream order");
@@ -525,15 +640,20 @@ msort_status learned_prepare(msort_ctx* ctx, const Plan& pl, const K* keys, size
     K* sorted = reinterpret_cast<K*>(s->sorted);
     k_sample<K><<<kSample / 256, 256, 0, s->side>>>(keys, n, 0x5EEDull + n, sample);
     ++ctx->launches;
+    if (keys_overwritten) {  // the sort's first kernel writes `keys`: it waits until the sample is taken
+        e = cudaEventRecord(s->sampled, s->side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, s->sampled, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "learned partitioner stream order");
+    }
     rs = sort_keys_internal<K>(ctx, sample, sorted, kSample, s->sort_scratch, s->side);
     if (rs != MSORT_OK) return rs;
     const int mt = kSample / kTrainStride;
     k_keys_to_x<K><<<mt / 256, 256, 0, s->side>>>(sorted, kSample, kTrainStride, s->x);
-    k_knot_init<<<1, kH, 0, s->side>>>(s->x, mt, s->params, s->m1, s->m2);
+    k_knot_init<<<1, kH, 0, s->side>>>(s->x, mt, s->params);
     ctx->launches += 2;
-    e = train_on(ctx, s, s->x, mt, s->params, kTrainSteps, kLr, s->side);
+    e = train_sample(ctx, s, mt);
     if (e == cudaSuccess) {
-        k_model_error<<<1, 256, 0, s->side>>>(s->x, mt, s->params, s->err);
+        k_model_error<<<1, 256, 0, s->side>>>(s->x, mt, s->params, s->err, s->ready, s->epoch);
         ++ctx->launches;
         e = cudaGetLastError();
     }
@@ -552,7 +672,9 @@ cudaError_t launch_guided_partition(msort_ctx* ctx, const Plan& pl, const K* src
     LearnedState* s = state(ctx);
     const bool model = pl.partition_mode == 1;
     const int exact_only = pl.partition_mode == 3;
-    if (model && s->pending) {
+    if (model && s->pending && ctx->count_probes) {
+        // counting probes measures the model: wait for it instead of
+        // searching from the ratio guess until it is ready
         cudaError_t e = cudaStreamWaitEvent(st, s->model_ready, 0);
         if (e != cudaSuccess) return e;
         s->pending = false;
@@ -560,13 +682,13 @@ cudaError_t launch_guided_partition(msort_ctx* ctx, const Plan& pl, const K* src
     const size_t nblocks = (n + pl.W - 1) / pl.W;
     const unsigned th = 128;
     k_partition_guided<K><<<(unsigned)((nblocks + th - 1) / th), th, 0, st>>>(
-        src, n, L, (size_t)pl.W, nblocks, splits, model ? s->params : nullptr, exact_only,
-        ctx->count_probes ? s->probes : nullptr);
+        src, n, L, (size_t)pl.W, nblocks, splits, model ? s->params : nullptr, s->frozen ? nullptr : s->ready,
+        s->epoch, exact_only, ctx->count_probes ? s->probes : nullptr);
     return cudaGetLastError();
 }
 
-template msort_status learned_prepare<uint32_t>(msort_ctx*, const Plan&, const uint32_t*, size_t, cudaStream_t);
-template msort_status learned_prepare<uint64_t>(msort_ctx*, const Plan&, const uint64_t*, size_t, cudaStream_t);
+template msort_status learned_prepare<uint32_t>(msort_ctx*, const Plan&, const uint32_t*, size_t, cudaStream_t, bool);
+template msort_status learned_prepare<uint64_t>(msort_ctx*, const Plan&, const uint64_t*, size_t, cudaStream_t, bool);
 template cudaError_t launch_guided_partition<uint32_t>(msort_ctx*, const Plan&, const uint32_t*, size_t, size_t,
                                                        unsigned long long*, cudaStream_t);
 template cudaError_t launch_guided_partition<uint64_t>(msort_ctx*, const Plan&, const uint64_t*, size_t, size_t,
@@ -589,10 +711,13 @@ msort_status msort_mlp_grad(msort_ctx* ctx, const float* d_x, size_t m, const fl
     LearnedState* s = state(ctx);
     cudaStream_t st = (cudaStream_t)stream;
     cudaStreamSynchronize(s->side);
-    k_mlp_train_fused<<<1, kTrainThreads, 0, st>>>(d_x, (int)m, const_cast<float*>(d_params), 0, 0.f, s->dy, d_grad,
-                                                   1);
+    k_mlp_round<<<kTrainBlocks, kRoundThreads, 0, st>>>(d_x, (int)m, const_cast<float*>(d_params),
+                                                        static_cast<TrainState*>(s->train), 1, 1, 0, 0.f, d_grad);
     ++ctx->launches;
     cudaError_t e = cudaGetLastError();
+    // the training state is shared with the side stream: its later work waits for this launch
+    if (e == cudaSuccess) e = cudaEventRecord(s->input_ready, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->side, s->input_ready, 0);
     return e == cudaSuccess ? MSORT_OK : cuda_fail(e, "gradient launch");
 }
 
@@ -609,10 +734,12 @@ msort_status msort_mlp_train(msort_ctx* ctx, const float* d_x, size_t m, float* 
     cudaStream_t st = (cudaStream_t)stream;
     cudaStreamSynchronize(s->side);
     if (knot_init) {
-        k_knot_init<<<1, kH, 0, st>>>(d_x, (int)m, d_params, s->m1, s->m2);
+        k_knot_init<<<1, kH, 0, st>>>(d_x, (int)m, d_params);
         ++ctx->launches;
     }
     cudaError_t e = train_on(ctx, s, d_x, (int)m, d_params, steps, lr, st);
+    if (e == cudaSuccess) e = cudaEventRecord(s->input_ready, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->side, s->input_ready, 0);
     return e == cudaSuccess ? MSORT_OK : cuda_fail(e, "training launch");
 }
 

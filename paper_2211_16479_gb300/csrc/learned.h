@@ -10,10 +10,14 @@ namespace msort {
 // First merge pass (0-based) whose partition uses the guided search.
 int learned_first_pass(const Plan& pl, size_t n);
 // Draw the key sample from the unsorted input, sort it and train the network
-// on the device.  Runs on a side stream that waits for `st`; the first
-// guided partition launch on `st` waits for the training to finish.
+// on the device.  Runs on a side stream that waits for `st`; the guided
+// partitions on `st` use the model once its training has finished (a device
+// flag), and the ratio guess before.  keys_overwritten: the sort's first
+// kernel writes `keys` (in place with an even number of passes), so `st`
+// waits until the sample is taken.
 template <class K>
-msort_status learned_prepare(msort_ctx* ctx, const Plan& pl, const K* keys, size_t n, cudaStream_t st);
+msort_status learned_prepare(msort_ctx* ctx, const Plan& pl, const K* keys, size_t n, cudaStream_t st,
+                             bool keys_overwritten);
 // Partition launch that starts each co-rank search from a prediction (the
 // network's in mode 1, the length ratio in mode 2) and verifies it; exact
 // binary search finishes inside the verified bracket.

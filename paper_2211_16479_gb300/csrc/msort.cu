@@ -597,7 +597,8 @@ static msort_status sort_entry(msort_ctx* ctx, const void* kin, const uint32_t* 
     msort_status s = ensure_scratch(ctx, scratch_need<K, PAIRS>(n, pl), st);
     if (s != MSORT_OK) return s;
     if (pl.partition_mode == 1 && pl.passes > 0) {
-        s = learned_prepare<K>(ctx, pl, static_cast<const K*>(kin), n, st);
+        // the tile sort writes the caller's output when the pass count is even
+        s = learned_prepare<K>(ctx, pl, static_cast<const K*>(kin), n, st, kin == kout && !(pl.passes & 1));
         if (s != MSORT_OK) return s;
     }
     // Graph replay for the exact partition (the learned one prepares its
@@ -855,7 +856,7 @@ static msort_status host_sort(msort_ctx* ctx, const void* h_kin_v, const uint32_
         cudaEventRecord(hp->in_ev[sl][0], hp->h2d);
         cudaStreamWaitEvent(cs, hp->in_ev[sl][0], 0);
         if (pl.partition_mode == 1 && P > 0) {
-            s = learned_prepare<K>(ctx, pl, S, n, cs);
+            s = learned_prepare<K>(ctx, pl, S, n, cs, !(P & 1));  // sorted in place
             if (s != MSORT_OK) return s;
         }
         s = run_sort<K, PAIRS>(ctx, S, SV, S, SV, n, pl, ctx->scratch, false, cs);
