@@ -435,7 +435,9 @@ msort_status msort_mlp_grad(msort_ctx* ctx, const float* d_x, size_t m, const fl
  * lr) on d_params in place: before each update the loss of the current
  * parameters is compared with the best so far; if it is higher, the best
  * parameters are restored, the rate halves and the Adam moments restart.
- * A final check keeps the best parameters seen.  knot_init != 0 first sets
+ * A final check keeps the best parameters seen.  Each step is one launch of
+ * 8 blocks that add their partial sums in block order, so the result does
+ * not depend on scheduling.  knot_init != 0 first sets
  * d_params to the piecewise-linear interpolant through 32 quantiles of the
  * sorted d_x. */
 msort_status msort_mlp_train(msort_ctx* ctx, const float* d_x, size_t m, float* d_params, int knot_init,
@@ -459,7 +461,9 @@ msort_status msort_learned_set_model(msort_ctx* ctx, const float* h_params, floa
  * it (Merge Path, cited in the paper's Section "Related Research").  mode:
  * 0 the exact binary search of the plain sort, 1 the learned network's
  * guided search (needs a model: a partition_mode 1 sort trained one on ctx,
- * or msort_learned_set_model installed one), 2 the ratio-guess guided
+ * or msort_learned_set_model installed one; while a sort's training is
+ * still running on the side stream, blocks start from the ratio guess), 2
+ * the ratio-guess guided
  * search, 3 the guided kernel's plain binary search.  Every mode returns the
  * same exact co-ranks.  d_splits holds ceil(n / block) uint64 entries;
  * unsigned key types only. */
