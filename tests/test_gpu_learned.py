@@ -106,6 +106,28 @@ def test_training_lowers_loss_and_tracks_fp64(ctx):
     assert l1 <= 1.25 * lr_ + 1e-8, (l1, lr_)
 
 
+def test_training_is_reproducible(ctx):
+    """Each training round adds its blocks' partial sums in block order, so
+    training twice on the same points gives bit-identical parameters, and
+    two learned sorts of the same keys train the same model."""
+    m = 1 << 14
+    x = np.sort(synth.lognormal3_u32(m, 6).astype(np.float64) / 2 ** 32).astype(np.float32)
+    dx = to_dev(x)
+    runs = []
+    for _ in range(2):
+        dp = torch.zeros(mlp.NPARAM, dtype=torch.float32, device="cuda")
+        ms.msort_mlp_train(ctx, dx, dp, steps=32, lr=1e-3, knot_init=True)
+        runs.append(to_host(dp).view(np.uint32))
+    assert np.array_equal(runs[0], runs[1])
+    keys = synth.lognormal3_u32((1 << 22) + 9, 7)
+    models = []
+    for _ in range(2):
+        d = to_dev(keys)
+        ms.msort_sort(ctx, d, options={"partition_mode": 1})
+        models.append(np.asarray(ms.msort_learned_model(ctx)[0], dtype=np.float32).view(np.uint32))
+    assert np.array_equal(models[0], models[1])
+
+
 @pytest.mark.parametrize("mode", [1, 2, 3])
 @pytest.mark.parametrize("dist", ["lognormal3", "uniform", "sorted", "zipf"])
 def test_guided_sorts_are_exact(ctx, mode, dist):
