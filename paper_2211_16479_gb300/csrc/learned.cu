@@ -406,6 +406,7 @@ __global__ void k_partition_guided(const K* __restrict__ src, size_t n, size_t L
                                    const unsigned int* ready, unsigned int epoch, int exact_only,
                                    unsigned long long* probes) {
     __shared__ float p[kNP];
+    __shared__ float fend[2][4];  // F at A[0], A[|A|-1], B[0], B[|B|-1] of the block's first two pairs
     __shared__ int use_model;
     if (threadIdx.x == 0) {
         unsigned int v = epoch;
@@ -416,6 +417,28 @@ __global__ void k_partition_guided(const K* __restrict__ src, size_t n, size_t L
     if (use_model)  // L2 loads: the parameters were written by another stream's kernels
         for (int i = threadIdx.x; i < kNP; i += blockDim.x) p[i] = __ldcg(params + i);
     __syncthreads();
+    // The searches of a block usually fall in one or two merge pairs (the
+    // guided passes' runs span many output blocks): evaluate the network at
+    // those pairs' run ends once, by 8 threads, instead of in every thread.
+    const size_t cfirst = (size_t)blockIdx.x * blockDim.x;
+    const size_t clast = (cfirst + blockDim.x < nblocks ? cfirst + blockDim.x : nblocks) - 1;
+    const size_t pair0 = cfirst * W / (2 * L);
+    const bool shared_ends = use_model && clast * W / (2 * L) - pair0 <= 1;  // block-uniform
+    if (shared_ends) {
+        if (threadIdx.x < 8) {
+            const size_t pp = pair0 + (threadIdx.x >> 2);
+            const int which = threadIdx.x & 3;
+            if (pp * 2 * L < n) {
+                const PassGeom gp = pass_geom(pp * 2 * L, n, L);
+                const K* pa = src + gp.pb;
+                const size_t len = which < 2 ? gp.alen : gp.blen;
+                const K* run = which < 2 ? pa : pa + gp.alen;
+                if (len > 0)
+                    fend[threadIdx.x >> 2][which] = mlp_f(p, key_to_x<K>(run[(which & 1) ? len - 1 : 0]));
+            }
+        }
+        __syncthreads();
+    }
     const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned int live = __ballot_sync(0xffffffffu, c < nblocks);  // lanes that search (blockDim % 32 == 0)
     if (c >= nblocks) return;
@@ -438,8 +461,19 @@ __global__ void k_partition_guided(const K* __restrict__ src, size_t n, size_t L
             // At a probe a the two keys sit near the split, so the model's
             // error largely cancels in F(B[d-1-a]) - F(A[a]).  Every probe
             // also narrows the bracket by its exact comparison.
-            const float fa0 = mlp_f(p, key_to_x<K>(A[0])), fa1 = mlp_f(p, key_to_x<K>(A[alen - 1]));
-            const float fb0 = mlp_f(p, key_to_x<K>(B[0])), fb1 = mlp_f(p, key_to_x<K>(B[blen - 1]));
+            float fa0, fa1, fb0, fb1;
+            if (shared_ends) {
+                const int q = (int)(g.pb / (2 * L) - pair0);
+                fa0 = fend[q][0];
+                fa1 = fend[q][1];
+                fb0 = fend[q][2];
+                fb1 = fend[q][3];
+            } else {
+                fa0 = mlp_f(p, key_to_x<K>(A[0]));
+                fa1 = mlp_f(p, key_to_x<K>(A[alen - 1]));
+                fb0 = mlp_f(p, key_to_x<K>(B[0]));
+                fb1 = mlp_f(p, key_to_x<K>(B[blen - 1]));
+            }
             np += 2;
             const float sA = fmaxf(fa1 - fa0, 1e-12f) / (float)alen;
             const float sB = fmaxf(fb1 - fb0, 1e-12f) / (float)blen;
