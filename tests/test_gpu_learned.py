@@ -84,6 +84,27 @@ def test_gradient_matches_fp64_oracle(ctx, seed):
     assert not bad.any(), list(zip(np.nonzero(bad)[0], g_gpu[bad], g_ref[bad], tol[bad]))
 
 
+@pytest.mark.parametrize("m", [1, 7, 1001, 16383, 65535])
+def test_gradient_uneven_point_counts(ctx, m):
+    """The training rounds split the points among their blocks by
+    floor(b m / B); counts that do not divide evenly (and fewer points than
+    blocks) still give the fp64 gradient."""
+    rng = np.random.default_rng(m)
+    x = np.sort(rng.uniform(0, 1, m)).astype(np.float32)
+    p = rng.normal(size=mlp.NPARAM).astype(np.float32)
+    p[0:mlp.H] = rng.uniform(0.5, 2, mlp.H) * rng.choice([-1, 1], mlp.H)
+    pre = x[:, None].astype(np.float64) * p[None, 0:mlp.H] + p[None, mlp.H:2 * mlp.H]
+    p[mlp.H:2 * mlp.H][(np.abs(pre) < 1e-4).any(0)] += 1e-2
+    dg = torch.empty(mlp.NPARAM, dtype=torch.float32, device="cuda")
+    ms.msort_mlp_grad(ctx, to_dev(x), to_dev(p), dg)
+    g_gpu = to_host(dg).astype(np.float64)
+    t = (np.arange(m) + 0.5) / m
+    g_ref, mag = mlp.grad(p.astype(np.float64), x.astype(np.float64), t)
+    tol = _tolerance(p.astype(np.float64), x, mag)
+    bad = np.abs(g_gpu - g_ref) > tol
+    assert not bad.any(), list(zip(np.nonzero(bad)[0], g_gpu[bad], g_ref[bad], tol[bad]))
+
+
 def test_training_lowers_loss_and_tracks_fp64(ctx):
     rng = np.random.default_rng(4)
     m = 1 << 14
