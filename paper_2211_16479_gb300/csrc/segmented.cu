@@ -12,11 +12,16 @@
 //      (32 x 17 up to 1024 x 33 keys) take segments from the list with an
 //      atomic counter and sort each one entirely in shared memory with the
 //      tile-sort body (network + merge-path rounds).
-//   3. One persistent launch for the segments longer than the largest
-//      on-chip tile: a block sorts the segment's tiles, then runs the
-//      segment's merge passes itself (co-ranks of all its output blocks by
-//      binary search in parallel, then the bulk-TMA merge body per block),
-//      ping-ponging between the keys and the context scratch.
+//   3. Segments of up to four large tiles (one or two merge passes): one
+//      persistent launch sorts every tile of every such segment, then each
+//      merge pass is one launch of co-rank searches (a thread per output
+//      block) and one persistent launch of bulk-TMA merge blocks, all
+//      segments' blocks at once, so the whole GPU runs each phase.
+//   4. One persistent launch for the longer segments: a block sorts the
+//      segment's tiles, then runs the segment's merge passes itself
+//      (co-ranks of all its output blocks by binary search in parallel, then
+//      the bulk-TMA merge body per block), ping-ponging between the keys and
+//      the context scratch.
 #include <cuda_runtime.h>
 
 #include <map>
@@ -32,13 +37,22 @@ namespace msort {
 
 constexpr int kSegMaxBuckets = 6;   // small buckets
 constexpr int kSegLarge = kSegMaxBuckets;  // index of the large-segment list
-constexpr int kSegLists = kSegMaxBuckets + 1;
+constexpr int kSegMid = kSegMaxBuckets + 1;  // index of the medium-segment list (up to kMidSlots tiles)
+constexpr int kSegLists = kSegMaxBuckets + 2;
+// counters[q] = entries of list q; counters[kSegLists + q] = its work-fetch
+// counter; then the fetch counters of the medium path's tile launch and of
+// its merge launches (one per pass)
+constexpr int kSegFetchMidTiles = 2 * kSegLists;
+constexpr int kSegFetchMidMerge = 2 * kSegLists + 1;
+constexpr int kMidSlots = 4;  // tiles, and output blocks per pass, of a medium segment
+constexpr int kMidPasses = 2;
 constexpr unsigned int kStatusBadInput = 2u;
 constexpr int kSegBadFlag = 63;  // counters[63]: this call's bad-input flag
 
 struct SegBuckets {
     int n;                       // number of small buckets in use
     int lim[kSegMaxBuckets];     // bucket b takes lengths in (lim[b-1], lim[b]]
+    int mid;                     // medium bucket: lengths in (lim[n-1], mid] (kMidSlots large tiles); 0 = none
 };
 
 // Device-side classification of segments into bucket work lists.
@@ -55,7 +69,7 @@ __global__ void k_seg_classify(const unsigned long long* __restrict__ off, size_
     }
     const unsigned long long len = e - b;
     if (len <= 1) return;
-    int q = kSegLarge;
+    int q = len <= (unsigned long long)bk.mid ? kSegMid : kSegLarge;
     for (int k = 0; k < bk.n; ++k)
         if (len <= (unsigned long long)bk.lim[k]) {
             q = k;
@@ -65,12 +79,17 @@ __global__ void k_seg_classify(const unsigned long long* __restrict__ off, size_
     lists[(size_t)q * nseg + pos] = (unsigned int)i;
 }
 
-// Next work item of list q for this block (all threads get the same value).
-__device__ __forceinline__ unsigned int seg_next(unsigned int* counters, int q, unsigned int* slot) {
+// Next value of fetch counter `idx` for this block (all threads get the same value).
+__device__ __forceinline__ unsigned int seg_fetch(unsigned int* counters, int idx, unsigned int* slot) {
     __syncthreads();
-    if (threadIdx.x == 0) *slot = atomicAdd(&counters[kSegLists + q], 1u);
+    if (threadIdx.x == 0) *slot = atomicAdd(&counters[idx], 1u);
     __syncthreads();
     return *slot;
+}
+
+// Next work item of list q for this block.
+__device__ __forceinline__ unsigned int seg_next(unsigned int* counters, int q, unsigned int* slot) {
+    return seg_fetch(counters, kSegLists + q, slot);
 }
 
 // Small bucket: every segment fits one block of THREADS x IPT keys.
@@ -205,6 +224,126 @@ k_seg_large(K* keys, uint32_t* vals, K* tkeys, uint32_t* tvals, const unsigned l
     }
 }
 
+// Medium segments: more than one on-chip tile, at most kMidSlots tiles of
+// T = THREADS x IPT keys, so one or two merge passes.  Work item it of a
+// phase is slot it % kMidSlots (tile, or output block of W = T keys) of the
+// segment at position it / kMidSlots of the medium list; slots past the end
+// of a shorter segment are skipped.  A segment's tiles land in the buffer
+// its last pass does not write (keys for two passes, the scratch for one),
+// and each pass ping-pongs to the other, so the last pass writes the keys.
+__device__ __forceinline__ int mid_passes(size_t len, size_t T) { return len > 2 * T ? 2 : 1; }
+
+template <class K, bool PAIRS, int THREADS, int IPT>
+__global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 3 : 2)
+k_seg_mid_tiles(K* keys, uint32_t* vals, K* tkeys, uint32_t* tvals, const unsigned long long* __restrict__ off,
+                size_t nseg, const unsigned int* __restrict__ lists, unsigned int* counters, unsigned int* status,
+                int xf) {
+    constexpr int T = THREADS * IPT;
+    constexpr int kHalfIpt = (IPT + 1) / 2;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ unsigned int slot;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    if (counters[kSegBadFlag]) return;  // malformed offsets: sort nothing
+    uint32_t phase = 0;
+    const unsigned int items = counters[kSegMid] * kMidSlots;
+    for (unsigned int it = seg_fetch(counters, kSegFetchMidTiles, &slot); it < items;
+         it = seg_fetch(counters, kSegFetchMidTiles, &slot)) {
+        const unsigned int s = lists[(size_t)kSegMid * nseg + it / kMidSlots];
+        const size_t j = (size_t)(it % kMidSlots) * T;
+        const size_t base = off[s], len = off[s + 1] - base;
+        if (j >= len) continue;
+        const int valid = (int)(len - j < (size_t)T ? len - j : (size_t)T);
+        const bool odd = mid_passes(len, T) & 1;
+        K* dk = (odd ? tkeys : keys) + base + j;
+        uint32_t* dv = PAIRS ? (odd ? tvals : vals) + base + j : nullptr;
+        // a tile's cost follows its shape, not its fill: a last tile of at
+        // most half the keys takes the shape with half the keys per thread
+        const bool ok = valid <= THREADS * kHalfIpt
+                            ? tile_sort_block<K, PAIRS, THREADS, kHalfIpt, true>(
+                                  keys + base + j, PAIRS ? vals + base + j : nullptr, dk, dv, valid, smem_raw, &bar,
+                                  phase, status, xf, 0)
+                            : tile_sort_block<K, PAIRS, THREADS, IPT, true>(
+                                  keys + base + j, PAIRS ? vals + base + j : nullptr, dk, dv, valid, smem_raw, &bar,
+                                  phase, status, xf, 0);
+        if (!ok) return;
+    }
+}
+
+// Co-rank of every output block start of merge pass `pass` (a thread per item).
+template <class K>
+__global__ void k_seg_mid_part(const K* __restrict__ keys, const K* __restrict__ tkeys,
+                               const unsigned long long* __restrict__ off, size_t nseg,
+                               const unsigned int* __restrict__ lists, const unsigned int* __restrict__ counters,
+                               int pass, size_t T, unsigned long long* __restrict__ splits) {
+    const size_t it = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (counters[kSegBadFlag]) return;
+    if (it >= (size_t)counters[kSegMid] * kMidSlots) return;
+    const unsigned int s = lists[(size_t)kSegMid * nseg + it / kMidSlots];
+    const size_t base = off[s], len = off[s + 1] - base;
+    const int P = mid_passes(len, T);
+    const size_t out0 = (it % kMidSlots) * T;
+    if (pass >= P || out0 >= len) return;
+    const K* src = (((P ^ pass) & 1) ? tkeys : keys) + base;  // the pass's input buffer
+    const PassGeom g = pass_geom(out0, len, T << pass);
+    splits[it] = corank_search(src + g.pb, g.alen, src + g.pb + g.alen, g.blen, out0 - g.pb);
+}
+
+// Merge blocks of pass `pass` over every medium segment still merging.
+template <class K, bool PAIRS, int THREADS, int IPT>
+__global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 3 : 2)
+k_seg_mid_merge(K* keys, uint32_t* vals, K* tkeys, uint32_t* tvals, const unsigned long long* __restrict__ off,
+                size_t nseg, const unsigned int* __restrict__ lists, unsigned int* counters, int pass,
+                const unsigned long long* __restrict__ splits, unsigned int* status, int xf) {
+    constexpr int W = THREADS * IPT;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ unsigned int slot;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    if (counters[kSegBadFlag]) return;
+    uint32_t phase = 0;
+    const unsigned int items = counters[kSegMid] * kMidSlots;
+    for (unsigned int it = seg_fetch(counters, kSegFetchMidMerge + pass, &slot); it < items;
+         it = seg_fetch(counters, kSegFetchMidMerge + pass, &slot)) {
+        const unsigned int s = lists[(size_t)kSegMid * nseg + it / kMidSlots];
+        const size_t base = off[s], len = off[s + 1] - base;
+        const int P = mid_passes(len, W);
+        const size_t out0 = (size_t)(it % kMidSlots) * W;
+        if (pass >= P || out0 >= len) continue;
+        const int cur = (P ^ pass) & 1;
+        K* bk[2] = {keys + base, tkeys + base};
+        uint32_t* bv[2] = {PAIRS ? vals + base : nullptr, PAIRS ? tvals + base : nullptr};
+        const K* src = bk[cur];
+        K* dst = bk[cur ^ 1];
+        const PassGeom g = pass_geom(out0, len, (size_t)W << pass);
+        const size_t d0 = out0 - g.pb;
+        const size_t dend = g.alen + g.blen;
+        const size_t d1 = (d0 + W < dend) ? d0 + W : dend;
+        const size_t a0 = splits[it];
+        const size_t a1 = (d1 == dend) ? g.alen : (size_t)splits[it + 1];  // the next block is in this pair
+        const int nA = (int)(a1 - a0);
+        const int nB = (int)(d1 - d0) - nA;
+        const size_t oA = g.pb + a0, oB = g.pb + g.alen + (d0 - a0);
+        const uint32_t* vA = PAIRS ? bv[cur] + oA : nullptr;
+        const uint32_t* vB = PAIRS ? bv[cur] + oB : nullptr;
+        uint32_t* vD = PAIRS ? bv[cur ^ 1] + out0 : nullptr;
+        const bool ok = (xf && pass + 1 == P)
+                            ? merge_block<K, PAIRS, THREADS, IPT, true>(src + oA, nA, src + oB, nB, vA, vB,
+                                                                        dst + out0, vD, smem_raw, &bar, phase,
+                                                                        status, xf)
+                            : merge_block<K, PAIRS, THREADS, IPT, false>(src + oA, nA, src + oB, nB, vA, vB,
+                                                                         dst + out0, vD, smem_raw, &bar, phase,
+                                                                         status, 0);
+        if (!ok) return;
+    }
+}
+
 // ----------------------------------------------------------------------------
 // Host side
 // ----------------------------------------------------------------------------
@@ -265,8 +404,38 @@ cudaError_t launch_large(K* keys, uint32_t* vals, K* tk, uint32_t* tv, const uns
     return cudaGetLastError();
 }
 
-// Bucket plans per key/value type: small buckets (threads x keys per thread)
-// and the tile of the large-segment kernel.
+// The medium path: the tile launch, then per merge pass the co-rank launch
+// and the merge launch (fixed shapes; work comes from the device-side list).
+template <class K, bool PAIRS, int TH, int IPT>
+cudaError_t launch_mid(K* keys, uint32_t* vals, K* tk, uint32_t* tv, const unsigned long long* off, size_t nseg,
+                       const unsigned int* lists, unsigned int* counters, unsigned long long* splits,
+                       unsigned int* status, cudaStream_t st, int xf) {
+    auto ft = k_seg_mid_tiles<K, PAIRS, TH, IPT>;
+    const size_t st_sm = tile_block_smem<K, PAIRS, TH>(TH * IPT);
+    cudaError_t e = allow_smem(ft, st_sm);
+    if (e != cudaSuccess) return e;
+    ft<<<persistent_blocks(ft, TH, st_sm), TH, st_sm, st>>>(keys, vals, tk, tv, off, nseg, lists, counters, status,
+                                                            xf);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    auto fm = k_seg_mid_merge<K, PAIRS, TH, IPT>;
+    const size_t m_sm = merge_block_smem<K, PAIRS, TH, IPT>();
+    if ((e = allow_smem(fm, m_sm)) != cudaSuccess) return e;
+    const int mblocks = persistent_blocks(fm, TH, m_sm);
+    const size_t items = (size_t)kMidSlots * nseg;
+    for (int pass = 0; pass < kMidPasses; ++pass) {
+        k_seg_mid_part<K><<<(unsigned)((items + 127) / 128), 128, 0, st>>>(keys, tk, off, nseg, lists, counters,
+                                                                           pass, (size_t)(TH * IPT), splits);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        fm<<<mblocks, TH, m_sm, st>>>(keys, vals, tk, tv, off, nseg, lists, counters, pass, splits, status, xf);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+constexpr int kMidLaunches = 1 + 2 * kMidPasses;
+
+// Bucket plans per key/value type: small buckets (threads x keys per thread),
+// the medium bucket (up to kMidSlots large tiles) and the tile of the
+// large-segment kernel.
 template <class K, bool PAIRS>
 struct SegPlan;
 
@@ -282,12 +451,13 @@ struct SegPlan;
 template <>
 struct SegPlan<uint32_t, false> {
     static SegBuckets buckets(const msort_ctx* ctx) {
-        if (ctx && ctx->seg_max_small == 33792) return SegBuckets{5, {544, 2176, 8448, 16896, 33792, 0}};
-        return SegBuckets{4, {544, 2176, 8448, 16896, 0, 0}};
+        const int mid = kMidSlots * ((ctx && ctx->seg_large_tile == 8448) ? 8448 : 16896);
+        if (ctx && ctx->seg_max_small == 33792) return SegBuckets{5, {544, 2176, 8448, 16896, 33792, 0}, mid};
+        return SegBuckets{4, {544, 2176, 8448, 16896, 0, 0}, mid};
     }
     static cudaError_t run(const msort_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t* tk, uint32_t* tv,
                            const unsigned long long* off, size_t nseg, const unsigned int* lists,
-                           unsigned int* counters, unsigned int* status, cudaStream_t st,
+                           unsigned int* counters, unsigned long long* msplits, unsigned int* status, cudaStream_t st,
                            int xf) {
         cudaError_t e;
         MSORT_SMALL_LAUNCHES(uint32_t, false)
@@ -296,23 +466,33 @@ struct SegPlan<uint32_t, false> {
         if (buckets(ctx).n == 5 &&
             (e = launch_small<uint32_t, false, 1024, 33>(keys, vals, off, nseg, lists, counters, 4, status, st, xf)))
             return e;
-        if (ctx && ctx->seg_large_tile == 8448)
+        if (ctx && ctx->seg_large_tile == 8448) {
+            if ((e = launch_mid<uint32_t, false, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, msplits,
+                                                          status, st, xf)))
+                return e;
             return launch_large<uint32_t, false, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, status,
                                                           st, xf);
+        }
+        if ((e = launch_mid<uint32_t, false, 512, 33>(keys, vals, tk, tv, off, nseg, lists, counters, msplits, status,
+                                                      st, xf)))
+            return e;
         return launch_large<uint32_t, false, 512, 33>(keys, vals, tk, tv, off, nseg, lists, counters, status, st, xf);
     }
 };
 
 template <>
 struct SegPlan<uint32_t, true> {
-    static SegBuckets buckets(const msort_ctx*) { return SegBuckets{4, {544, 2176, 8448, 16896, 0, 0}}; }
+    static SegBuckets buckets(const msort_ctx*) { return SegBuckets{4, {544, 2176, 8448, 16896, 0, 0}, kMidSlots * 8448}; }
     static cudaError_t run(const msort_ctx*, uint32_t* keys, uint32_t* vals, uint32_t* tk, uint32_t* tv,
                            const unsigned long long* off,
-                           size_t nseg, const unsigned int* lists, unsigned int* counters, unsigned int* status,
-                           cudaStream_t st, int xf) {
+                           size_t nseg, const unsigned int* lists, unsigned int* counters, unsigned long long* msplits,
+                           unsigned int* status, cudaStream_t st, int xf) {
         cudaError_t e;
         MSORT_SMALL_LAUNCHES(uint32_t, true)
         if ((e = launch_small<uint32_t, true, 512, 33>(keys, vals, off, nseg, lists, counters, 3, status, st, xf)))
+            return e;
+        if ((e = launch_mid<uint32_t, true, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, msplits, status,
+                                                     st, xf)))
             return e;
         return launch_large<uint32_t, true, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, status, st, xf);
     }
@@ -320,14 +500,17 @@ struct SegPlan<uint32_t, true> {
 
 template <>
 struct SegPlan<uint64_t, false> {
-    static SegBuckets buckets(const msort_ctx*) { return SegBuckets{4, {544, 2176, 8448, 16896, 0, 0}}; }
+    static SegBuckets buckets(const msort_ctx*) { return SegBuckets{4, {544, 2176, 8448, 16896, 0, 0}, kMidSlots * 8448}; }
     static cudaError_t run(const msort_ctx*, uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv,
                            const unsigned long long* off,
-                           size_t nseg, const unsigned int* lists, unsigned int* counters, unsigned int* status,
-                           cudaStream_t st, int xf) {
+                           size_t nseg, const unsigned int* lists, unsigned int* counters, unsigned long long* msplits,
+                           unsigned int* status, cudaStream_t st, int xf) {
         cudaError_t e;
         MSORT_SMALL_LAUNCHES(uint64_t, false)
         if ((e = launch_small<uint64_t, false, 512, 33>(keys, vals, off, nseg, lists, counters, 3, status, st, xf)))
+            return e;
+        if ((e = launch_mid<uint64_t, false, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, msplits, status,
+                                                      st, xf)))
             return e;
         return launch_large<uint64_t, false, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, status, st, xf);
     }
@@ -335,19 +518,22 @@ struct SegPlan<uint64_t, false> {
 
 template <>
 struct SegPlan<uint64_t, true> {
-    static SegBuckets buckets(const msort_ctx*) { return SegBuckets{3, {544, 2176, 8448, 0, 0, 0}}; }
+    static SegBuckets buckets(const msort_ctx*) { return SegBuckets{3, {544, 2176, 8448, 0, 0, 0}, kMidSlots * 4352}; }
     static cudaError_t run(const msort_ctx*, uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv,
                            const unsigned long long* off,
-                           size_t nseg, const unsigned int* lists, unsigned int* counters, unsigned int* status,
-                           cudaStream_t st, int xf) {
+                           size_t nseg, const unsigned int* lists, unsigned int* counters, unsigned long long* msplits,
+                           unsigned int* status, cudaStream_t st, int xf) {
         cudaError_t e;
         MSORT_SMALL_LAUNCHES(uint64_t, true)
+        if ((e = launch_mid<uint64_t, true, 256, 17>(keys, vals, tk, tv, off, nseg, lists, counters, msplits, status,
+                                                     st, xf)))
+            return e;
         return launch_large<uint64_t, true, 256, 17>(keys, vals, tk, tv, off, nseg, lists, counters, status, st, xf);
     }
 };
 
 struct SegLayout {
-    size_t keys, vals, lists, counters, end;
+    size_t keys, vals, lists, counters, msplits, end;
 };
 
 template <class K, bool PAIRS>
@@ -357,7 +543,8 @@ SegLayout seg_layout(size_t n, size_t nseg) {
     l.vals = align_up(n * sizeof(K), 256);
     l.lists = l.vals + (PAIRS ? align_up(n * 4, 256) : 0);
     l.counters = l.lists + align_up((size_t)kSegLists * nseg * 4, 256);
-    l.end = l.counters + 256;
+    l.msplits = l.counters + 256;
+    l.end = l.msplits + align_up((size_t)kMidSlots * nseg * sizeof(unsigned long long), 256);
     return l;
 }
 
@@ -370,6 +557,7 @@ msort_status seg_enqueue(msort_ctx* ctx, K* keys, uint32_t* vals, const unsigned
     uint32_t* tv = PAIRS ? reinterpret_cast<uint32_t*>(sp + l.vals) : nullptr;
     unsigned int* lists = reinterpret_cast<unsigned int*>(sp + l.lists);
     unsigned int* counters = reinterpret_cast<unsigned int*>(sp + l.counters);
+    unsigned long long* msplits = reinterpret_cast<unsigned long long*>(sp + l.msplits);
     cudaError_t e = cudaMemsetAsync(counters, 0, 256, st);
     if (e != cudaSuccess) return cuda_fail(e, "clearing segment counters");
     prof_begin(ctx, KK_SEGMENTED, st);
@@ -377,9 +565,10 @@ msort_status seg_enqueue(msort_ctx* ctx, K* keys, uint32_t* vals, const unsigned
                                                                    lists, counters, ctx->d_status);
     e = cudaGetLastError();
     if (e == cudaSuccess)
-        e = SegPlan<K, PAIRS>::run(ctx, keys, vals, tk, tv, off, nseg, lists, counters, ctx->d_status, st, xf);
+        e = SegPlan<K, PAIRS>::run(ctx, keys, vals, tk, tv, off, nseg, lists, counters, msplits, ctx->d_status, st,
+                                   xf);
     prof_end(ctx, KK_SEGMENTED, st);
-    ctx->launches += 1 + SegPlan<K, PAIRS>::buckets(ctx).n + 1;
+    ctx->launches += 1 + SegPlan<K, PAIRS>::buckets(ctx).n + kMidLaunches + 1;
     if (e != cudaSuccess) return cuda_fail(e, "segmented sort launch");
     return MSORT_OK;
 }

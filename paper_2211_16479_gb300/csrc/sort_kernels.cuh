@@ -732,28 +732,38 @@ __device__ __forceinline__ bool merge_block(const K* gA, int nA, const K* gB, in
     __syncthreads();
 
     // Outputs back to shared memory (thread t at [t*IPT, t*IPT + IPT)),
-    // then out with one bulk store per array.
+    // shifted by the destination's element offset within 16 bytes, so that
+    // the outputs from D's first 16-byte boundary on sit at a 16-byte
+    // boundary of shared memory too: the whole 16-byte units go out with one
+    // bulk store per array, the head before the boundary and the tail by
+    // plain stores.  (An aligned destination has no shift and no head.)
     const int mine = total - t * IPT;
+    const int ks0 = (int)((reinterpret_cast<uintptr_t>(D) & 15) / KS);
+    const int vs0 = PAIRS ? (int)((reinterpret_cast<uintptr_t>(VD) & 15) / 4) : 0;
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
         if (i < mine) {
-            sk[t * IPT + i] = XF ? xf_inverse(ok[i], xf_out) : ok[i];
-            if (PAIRS) sv[t * IPT + i] = ov[i];
+            sk[ks0 + t * IPT + i] = XF ? xf_inverse(ok[i], xf_out) : ok[i];
+            if (PAIRS) sv[vs0 + t * IPT + i] = ov[i];
         }
     }
-    const bool dst_ok = aligned16(D) && (!PAIRS || aligned16(VD));
-    const int nbk = dst_ok ? (total * KS / 16) * 16 / KS : 0;      // keys by bulk store
-    const int nbv = dst_ok && PAIRS ? (total * 4 / 16) * 16 / 4 : 0;  // values by bulk store
+    const int khead = ks0 ? 16 / KS - ks0 : 0;                                   // keys before the boundary
+    const int kbody = total > khead ? ((total - khead) * KS / 16) * 16 / KS : 0;  // keys by bulk store
+    const int vhead = vs0 ? 4 - vs0 : 0;
+    const int vbody = PAIRS && total > vhead ? ((total - vhead) * 4 / 16) * 4 : 0;
     fence_proxy_async_smem();
     __syncthreads();
     if (t == 0) {
-        if (nbk) tma_store_1d(D, sk, (uint32_t)(nbk * KS));
-        if (PAIRS && nbv) tma_store_1d(VD, sv, (uint32_t)(nbv * 4));
+        if (kbody) tma_store_1d(D + khead, sk + ks0 + khead, (uint32_t)(kbody * KS));
+        if (PAIRS && vbody) tma_store_1d(VD + vhead, sv + vs0 + vhead, (uint32_t)(vbody * 4));
         tma_store_commit();
     }
-    for (int i = nbk + t; i < total; i += THREADS) D[i] = sk[i];
-    if (PAIRS)
-        for (int i = nbv + t; i < total; i += THREADS) VD[i] = sv[i];
+    if (t < khead && t < total) D[t] = sk[ks0 + t];
+    for (int i = khead + kbody + t; i < total; i += THREADS) D[i] = sk[ks0 + i];
+    if (PAIRS) {
+        if (t < vhead && t < total) VD[t] = sv[vs0 + t];
+        for (int i = vhead + vbody + t; i < total; i += THREADS) VD[i] = sv[vs0 + i];
+    }
     if (t == 0) tma_store_wait_read();
     return true;
 }

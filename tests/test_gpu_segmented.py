@@ -17,7 +17,13 @@ ms = pytest.importorskip("paper_2211_16479_gb300")
 pytestmark = pytest.mark.gpu
 
 BOUNDARY_LENS = [0, 1, 2, 3, 17, 33, 543, 544, 545, 2175, 2176, 2177, 4352, 8447, 8448, 8449, 16895, 16896, 16897,
-                 33791, 33792, 33793, 65536, 100003]
+                 33791, 33792, 33793, 65536, 100003,
+                 # medium segments (two to four large tiles of T keys; a last tile of at most half a tile takes
+                 # the half shape): T = 16896 for 32-bit keys, 8448 for 32-bit pairs and 64-bit keys, 4352
+                 # for 64-bit pairs; around T + T/2, 2T, 3T, 3T + T/2 and 4T
+                 25600, 25601, 50688, 50689, 59392, 59393, 67584, 67585,
+                 21248, 21249, 25344, 25345, 29696, 29697,
+                 11008, 11009, 13056, 13057, 15360, 15361, 17408, 17409]
 
 
 @pytest.fixture(scope="module")
