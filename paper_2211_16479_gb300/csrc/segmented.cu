@@ -444,6 +444,18 @@ struct SegPlan;
     if ((e = launch_small<K, PAIRS, 128, 17>(keys, vals, off, nseg, lists, counters, 1, status, st, xf))) return e; \
     if ((e = launch_small<K, PAIRS, 256, 33>(keys, vals, off, nseg, lists, counters, 2, status, st, xf))) return e;
 
+// Small buckets a factor of two apart (544 ... 8448 keys; the first five
+// launches, buckets 0-4).  A block's cost follows its shape, not its fill,
+// and segment lengths spread evenly on a log scale fill a bucket twice as
+// wide as the one below it to about 72% on average, against 54% for four
+// times as wide: on 50,000 log-uniform segments 3.52 against 3.57 ms.
+#define MSORT_SMALL2X_LAUNCHES(K, PAIRS)                                                                        \
+    if ((e = launch_small<K, PAIRS, 32, 17>(keys, vals, off, nseg, lists, counters, 0, status, st, xf))) return e;  \
+    if ((e = launch_small<K, PAIRS, 64, 17>(keys, vals, off, nseg, lists, counters, 1, status, st, xf))) return e;  \
+    if ((e = launch_small<K, PAIRS, 128, 17>(keys, vals, off, nseg, lists, counters, 2, status, st, xf))) return e; \
+    if ((e = launch_small<K, PAIRS, 256, 17>(keys, vals, off, nseg, lists, counters, 3, status, st, xf))) return e; \
+    if ((e = launch_small<K, PAIRS, 256, 33>(keys, vals, off, nseg, lists, counters, 4, status, st, xf))) return e;
+
 // 32-bit keys only: the largest on-chip bucket (16896 or 33792 keys) and the
 // large-segment tile (8448 or 16896) are tunable (msort_tune).  Default
 // 16896 / 16896: on the 50,000-segment workload 1.5% faster than a 33792-key
@@ -453,19 +465,27 @@ struct SegPlan<uint32_t, false> {
     static SegBuckets buckets(const msort_ctx* ctx) {
         const int mid = kMidSlots * ((ctx && ctx->seg_large_tile == 8448) ? 8448 : 16896);
         if (ctx && ctx->seg_max_small == 33792) return SegBuckets{5, {544, 2176, 8448, 16896, 33792, 0}, mid};
-        return SegBuckets{4, {544, 2176, 8448, 16896, 0, 0}, mid};
+        return SegBuckets{6, {544, 1088, 2176, 4352, 8448, 16896}, mid};
     }
     static cudaError_t run(const msort_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t* tk, uint32_t* tv,
                            const unsigned long long* off, size_t nseg, const unsigned int* lists,
                            unsigned int* counters, unsigned long long* msplits, unsigned int* status, cudaStream_t st,
                            int xf) {
         cudaError_t e;
-        MSORT_SMALL_LAUNCHES(uint32_t, false)
-        if ((e = launch_small<uint32_t, false, 512, 33>(keys, vals, off, nseg, lists, counters, 3, status, st, xf)))
-            return e;
-        if (buckets(ctx).n == 5 &&
-            (e = launch_small<uint32_t, false, 1024, 33>(keys, vals, off, nseg, lists, counters, 4, status, st, xf)))
-            return e;
+        if (buckets(ctx).n == 6) {
+            MSORT_SMALL2X_LAUNCHES(uint32_t, false)
+            if ((e = launch_small<uint32_t, false, 512, 33>(keys, vals, off, nseg, lists, counters, 5, status, st,
+                                                            xf)))
+                return e;
+        } else {  // the tuned plan with on-chip segments up to 33792 keys
+            MSORT_SMALL_LAUNCHES(uint32_t, false)
+            if ((e = launch_small<uint32_t, false, 512, 33>(keys, vals, off, nseg, lists, counters, 3, status, st,
+                                                            xf)))
+                return e;
+            if ((e = launch_small<uint32_t, false, 1024, 33>(keys, vals, off, nseg, lists, counters, 4, status, st,
+                                                             xf)))
+                return e;
+        }
         if (ctx && ctx->seg_large_tile == 8448) {
             if ((e = launch_mid<uint32_t, false, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, msplits,
                                                           status, st, xf)))
@@ -482,14 +502,16 @@ struct SegPlan<uint32_t, false> {
 
 template <>
 struct SegPlan<uint32_t, true> {
-    static SegBuckets buckets(const msort_ctx*) { return SegBuckets{4, {544, 2176, 8448, 16896, 0, 0}, kMidSlots * 8448}; }
+    static SegBuckets buckets(const msort_ctx*) {
+        return SegBuckets{6, {544, 1088, 2176, 4352, 8448, 16896}, kMidSlots * 8448};
+    }
     static cudaError_t run(const msort_ctx*, uint32_t* keys, uint32_t* vals, uint32_t* tk, uint32_t* tv,
                            const unsigned long long* off,
                            size_t nseg, const unsigned int* lists, unsigned int* counters, unsigned long long* msplits,
                            unsigned int* status, cudaStream_t st, int xf) {
         cudaError_t e;
-        MSORT_SMALL_LAUNCHES(uint32_t, true)
-        if ((e = launch_small<uint32_t, true, 512, 33>(keys, vals, off, nseg, lists, counters, 3, status, st, xf)))
+        MSORT_SMALL2X_LAUNCHES(uint32_t, true)
+        if ((e = launch_small<uint32_t, true, 512, 33>(keys, vals, off, nseg, lists, counters, 5, status, st, xf)))
             return e;
         if ((e = launch_mid<uint32_t, true, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, msplits, status,
                                                      st, xf)))
@@ -500,14 +522,16 @@ struct SegPlan<uint32_t, true> {
 
 template <>
 struct SegPlan<uint64_t, false> {
-    static SegBuckets buckets(const msort_ctx*) { return SegBuckets{4, {544, 2176, 8448, 16896, 0, 0}, kMidSlots * 8448}; }
+    static SegBuckets buckets(const msort_ctx*) {
+        return SegBuckets{6, {544, 1088, 2176, 4352, 8448, 16896}, kMidSlots * 8448};
+    }
     static cudaError_t run(const msort_ctx*, uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv,
                            const unsigned long long* off,
                            size_t nseg, const unsigned int* lists, unsigned int* counters, unsigned long long* msplits,
                            unsigned int* status, cudaStream_t st, int xf) {
         cudaError_t e;
-        MSORT_SMALL_LAUNCHES(uint64_t, false)
-        if ((e = launch_small<uint64_t, false, 512, 33>(keys, vals, off, nseg, lists, counters, 3, status, st, xf)))
+        MSORT_SMALL2X_LAUNCHES(uint64_t, false)
+        if ((e = launch_small<uint64_t, false, 512, 33>(keys, vals, off, nseg, lists, counters, 5, status, st, xf)))
             return e;
         if ((e = launch_mid<uint64_t, false, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, msplits, status,
                                                       st, xf)))
@@ -518,13 +542,15 @@ struct SegPlan<uint64_t, false> {
 
 template <>
 struct SegPlan<uint64_t, true> {
-    static SegBuckets buckets(const msort_ctx*) { return SegBuckets{3, {544, 2176, 8448, 0, 0, 0}, kMidSlots * 4352}; }
+    static SegBuckets buckets(const msort_ctx*) {
+        return SegBuckets{5, {544, 1088, 2176, 4352, 8448, 0}, kMidSlots * 4352};
+    }
     static cudaError_t run(const msort_ctx*, uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv,
                            const unsigned long long* off,
                            size_t nseg, const unsigned int* lists, unsigned int* counters, unsigned long long* msplits,
                            unsigned int* status, cudaStream_t st, int xf) {
         cudaError_t e;
-        MSORT_SMALL_LAUNCHES(uint64_t, true)
+        MSORT_SMALL2X_LAUNCHES(uint64_t, true)
         if ((e = launch_mid<uint64_t, true, 256, 17>(keys, vals, tk, tv, off, nseg, lists, counters, msplits, status,
                                                      st, xf)))
             return e;

@@ -16,7 +16,8 @@ ms = pytest.importorskip("paper_2211_16479_gb300")
 
 pytestmark = pytest.mark.gpu
 
-BOUNDARY_LENS = [0, 1, 2, 3, 17, 33, 543, 544, 545, 2175, 2176, 2177, 4352, 8447, 8448, 8449, 16895, 16896, 16897,
+BOUNDARY_LENS = [0, 1, 2, 3, 17, 33, 543, 544, 545, 1087, 1088, 1089, 2175, 2176, 2177, 4351, 4352, 4353, 8447, 8448,
+                 8449, 16895, 16896, 16897,
                  33791, 33792, 33793, 65536, 100003,
                  # medium segments (two to four large tiles of T keys; a last tile of at most half a tile takes
                  # the half shape): T = 16896 for 32-bit keys, 8448 for 32-bit pairs and 64-bit keys, 4352
