@@ -46,6 +46,43 @@ def test_merge_two_runs(ctx, kt, pairs, na, nb):
         assert np.array_equal(to_host(vout), ev)
 
 
+@pytest.mark.parametrize("kt", ["u32", "u64"])
+@pytest.mark.parametrize("pairs", [False, True])
+@pytest.mark.parametrize("shift", [(1, 2), (3, 1), (2, 3)])
+@pytest.mark.parametrize("na,nb", [(1, 2), (37, 5), (4351, 4353), (100003, 77777)])
+def test_merge_unaligned_outputs(ctx, kt, pairs, shift, na, nb):
+    """Outputs (and inputs) that start 1 to 3 elements into their buffers:
+    each merge block stages its outputs shifted by the destination's offset
+    within 16 bytes and bulk-stores the aligned middle; the head and tail
+    go by plain stores."""
+    ks, vs = shift
+    if kt == "u32":
+        a = np.sort(synth.uniform_u32(na, 3) % np.uint32(700))
+        b = np.sort(synth.uniform_u32(nb, 4) % np.uint32(700))
+    else:
+        a = np.sort(synth.dup_u64(na, 3, distinct=400)[0])
+        b = np.sort(synth.dup_u64(nb, 4, distinct=400)[0])
+    va = np.arange(na, dtype=np.uint32) if pairs else None
+    vb = np.arange(na, na + nb, dtype=np.uint32) if pairs else None
+    da = to_dev(np.concatenate([a[:1].repeat(ks), a]))[ks:]
+    db = to_dev(np.concatenate([b[:1].repeat(vs), b]))[vs:]
+    big = torch.zeros(na + nb + 8, dtype=da.dtype, device="cuda")
+    out = big[ks:ks + na + nb]
+    dva = to_dev(np.concatenate([np.zeros(vs, np.uint32), va]))[vs:] if pairs else None
+    dvb = to_dev(np.concatenate([np.zeros(ks, np.uint32), vb]))[ks:] if pairs else None
+    vbig = torch.zeros(na + nb + 8, dtype=torch.uint32, device="cuda") if pairs else None
+    vout = vbig[vs:vs + na + nb] if pairs else None
+    ms.msort_merge(ctx, da, db, out, va=dva, vb=dvb, vout=vout)
+    ek, ev = oracle.merge(a, b, va, vb)
+    got = to_host(big)
+    assert np.array_equal(got[ks:ks + na + nb], ek)
+    assert not got[:ks].any() and not got[ks + na + nb:].any()  # nothing written outside the view
+    if pairs:
+        gv = to_host(vbig)
+        assert np.array_equal(gv[vs:vs + na + nb], ev)
+        assert not gv[:vs].any() and not gv[vs + na + nb:].any()
+
+
 def _run_lengths(seed, count, hi):
     rng = np.random.default_rng(seed)
     lens = rng.integers(0, hi, size=count)
