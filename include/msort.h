@@ -266,12 +266,15 @@ size_t msort_external_plan(const void* h_runs, size_t n, msort_key_type kt, size
  * Out of core: when the context has a budget and the three staging slots
  * plus the scratch for n elements would exceed it, the array is sorted in
  * budget-sized chunks C whose sorted runs go to a pinned host buffer owned by
- * the context (n keys and values, kept for later calls).  With B = C/2,
- * every B/(16R)-th element of the R runs is sampled, and every 15R-th sample
- * in (key, position) order becomes a splitter (B/(2R) and R when 16R > B),
- * so each block between consecutive splitters holds at most B elements.  Each block's slices of
- * all runs are copied to a staging slot, merged there (msort_merge_runs'
- * rounds; ties in run order) and copied to their place in the output,
+ * the context (n keys and values, kept for later calls).  With a block
+ * bound B of up to C (as many elements as the context scratch holds beside
+ * the merge's split table, at least C/2), every B/(16R)-th element of the R
+ * runs is sampled, and every 15R-th sample in (key, position) order becomes
+ * a splitter (B/(2R) and R when 16R > B), so each block between consecutive
+ * splitters holds at most B elements.  Each block's slices of all runs are
+ * copied to a staging slot, merged there with the scratch as the second
+ * buffer (msort_merge_runs' rounds; ties in run order) and copied to their
+ * place in the output,
  * consecutive blocks overlapping on the context's streams.  MSORT_ERR_OOM if
  * the budget does not fit a chunk of four 16896-key tiles.
  * This path is taken by msort_sort_host_async too, and then returns with the

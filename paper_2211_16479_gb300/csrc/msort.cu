@@ -1105,10 +1105,18 @@ static msort_status host_sort_external(msort_ctx* ctx, const K* h_kin, const uin
     K* tk = static_cast<K*>(hp->runs);
     uint32_t* tv = PAIRS ? reinterpret_cast<uint32_t*>(tk + n) : nullptr;
     const size_t R = (n + chunk - 1) / chunk;
-    // A block is at most half a chunk: its merge rounds ping-pong between the
-    // two halves of a staging slot.
-    const size_t B = (chunk / 2) & ~size_t(63);
-    if (2 * R > B) return fail(MSORT_ERR_OOM, "the context budget is too small for this many out-of-core runs");
+    // A block fills a staging slot (up to a chunk); its merge rounds
+    // ping-pong between the slot and the context scratch, which phase 1
+    // sized for the in-core sort of a chunk and which holds, after the
+    // block's keys and values, the rounds' split table.  The largest block
+    // whose share fits the scratch as it stands: larger blocks mean larger
+    // slices, which the host link moves faster.
+    auto scratch_for = [](size_t b) {
+        return align_up(b * sizeof(K), 256) + (PAIRS ? align_up(b * 4, 256) : 0) +
+               align_up(merge_runs_splits<K, PAIRS>(b) * sizeof(unsigned long long), 256);
+    };
+    if (2 * R > ((chunk / 2) & ~size_t(63)))
+        return fail(MSORT_ERR_OOM, "the context budget is too small for this many out-of-core runs");
 
     // 1. sorted runs, one budget-sized chunk at a time (consecutive chunks
     //    overlap on the context's streams).  The runs keep their keys
@@ -1124,6 +1132,11 @@ static msort_status host_sort_external(msort_ctx* ctx, const K* h_kin, const uin
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
 
+    // the block size, now that phase 1 has sized the scratch
+    size_t B = chunk & ~size_t(63);
+    while (B > 64 && scratch_for(B) > ctx->scratch_bytes) B = (B - B / 16) & ~size_t(63);
+    if (2 * R > B) return fail(MSORT_ERR_OOM, "the context budget is too small for this many out-of-core runs");
+
     // 2. splitters from regular samples of the runs
     size_t nb = 0;
     const std::vector<size_t> cut = external_cuts<K>(tk, n, chunk, B, &nb);
@@ -1134,8 +1147,20 @@ static msort_status host_sort_external(msort_ctx* ctx, const K* h_kin, const uin
     const size_t kb = align_up(B * sizeof(K), 256), vb = PAIRS ? align_up(B * 4, 256) : 0;
     int slots[kHostSlots], ns = 0;
     for (int i = 0; i < kHostSlots; ++i)
-        if (hp->slot_bytes[i] >= 2 * (kb + vb)) slots[ns++] = i;
+        if (hp->slot_bytes[i] >= kb + vb) slots[ns++] = i;
     if (!ns) return fail(MSORT_ERR_CUDA, "no staging slot holds an out-of-core block");
+    K* pk = nullptr;  // the rounds' second buffer, in the scratch
+    uint32_t* pv = nullptr;
+    unsigned long long* splits = nullptr;
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        msort_status s = ensure_scratch(ctx, scratch_for(B), hp->cs);
+        if (s != MSORT_OK) return s;
+        unsigned char* sp = static_cast<unsigned char*>(ctx->scratch);
+        pk = reinterpret_cast<K*>(sp);
+        pv = PAIRS ? reinterpret_cast<uint32_t*>(sp + kb) : nullptr;
+        splits = reinterpret_cast<unsigned long long*>(sp + kb + vb);
+    }
     size_t out = 0, bi = 0;
     int last = -1;
     for (size_t b = 0; b < nb; ++b) {
@@ -1145,9 +1170,8 @@ static msort_status host_sort_external(msort_ctx* ctx, const K* h_kin, const uin
         if (len > B) return fail(MSORT_ERR_CUDA, "out-of-core block larger than its bound");
         const int sl = slots[bi++ % ns];
         unsigned char* base = static_cast<unsigned char*>(hp->slot[sl]);
-        K* dk[2] = {reinterpret_cast<K*>(base), reinterpret_cast<K*>(base + kb + vb)};
-        uint32_t* dv[2] = {PAIRS ? reinterpret_cast<uint32_t*>(base + kb) : nullptr,
-                           PAIRS ? reinterpret_cast<uint32_t*>(base + 2 * kb + vb) : nullptr};
+        K* dk[2] = {reinterpret_cast<K*>(base), pk};
+        uint32_t* dv[2] = {PAIRS ? reinterpret_cast<uint32_t*>(base + kb) : nullptr, pv};
         if (hp->used[sl]) cudaStreamWaitEvent(hp->h2d, hp->done[sl], 0);  // its last block has left
         std::vector<size_t> ro(1, 0);  // boundaries of the block's non-empty slices
         for (size_t r = 0; r < R; ++r) {
@@ -1164,12 +1188,10 @@ static msort_status host_sort_external(msort_ctx* ctx, const K* h_kin, const uin
         cudaStreamWaitEvent(hp->cs, hp->in_ev[sl][0], 0);
         // merge-tree rounds over the slices (at least one, which undoes the
         // key transform)
-        int fin = 0;  // half of the slot that holds the block's result
+        int fin = 0;  // buffer that holds the block's result: 0 the slot, 1 the scratch
         {
             std::lock_guard<std::mutex> g(ctx->mu);
-            msort_status s = ensure_scratch(ctx, merge_runs_splits<K, PAIRS>(B) * sizeof(unsigned long long), hp->cs);
-            if (s != MSORT_OK) return s;
-            unsigned long long* splits = static_cast<unsigned long long*>(ctx->scratch);
+            msort_status s;
             do {
                 const bool lastr = ro.size() <= 3;
                 s = merge_runs_round<K, PAIRS>(ctx, dk[fin], dk[fin ^ 1], dv[fin], dv[fin ^ 1], ro, splits,
@@ -1177,7 +1199,13 @@ static msort_status host_sort_external(msort_ctx* ctx, const K* h_kin, const uin
                 if (s != MSORT_OK) return s;
                 fin ^= 1;
             } while (ro.size() > 2);
-            scratch_release(ctx, hp->cs);
+            if (fin) {  // back into the slot: the next block's rounds reuse the scratch while this one is copied out
+                e = cudaMemcpyAsync(dk[0], dk[1], len * sizeof(K), cudaMemcpyDeviceToDevice, hp->cs);
+                if (e == cudaSuccess && PAIRS)
+                    e = cudaMemcpyAsync(dv[0], dv[1], len * 4, cudaMemcpyDeviceToDevice, hp->cs);
+                if (e != cudaSuccess) return cuda_fail(e, "copy of a merged block into its slot");
+                fin = 0;
+            }
         }
         cudaEventRecord(hp->out_ev[sl][0], hp->cs);
         cudaStreamWaitEvent(hp->d2h, hp->out_ev[sl][0], 0);
@@ -1189,6 +1217,10 @@ static msort_status host_sort_external(msort_ctx* ctx, const K* h_kin, const uin
         hp->used[sl] = true;
         last = sl;
         out += len;
+    }
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        scratch_release(ctx, hp->cs);
     }
     if (last >= 0) cudaStreamWaitEvent(st, hp->done[last], 0);
     e = cudaStreamSynchronize(st);  // the caller's host output is complete on return
