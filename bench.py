@@ -33,7 +33,10 @@ Printed as one JSON line on rank 0.  Also reported:
                 ablation), the batched segmented sort (50,000 arrays) and the
                 continuous-batching server (2,000 requests; p50/p99);
   small_config  the 2^20-key configuration (L2-resident): the single
-                cooperative launch against the multi-launch plan.
+                cooperative launch against the multi-launch plan;
+  pairs_config  the key-value configuration: a stable sort of 2^27 (uint64
+                key, uint32 original index) pairs with heavy duplicates, its
+                stability checked on the device.
 
 --impl reference times the CPU oracle itself on the same metric (there is no
 GPU reference implementation of this method).
@@ -420,12 +423,13 @@ def run_ours(args):
                "context": cpu_context_rates(sample)}
 
     # the chosen forms against the plain sort (rank 0, after the collectives)
-    chosen = small = None
+    chosen = small = pairs = None
     if rank == 0 and not args.no_chosen:
         if not args.no_e2e:
             del h_in, h_out, h_outs
         chosen = chosen_vs_plain(args, h, dev, stream)
         small = form_small(h, dev, stream, 500)
+        pairs = form_pairs(h, dev, stream, 5)
 
     if rank == 0:
         line = {
@@ -462,6 +466,7 @@ def run_ours(args):
             "clocks": clocks,
             "chosen_vs_plain": chosen,
             "small_config": small,
+            "pairs_config": pairs,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -635,6 +640,52 @@ def run_external(args):
                       note="two host round trips: sorted runs, then the blockwise merge")
     print(json.dumps(line), flush=True)
     ctx.close()
+
+
+def form_pairs(h, dev, stream, reps):
+    """The key-value configuration: a stable sort of 2^27 (uint64 key,
+    uint32 value) pairs, keys drawn from 2^20 distinct values (heavy
+    duplicates), values = original index, so the output is the stable sort
+    exactly when the keys ascend and equal keys keep increasing values; that
+    is checked on the device.  reps timed repetitions (CUDA events each),
+    then one profiled sort for the kernel split."""
+    import torch
+
+    import paper_2211_16479_gb300 as ms
+    from synth import torch_gen
+    n = 1 << 27
+    keys, vals = torch_gen.dup_u64(n, 1, device=dev)
+    ok, ov = torch.empty_like(keys), torch.empty_like(vals)
+    step = lambda: ms.msort_sort_copy(h, keys, ok, vals, ov, stream=stream)
+    for _ in range(3):
+        step()
+    ms.msort_ctx_sync(h, stream)
+    k64 = ok.view(torch.int64) ^ torch.iinfo(torch.int64).min  # unsigned order as signed
+    v64 = ov.to(torch.int64)
+    same = k64[1:] == k64[:-1]
+    stable = bool((k64[1:] >= k64[:-1]).all()) and bool((v64[1:][same] > v64[:-1][same]).all())
+    del k64, v64, same
+    t = [_events_ms(step, 1, stream) for _ in range(reps)]
+    ms.msort_ctx_set_profiling(h, True)
+    step()
+    kern = {name: ms.msort_ctx_kernel_times(h, k)[1] for name, k in
+            (("tile_sort", ms.MSORT_KERNEL_TILE), ("partition", ms.MSORT_KERNEL_PARTITION),
+             ("merge", ms.MSORT_KERNEL_MERGE))}
+    ms.msort_ctx_set_profiling(h, False)
+    T, W, P = ms.msort_plan_info(n, ms.MSORT_U64, True)
+    alg = 2 * n * 12 * (1 + P)
+    med = statistics.median(t)
+    peak, kind = _peaks()
+    del keys, vals, ok, ov
+    torch.cuda.empty_cache()
+    return {"workload": "2^27 (uint64 key, uint32 original index) pairs, keys from 2^20 distinct values, "
+                        "stable out-of-place sort",
+            "n": n, "tile": T, "merge_block_outputs": W, "merge_passes": P, "repetitions": reps,
+            "ms": _spread(t), "gpairs_per_s": n / med / 1e6, "stable_and_sorted": stable,
+            "kernel_ms_per_sort": kern,
+            "merge_pass_gbs": 2 * n * 12 * P / (kern["merge"] * 1e-3) / 1e9,
+            "roofline": {"bound": "hbm", "algorithmic_bytes": alg,
+                         "frac_of_peak": alg / (med * 1e-3) / 1e9 / peak, "peak": peak, "peak_kind": kind}}
 
 
 def run_pairs(args):
