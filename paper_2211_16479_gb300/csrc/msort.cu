@@ -769,7 +769,6 @@ static msort_status host_sort(msort_ctx* ctx, const void* h_kin_v, const uint32_
     const K* h_kin = static_cast<const K*>(h_kin_v);
     K* h_kout = static_cast<K*>(h_kout_v);
     msort_options tuned_opt{};
-    const msort_options* caller = opt;
     const bool single = single_wanted(n, opt);  // tuned shapes do not apply to the single launch
     if (!single && (!opt || !opt->tile)) {
         const int tile = tuned_tile_for(ctx, (int)sizeof(K), PAIRS, n);

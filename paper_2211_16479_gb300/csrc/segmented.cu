@@ -233,13 +233,23 @@ k_seg_large(K* keys, uint32_t* vals, K* tkeys, uint32_t* tvals, const unsigned l
 // and each pass ping-pongs to the other, so the last pass writes the keys.
 __device__ __forceinline__ int mid_passes(size_t len, size_t T) { return len > 2 * T ? 2 : 1; }
 
-template <class K, bool PAIRS, int THREADS, int IPT>
+// Odd keys per thread (conflict-free strided shared-memory access) for a
+// shape holding about num/4 of a large tile.
+__host__ __device__ constexpr int odd_ipt(int ipt, int num) {
+    return (num * ipt + 3) / 4 + ((num * ipt + 3) / 4 % 2 == 0 ? 1 : 0);
+}
+
+// XF: whether the keys take a transform (signed or floating-point keys);
+// the instance without one keeps the transform's registers out of the
+// tile and merge bodies, which at 40 registers would otherwise spill.
+template <class K, bool PAIRS, int THREADS, int IPT, bool XF>
 __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 3 : 2)
 k_seg_mid_tiles(K* keys, uint32_t* vals, K* tkeys, uint32_t* tvals, const unsigned long long* __restrict__ off,
                 size_t nseg, const unsigned int* __restrict__ lists, unsigned int* counters, unsigned int* status,
                 int xf) {
     constexpr int T = THREADS * IPT;
-    constexpr int kHalfIpt = (IPT + 1) / 2;
+    constexpr int kQ1 = odd_ipt(IPT, 1), kQ2 = odd_ipt(IPT, 2), kQ3 = odd_ipt(IPT, 3);
+    static_assert(kQ1 < kQ2 && kQ2 < kQ3 && kQ3 < IPT, "four distinct tile shapes");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ unsigned int slot;
@@ -260,15 +270,20 @@ k_seg_mid_tiles(K* keys, uint32_t* vals, K* tkeys, uint32_t* tvals, const unsign
         const bool odd = mid_passes(len, T) & 1;
         K* dk = (odd ? tkeys : keys) + base + j;
         uint32_t* dv = PAIRS ? (odd ? tvals : vals) + base + j : nullptr;
-        // a tile's cost follows its shape, not its fill: a last tile of at
-        // most half the keys takes the shape with half the keys per thread
-        const bool ok = valid <= THREADS * kHalfIpt
-                            ? tile_sort_block<K, PAIRS, THREADS, kHalfIpt, true>(
-                                  keys + base + j, PAIRS ? vals + base + j : nullptr, dk, dv, valid, smem_raw, &bar,
-                                  phase, status, xf, 0)
-                            : tile_sort_block<K, PAIRS, THREADS, IPT, true>(
-                                  keys + base + j, PAIRS ? vals + base + j : nullptr, dk, dv, valid, smem_raw, &bar,
-                                  phase, status, xf, 0);
+        // a tile's cost follows its shape, not its fill: a segment's last
+        // tile takes the smallest of four shapes (about a quarter, half,
+        // three quarters or all of the keys per thread) that holds it
+        const K* sk = keys + base + j;
+        const uint32_t* sv = PAIRS ? vals + base + j : nullptr;
+        bool ok;
+        if (valid <= THREADS * kQ1)
+            ok = tile_sort_block<K, PAIRS, THREADS, kQ1, XF>(sk, sv, dk, dv, valid, smem_raw, &bar, phase, status, xf, 0);
+        else if (valid <= THREADS * kQ2)
+            ok = tile_sort_block<K, PAIRS, THREADS, kQ2, XF>(sk, sv, dk, dv, valid, smem_raw, &bar, phase, status, xf, 0);
+        else if (valid <= THREADS * kQ3)
+            ok = tile_sort_block<K, PAIRS, THREADS, kQ3, XF>(sk, sv, dk, dv, valid, smem_raw, &bar, phase, status, xf, 0);
+        else
+            ok = tile_sort_block<K, PAIRS, THREADS, IPT, XF>(sk, sv, dk, dv, valid, smem_raw, &bar, phase, status, xf, 0);
         if (!ok) return;
     }
 }
@@ -293,7 +308,7 @@ __global__ void k_seg_mid_part(const K* __restrict__ keys, const K* __restrict__
 }
 
 // Merge blocks of pass `pass` over every medium segment still merging.
-template <class K, bool PAIRS, int THREADS, int IPT>
+template <class K, bool PAIRS, int THREADS, int IPT, bool XF>
 __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 3 : 2)
 k_seg_mid_merge(K* keys, uint32_t* vals, K* tkeys, uint32_t* tvals, const unsigned long long* __restrict__ off,
                 size_t nseg, const unsigned int* __restrict__ lists, unsigned int* counters, int pass,
@@ -333,7 +348,7 @@ k_seg_mid_merge(K* keys, uint32_t* vals, K* tkeys, uint32_t* tvals, const unsign
         const uint32_t* vA = PAIRS ? bv[cur] + oA : nullptr;
         const uint32_t* vB = PAIRS ? bv[cur] + oB : nullptr;
         uint32_t* vD = PAIRS ? bv[cur ^ 1] + out0 : nullptr;
-        const bool ok = (xf && pass + 1 == P)
+        const bool ok = (XF && pass + 1 == P)
                             ? merge_block<K, PAIRS, THREADS, IPT, true>(src + oA, nA, src + oB, nB, vA, vB,
                                                                         dst + out0, vD, smem_raw, &bar, phase,
                                                                         status, xf)
@@ -406,18 +421,18 @@ cudaError_t launch_large(K* keys, uint32_t* vals, K* tk, uint32_t* tv, const uns
 
 // The medium path: the tile launch, then per merge pass the co-rank launch
 // and the merge launch (fixed shapes; work comes from the device-side list).
-template <class K, bool PAIRS, int TH, int IPT>
-cudaError_t launch_mid(K* keys, uint32_t* vals, K* tk, uint32_t* tv, const unsigned long long* off, size_t nseg,
-                       const unsigned int* lists, unsigned int* counters, unsigned long long* splits,
-                       unsigned int* status, cudaStream_t st, int xf) {
-    auto ft = k_seg_mid_tiles<K, PAIRS, TH, IPT>;
+template <class K, bool PAIRS, int TH, int IPT, bool XF>
+cudaError_t launch_mid_xf(K* keys, uint32_t* vals, K* tk, uint32_t* tv, const unsigned long long* off, size_t nseg,
+                          const unsigned int* lists, unsigned int* counters, unsigned long long* splits,
+                          unsigned int* status, cudaStream_t st, int xf) {
+    auto ft = k_seg_mid_tiles<K, PAIRS, TH, IPT, XF>;
     const size_t st_sm = tile_block_smem<K, PAIRS, TH>(TH * IPT);
     cudaError_t e = allow_smem(ft, st_sm);
     if (e != cudaSuccess) return e;
     ft<<<persistent_blocks(ft, TH, st_sm), TH, st_sm, st>>>(keys, vals, tk, tv, off, nseg, lists, counters, status,
                                                             xf);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    auto fm = k_seg_mid_merge<K, PAIRS, TH, IPT>;
+    auto fm = k_seg_mid_merge<K, PAIRS, TH, IPT, XF>;
     const size_t m_sm = merge_block_smem<K, PAIRS, TH, IPT>();
     if ((e = allow_smem(fm, m_sm)) != cudaSuccess) return e;
     const int mblocks = persistent_blocks(fm, TH, m_sm);
@@ -430,6 +445,15 @@ cudaError_t launch_mid(K* keys, uint32_t* vals, K* tk, uint32_t* tv, const unsig
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+template <class K, bool PAIRS, int TH, int IPT>
+cudaError_t launch_mid(K* keys, uint32_t* vals, K* tk, uint32_t* tv, const unsigned long long* off, size_t nseg,
+                       const unsigned int* lists, unsigned int* counters, unsigned long long* splits,
+                       unsigned int* status, cudaStream_t st, int xf) {
+    return xf ? launch_mid_xf<K, PAIRS, TH, IPT, true>(keys, vals, tk, tv, off, nseg, lists, counters, splits, status,
+                                                       st, xf)
+              : launch_mid_xf<K, PAIRS, TH, IPT, false>(keys, vals, tk, tv, off, nseg, lists, counters, splits,
+                                                        status, st, 0);
 }
 constexpr int kMidLaunches = 1 + 2 * kMidPasses;
 

@@ -24,7 +24,13 @@ BOUNDARY_LENS = [0, 1, 2, 3, 17, 33, 543, 544, 545, 1087, 1088, 1089, 2175, 2176
                  # for 64-bit pairs; around T + T/2, 2T, 3T, 3T + T/2 and 4T
                  25600, 25601, 50688, 50689, 59392, 59393, 67584, 67585,
                  21248, 21249, 25344, 25345, 29696, 29697,
-                 11008, 11009, 13056, 13057, 15360, 15361, 17408, 17409]
+                 11008, 11009, 13056, 13057, 15360, 15361, 17408, 17409,
+                 # a medium segment's last tile takes the smallest of four shapes that holds it (about a
+                 # quarter, half, three quarters or all of a tile): T + q and 3T + q, q at each shape's limit
+                 # (q = 4608, 8704, 12800 of T = 16896; 2304, 4352, 6400 of 8448; 1280, 2304, 3328 of 4352)
+                 21504, 21505, 55296, 55297, 63488, 63489,
+                 10752, 10753, 27648, 27649, 14848, 14849, 31744, 31745,
+                 5632, 5633, 14336, 14337, 6656, 6657, 15360, 7680, 7681, 16384, 16385]
 
 
 @pytest.fixture(scope="module")
