@@ -44,7 +44,8 @@ constexpr int kSegLists = kSegMaxBuckets + 2;
 // its merge launches (one per pass)
 constexpr int kSegFetchMidTiles = 2 * kSegLists;
 constexpr int kSegFetchMidMerge = 2 * kSegLists + 1;
-constexpr int kMidSlots = 4;  // tiles, and output blocks per pass, of a medium segment
+constexpr int kMidSlots = 4;  // tiles of a medium segment
+constexpr int kMidMergeSplit = 2;  // most merge output blocks per medium tile
 constexpr int kMidPasses = 2;
 constexpr unsigned int kStatusBadInput = 2u;
 constexpr int kSegBadFlag = 63;  // counters[63]: this call's bad-input flag
@@ -225,10 +226,11 @@ k_seg_large(K* keys, uint32_t* vals, K* tkeys, uint32_t* tvals, const unsigned l
 }
 
 // Medium segments: more than one on-chip tile, at most kMidSlots tiles of
-// T = THREADS x IPT keys, so one or two merge passes.  Work item it of a
-// phase is slot it % kMidSlots (tile, or output block of W = T keys) of the
-// segment at position it / kMidSlots of the medium list; slots past the end
-// of a shorter segment are skipped.  A segment's tiles land in the buffer
+// T = THREADS x IPT keys, so one or two merge passes.  Work item it of the
+// tile phase is tile it % kMidSlots of the segment at position
+// it / kMidSlots of the medium list; an item of a merge pass is output block
+// it % S (W keys, S = kMidSlots x T / W) of the segment at position it / S.
+// Slots past the end of a shorter segment are skipped.  A segment's tiles land in the buffer
 // its last pass does not write (keys for two passes, the scratch for one),
 // and each pass ping-pongs to the other, so the last pass writes the keys.
 __device__ __forceinline__ int mid_passes(size_t len, size_t T) { return len > 2 * T ? 2 : 1; }
@@ -293,27 +295,31 @@ template <class K>
 __global__ void k_seg_mid_part(const K* __restrict__ keys, const K* __restrict__ tkeys,
                                const unsigned long long* __restrict__ off, size_t nseg,
                                const unsigned int* __restrict__ lists, const unsigned int* __restrict__ counters,
-                               int pass, size_t T, unsigned long long* __restrict__ splits) {
+                               int pass, size_t T, size_t W, unsigned long long* __restrict__ splits) {
     const size_t it = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t slots = kMidSlots * (T / W);
     if (counters[kSegBadFlag]) return;
-    if (it >= (size_t)counters[kSegMid] * kMidSlots) return;
-    const unsigned int s = lists[(size_t)kSegMid * nseg + it / kMidSlots];
+    if (it >= (size_t)counters[kSegMid] * slots) return;
+    const unsigned int s = lists[(size_t)kSegMid * nseg + it / slots];
     const size_t base = off[s], len = off[s + 1] - base;
     const int P = mid_passes(len, T);
-    const size_t out0 = (it % kMidSlots) * T;
+    const size_t out0 = (it % slots) * W;
     if (pass >= P || out0 >= len) return;
     const K* src = (((P ^ pass) & 1) ? tkeys : keys) + base;  // the pass's input buffer
     const PassGeom g = pass_geom(out0, len, T << pass);
     splits[it] = corank_search(src + g.pb, g.alen, src + g.pb + g.alen, g.blen, out0 - g.pb);
 }
 
-// Merge blocks of pass `pass` over every medium segment still merging.
-template <class K, bool PAIRS, int THREADS, int IPT, bool XF>
-__global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 3 : 2)
+// Merge blocks of pass `pass` over every medium segment still merging
+// (blocks of W = THREADS x IPT outputs, segments of tiles of TILE keys).
+template <class K, bool PAIRS, int THREADS, int IPT, bool XF, int TILE>
+__global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 3 : (sizeof(K) == 4 && !PAIRS && IPT == 33 ? 6 : 2))
 k_seg_mid_merge(K* keys, uint32_t* vals, K* tkeys, uint32_t* tvals, const unsigned long long* __restrict__ off,
                 size_t nseg, const unsigned int* __restrict__ lists, unsigned int* counters, int pass,
                 const unsigned long long* __restrict__ splits, unsigned int* status, int xf) {
     constexpr int W = THREADS * IPT;
+    static_assert(TILE % W == 0 && TILE / W <= kMidMergeSplit, "merge blocks tile a medium tile");
+    constexpr unsigned int kSlots = kMidSlots * (TILE / W);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ unsigned int slot;
@@ -323,20 +329,20 @@ k_seg_mid_merge(K* keys, uint32_t* vals, K* tkeys, uint32_t* tvals, const unsign
     }
     if (counters[kSegBadFlag]) return;
     uint32_t phase = 0;
-    const unsigned int items = counters[kSegMid] * kMidSlots;
+    const unsigned int items = counters[kSegMid] * kSlots;
     for (unsigned int it = seg_fetch(counters, kSegFetchMidMerge + pass, &slot); it < items;
          it = seg_fetch(counters, kSegFetchMidMerge + pass, &slot)) {
-        const unsigned int s = lists[(size_t)kSegMid * nseg + it / kMidSlots];
+        const unsigned int s = lists[(size_t)kSegMid * nseg + it / kSlots];
         const size_t base = off[s], len = off[s + 1] - base;
-        const int P = mid_passes(len, W);
-        const size_t out0 = (size_t)(it % kMidSlots) * W;
+        const int P = mid_passes(len, TILE);
+        const size_t out0 = (size_t)(it % kSlots) * W;
         if (pass >= P || out0 >= len) continue;
         const int cur = (P ^ pass) & 1;
         K* bk[2] = {keys + base, tkeys + base};
         uint32_t* bv[2] = {PAIRS ? vals + base : nullptr, PAIRS ? tvals + base : nullptr};
         const K* src = bk[cur];
         K* dst = bk[cur ^ 1];
-        const PassGeom g = pass_geom(out0, len, (size_t)W << pass);
+        const PassGeom g = pass_geom(out0, len, (size_t)TILE << pass);
         const size_t d0 = out0 - g.pb;
         const size_t dend = g.alen + g.blen;
         const size_t d1 = (d0 + W < dend) ? d0 + W : dend;
@@ -421,7 +427,8 @@ cudaError_t launch_large(K* keys, uint32_t* vals, K* tk, uint32_t* tv, const uns
 
 // The medium path: the tile launch, then per merge pass the co-rank launch
 // and the merge launch (fixed shapes; work comes from the device-side list).
-template <class K, bool PAIRS, int TH, int IPT, bool XF>
+// Tiles of TH x IPT keys; merge blocks of MTH x IPT outputs.
+template <class K, bool PAIRS, int TH, int IPT, int MTH, bool XF>
 cudaError_t launch_mid_xf(K* keys, uint32_t* vals, K* tk, uint32_t* tv, const unsigned long long* off, size_t nseg,
                           const unsigned int* lists, unsigned int* counters, unsigned long long* splits,
                           unsigned int* status, cudaStream_t st, int xf) {
@@ -432,28 +439,29 @@ cudaError_t launch_mid_xf(K* keys, uint32_t* vals, K* tk, uint32_t* tv, const un
     ft<<<persistent_blocks(ft, TH, st_sm), TH, st_sm, st>>>(keys, vals, tk, tv, off, nseg, lists, counters, status,
                                                             xf);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    auto fm = k_seg_mid_merge<K, PAIRS, TH, IPT, XF>;
-    const size_t m_sm = merge_block_smem<K, PAIRS, TH, IPT>();
+    auto fm = k_seg_mid_merge<K, PAIRS, MTH, IPT, XF, TH * IPT>;
+    const size_t m_sm = merge_block_smem<K, PAIRS, MTH, IPT>();
     if ((e = allow_smem(fm, m_sm)) != cudaSuccess) return e;
-    const int mblocks = persistent_blocks(fm, TH, m_sm);
-    const size_t items = (size_t)kMidSlots * nseg;
+    const int mblocks = persistent_blocks(fm, MTH, m_sm);
+    const size_t items = (size_t)kMidSlots * (TH / MTH) * nseg;
     for (int pass = 0; pass < kMidPasses; ++pass) {
-        k_seg_mid_part<K><<<(unsigned)((items + 127) / 128), 128, 0, st>>>(keys, tk, off, nseg, lists, counters,
-                                                                           pass, (size_t)(TH * IPT), splits);
+        k_seg_mid_part<K><<<(unsigned)((items + 127) / 128), 128, 0, st>>>(
+            keys, tk, off, nseg, lists, counters, pass, (size_t)(TH * IPT), (size_t)(MTH * IPT), splits);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        fm<<<mblocks, TH, m_sm, st>>>(keys, vals, tk, tv, off, nseg, lists, counters, pass, splits, status, xf);
+        fm<<<mblocks, MTH, m_sm, st>>>(keys, vals, tk, tv, off, nseg, lists, counters, pass, splits, status, xf);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
-template <class K, bool PAIRS, int TH, int IPT>
+template <class K, bool PAIRS, int TH, int IPT, int MTH = TH>
 cudaError_t launch_mid(K* keys, uint32_t* vals, K* tk, uint32_t* tv, const unsigned long long* off, size_t nseg,
                        const unsigned int* lists, unsigned int* counters, unsigned long long* splits,
                        unsigned int* status, cudaStream_t st, int xf) {
-    return xf ? launch_mid_xf<K, PAIRS, TH, IPT, true>(keys, vals, tk, tv, off, nseg, lists, counters, splits, status,
-                                                       st, xf)
-              : launch_mid_xf<K, PAIRS, TH, IPT, false>(keys, vals, tk, tv, off, nseg, lists, counters, splits,
-                                                        status, st, 0);
+    static_assert(TH % MTH == 0 && TH / MTH <= kMidMergeSplit, "merge blocks tile a medium tile");
+    return xf ? launch_mid_xf<K, PAIRS, TH, IPT, MTH, true>(keys, vals, tk, tv, off, nseg, lists, counters, splits,
+                                                            status, st, xf)
+              : launch_mid_xf<K, PAIRS, TH, IPT, MTH, false>(keys, vals, tk, tv, off, nseg, lists, counters, splits,
+                                                             status, st, 0);
 }
 constexpr int kMidLaunches = 1 + 2 * kMidPasses;
 
@@ -517,8 +525,10 @@ struct SegPlan<uint32_t, false> {
             return launch_large<uint32_t, false, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, status,
                                                           st, xf);
         }
-        if ((e = launch_mid<uint32_t, false, 512, 33>(keys, vals, tk, tv, off, nseg, lists, counters, msplits, status,
-                                                      st, xf)))
+        // merge blocks of half a tile: 256 x 33 at 40 registers fits six
+        // blocks per SM, the shape of the plain merge pass
+        if ((e = launch_mid<uint32_t, false, 512, 33, 256>(keys, vals, tk, tv, off, nseg, lists, counters, msplits,
+                                                           status, st, xf)))
             return e;
         return launch_large<uint32_t, false, 512, 33>(keys, vals, tk, tv, off, nseg, lists, counters, status, st, xf);
     }
@@ -594,7 +604,7 @@ SegLayout seg_layout(size_t n, size_t nseg) {
     l.lists = l.vals + (PAIRS ? align_up(n * 4, 256) : 0);
     l.counters = l.lists + align_up((size_t)kSegLists * nseg * 4, 256);
     l.msplits = l.counters + 256;
-    l.end = l.msplits + align_up((size_t)kMidSlots * nseg * sizeof(unsigned long long), 256);
+    l.end = l.msplits + align_up((size_t)kMidSlots * kMidMergeSplit * nseg * sizeof(unsigned long long), 256);
     return l;
 }
 
