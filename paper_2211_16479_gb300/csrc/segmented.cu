@@ -93,9 +93,39 @@ __device__ __forceinline__ unsigned int seg_next(unsigned int* counters, int q, 
     return seg_fetch(counters, kSegLists + q, slot);
 }
 
-// Small bucket: every segment fits one block of THREADS x IPT keys.
+// Odd keys per thread (conflict-free strided shared-memory access) for a
+// shape holding about num/4 of a THREADS x ipt tile.
+__host__ __device__ constexpr int odd_ipt(int ipt, int num) {
+    return (num * ipt + 3) / 4 + ((num * ipt + 3) / 4 % 2 == 0 ? 1 : 0);
+}
+
+// Blocks of a tile-sort shape that fit on one SM by shared memory (228 KB,
+// 1 KB reserved per block), threads (2048) and the block limit (32).
 template <class K, bool PAIRS, int THREADS, int IPT>
-__global__ void __launch_bounds__(THREADS)
+__host__ __device__ constexpr int tile_blocks_per_sm() {
+    const int by_smem = (int)((228u << 10) / (tile_block_smem<K, PAIRS, THREADS>(THREADS * IPT) + 1024u));
+    const int by_threads = 2048 / THREADS;
+    const int b = by_smem < by_threads ? by_smem : by_threads;
+    return b < 32 ? b : 32;
+}
+
+// Minimum blocks per SM for the small-bucket kernel of unsigned 32-bit keys
+// without values: the 17-key shapes as many as shared memory allows (32
+// registers); the 33-key shapes as many as 48 registers allow, the most
+// they take without spilling.  Other key types are left to the compiler.
+template <class K, bool PAIRS, int THREADS, int IPT, bool XF>
+__host__ __device__ constexpr int small_min_blocks() {
+    if (sizeof(K) != 4 || PAIRS || XF) return 0;
+    if (IPT <= 17) return tile_blocks_per_sm<K, PAIRS, THREADS, IPT>();
+    return 65536 / (48 * THREADS) > 0 ? 65536 / (48 * THREADS) : 1;
+}
+
+// Small bucket: every segment fits one block of THREADS x IPT keys.  A
+// block's cost follows its shape, not its fill, so a segment of at most
+// about three quarters of that takes the shape with three quarters of the
+// keys per thread.  XF as for the medium kernels.
+template <class K, bool PAIRS, int THREADS, int IPT, bool XF>
+__global__ void __launch_bounds__(THREADS, small_min_blocks<K, PAIRS, THREADS, IPT, XF>())
 k_seg_small(K* keys, uint32_t* vals, const unsigned long long* __restrict__ off, size_t nseg,
             const unsigned int* __restrict__ lists, unsigned int* counters, int q, unsigned int* status, int xf) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -112,10 +142,16 @@ k_seg_small(K* keys, uint32_t* vals, const unsigned long long* __restrict__ off,
         const unsigned int s = lists[(size_t)q * nseg + w];
         const size_t b = off[s];
         const int len = (int)(off[s + 1] - b);
-        if (!tile_sort_block<K, PAIRS, THREADS, IPT, true>(keys + b, PAIRS ? vals + b : nullptr, keys + b,
-                                                     PAIRS ? vals + b : nullptr, len, smem_raw, &bar, phase,
-                                                     status, xf, xf))
-            return;
+        constexpr int kQ3 = odd_ipt(IPT, 3);
+        static_assert(kQ3 < IPT, "a smaller shape");
+        K* sk = keys + b;
+        uint32_t* sv = PAIRS ? vals + b : nullptr;
+        const bool ok = len <= THREADS * kQ3
+                            ? tile_sort_block<K, PAIRS, THREADS, kQ3, XF>(sk, sv, sk, sv, len, smem_raw, &bar,
+                                                                          phase, status, xf, xf)
+                            : tile_sort_block<K, PAIRS, THREADS, IPT, XF>(sk, sv, sk, sv, len, smem_raw, &bar,
+                                                                          phase, status, xf, xf);
+        if (!ok) return;
     }
 }
 
@@ -234,12 +270,6 @@ k_seg_large(K* keys, uint32_t* vals, K* tkeys, uint32_t* tvals, const unsigned l
 // its last pass does not write (keys for two passes, the scratch for one),
 // and each pass ping-pongs to the other, so the last pass writes the keys.
 __device__ __forceinline__ int mid_passes(size_t len, size_t T) { return len > 2 * T ? 2 : 1; }
-
-// Odd keys per thread (conflict-free strided shared-memory access) for a
-// shape holding about num/4 of a large tile.
-__host__ __device__ constexpr int odd_ipt(int ipt, int num) {
-    return (num * ipt + 3) / 4 + ((num * ipt + 3) / 4 % 2 == 0 ? 1 : 0);
-}
 
 // XF: whether the keys take a transform (signed or floating-point keys);
 // the instance without one keeps the transform's registers out of the
@@ -402,7 +432,7 @@ template <class K, bool PAIRS, int TH, int IPT>
 cudaError_t launch_small(K* keys, uint32_t* vals, const unsigned long long* off, size_t nseg,
                          const unsigned int* lists, unsigned int* counters, int q, unsigned int* status,
                          cudaStream_t st, int xf) {
-    auto f = k_seg_small<K, PAIRS, TH, IPT>;
+    auto f = xf ? k_seg_small<K, PAIRS, TH, IPT, true> : k_seg_small<K, PAIRS, TH, IPT, false>;
     const size_t sm = tile_block_smem<K, PAIRS, TH>(TH * IPT);
     cudaError_t e = allow_smem(f, sm);
     if (e != cudaSuccess) return e;
