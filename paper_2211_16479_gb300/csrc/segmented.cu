@@ -15,8 +15,9 @@
 //   3. Segments of up to four large tiles (one or two merge passes): one
 //      persistent launch sorts every tile of every such segment, then each
 //      merge pass is one launch of co-rank searches (a thread per output
-//      block) and one persistent launch of bulk-TMA merge blocks, all
-//      segments' blocks at once, so the whole GPU runs each phase.
+//      block, writing the block's descriptor) and one persistent launch of
+//      bulk-TMA merge blocks, all segments' blocks at once, so the whole GPU
+//      runs each phase.
 //   4. One persistent launch for the longer segments: a block sorts the
 //      segment's tiles, then runs the segment's merge passes itself
 //      (co-ranks of all its output blocks by binary search in parallel, then
@@ -40,10 +41,10 @@ constexpr int kSegLarge = kSegMaxBuckets;  // index of the large-segment list
 constexpr int kSegMid = kSegMaxBuckets + 1;  // index of the medium-segment list (up to kMidSlots tiles)
 constexpr int kSegLists = kSegMaxBuckets + 2;
 // counters[q] = entries of list q; counters[kSegLists + q] = its work-fetch
-// counter; then the fetch counters of the medium path's tile launch and of
-// its merge launches (one per pass)
+// counter; then the fetch counter of the medium path's tile launch and the
+// number of output blocks of each of its merge passes
 constexpr int kSegFetchMidTiles = 2 * kSegLists;
-constexpr int kSegFetchMidMerge = 2 * kSegLists + 1;
+constexpr int kSegMidBlocks = 2 * kSegLists + 1;  // + pass: output blocks of that medium merge pass
 constexpr int kMidSlots = 4;  // tiles of a medium segment
 constexpr int kMidMergeSplit = 2;  // most merge output blocks per medium tile
 constexpr int kMidPasses = 2;
@@ -320,77 +321,143 @@ k_seg_mid_tiles(K* keys, uint32_t* vals, K* tkeys, uint32_t* tvals, const unsign
     }
 }
 
-// Co-rank of every output block start of merge pass `pass` (a thread per item).
+// One output block of a medium merge pass, written by k_seg_mid_part and
+// read by k_seg_mid_merge (48 bytes, copied to shared memory in three
+// 16-byte pieces).
+struct __align__(16) MidBlock {
+    unsigned long long a, b, d;  // element offsets: the A and B windows (source buffer), the output (other one)
+    unsigned int na, nb;         // window lengths
+    unsigned int src;            // source buffer: 0 the keys, 1 the scratch
+    unsigned int last;           // 1 on the segment's last merge pass
+    unsigned int pad[2];
+};
+static_assert(sizeof(MidBlock) == 48, "three 16-byte pieces");
+
+// Most medium merge blocks of one pass: a medium segment holds more than
+// 1024 keys in every plan, so there are at most n / 1025 of them.
+inline size_t mid_block_cap(size_t n, size_t nseg) {
+    const size_t segs = n / 1025 < nseg ? n / 1025 : nseg;
+    return (segs + 1) * kMidSlots * kMidMergeSplit;
+}
+
+// Output blocks of merge pass `pass` (a thread per segment slot): the stable
+// co-ranks of the block's first and last diagonal, appended to `blocks` in
+// any order (the blocks are independent).  A block's end co-rank is the next
+// slot's start co-rank, so lanes take it from their neighbour and only the
+// last lane of a warp searches twice.
 template <class K>
 __global__ void k_seg_mid_part(const K* __restrict__ keys, const K* __restrict__ tkeys,
                                const unsigned long long* __restrict__ off, size_t nseg,
-                               const unsigned int* __restrict__ lists, const unsigned int* __restrict__ counters,
-                               int pass, size_t T, size_t W, unsigned long long* __restrict__ splits) {
+                               const unsigned int* __restrict__ lists, unsigned int* counters, int pass, size_t T,
+                               size_t W, MidBlock* __restrict__ blocks) {
     const size_t it = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned int lane = threadIdx.x & 31u;
     const size_t slots = kMidSlots * (T / W);
-    if (counters[kSegBadFlag]) return;
-    if (it >= (size_t)counters[kSegMid] * slots) return;
-    const unsigned int s = lists[(size_t)kSegMid * nseg + it / slots];
-    const size_t base = off[s], len = off[s + 1] - base;
-    const int P = mid_passes(len, T);
-    const size_t out0 = (it % slots) * W;
-    if (pass >= P || out0 >= len) return;
-    const K* src = (((P ^ pass) & 1) ? tkeys : keys) + base;  // the pass's input buffer
-    const PassGeom g = pass_geom(out0, len, T << pass);
-    splits[it] = corank_search(src + g.pb, g.alen, src + g.pb + g.alen, g.blen, out0 - g.pb);
+    if (counters[kSegBadFlag]) return;  // the same for every thread
+    bool valid = false;
+    size_t a0 = 0, d0 = 0, d1 = 0, dend = 0;
+    size_t base = 0, pb = 0, alen = 0, blen = 0, out0 = 0;
+    int P = 0;
+    const K* src = nullptr;
+    if (it < (size_t)counters[kSegMid] * slots) {
+        const unsigned int s = lists[(size_t)kSegMid * nseg + it / slots];
+        base = off[s];
+        const size_t len = off[s + 1] - base;
+        P = mid_passes(len, T);
+        out0 = (it % slots) * W;
+        if (pass < P && out0 < len) {
+            valid = true;
+            src = (((P ^ pass) & 1) ? tkeys : keys) + base;  // the pass's input buffer
+            const PassGeom g = pass_geom(out0, len, T << pass);
+            pb = g.pb;
+            alen = g.alen;
+            blen = g.blen;
+            d0 = out0 - pb;
+            dend = alen + blen;
+            d1 = d0 + W < dend ? d0 + W : dend;
+            a0 = corank_search(src + pb, alen, src + pb + alen, blen, d0);
+        }
+    }
+    // the next slot (lane + 1) starts where this block ends when the pair goes on
+    const unsigned long long next = __shfl_down_sync(0xffffffffu, (unsigned long long)a0, 1);
+    size_t a1 = alen;
+    if (valid && d1 < dend) a1 = lane < 31 ? (size_t)next : corank_search(src + pb, alen, src + pb + alen, blen, d1);
+    const unsigned int mask = __ballot_sync(0xffffffffu, valid);
+    if (!mask) return;  // the same for the whole warp
+    const int leader = __ffs(mask) - 1;
+    unsigned int first = 0;
+    if ((int)lane == leader) first = atomicAdd(&counters[kSegMidBlocks + pass], (unsigned int)__popc(mask));
+    first = __shfl_sync(0xffffffffu, first, leader);
+    if (!valid) return;
+    MidBlock mb;
+    mb.a = base + pb + a0;
+    mb.b = base + pb + alen + (d0 - a0);
+    mb.d = base + out0;
+    mb.na = (unsigned int)(a1 - a0);
+    mb.nb = (unsigned int)((d1 - d0) - (a1 - a0));
+    mb.src = (unsigned int)((P ^ pass) & 1);
+    mb.last = pass + 1 == P ? 1u : 0u;
+    mb.pad[0] = mb.pad[1] = 0u;
+    blocks[first + __popc(mask & ((1u << lane) - 1u))] = mb;
 }
 
-// Merge blocks of pass `pass` over every medium segment still merging
-// (blocks of W = THREADS x IPT outputs, segments of tiles of TILE keys).
-template <class K, bool PAIRS, int THREADS, int IPT, bool XF, int TILE>
+// 16-byte asynchronous copy from global to shared memory, completed by the
+// issuing thread's cp_async_wait_all.
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(sdst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// The output blocks of merge pass `pass` (W = THREADS x IPT outputs each),
+// block i to CTA i mod gridDim.x.  Thread 0 copies the next block's
+// descriptor to shared memory while the current one merges, so a block's
+// work starts without a chain of dependent loads.
+template <class K, bool PAIRS, int THREADS, int IPT, bool XF>
 __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 3 : (sizeof(K) == 4 && !PAIRS && IPT == 33 ? 6 : 2))
-k_seg_mid_merge(K* keys, uint32_t* vals, K* tkeys, uint32_t* tvals, const unsigned long long* __restrict__ off,
-                size_t nseg, const unsigned int* __restrict__ lists, unsigned int* counters, int pass,
-                const unsigned long long* __restrict__ splits, unsigned int* status, int xf) {
-    constexpr int W = THREADS * IPT;
-    static_assert(TILE % W == 0 && TILE / W <= kMidMergeSplit, "merge blocks tile a medium tile");
-    constexpr unsigned int kSlots = kMidSlots * (TILE / W);
+k_seg_mid_merge(K* keys, uint32_t* vals, K* tkeys, uint32_t* tvals, const unsigned int* __restrict__ counters,
+                int pass, const MidBlock* __restrict__ blocks, unsigned int* status, int xf) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
-    __shared__ unsigned int slot;
-    if (threadIdx.x == 0) {
+    __shared__ MidBlock desc[2];
+    const int t = threadIdx.x;
+    if (t == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
     }
     if (counters[kSegBadFlag]) return;
     uint32_t phase = 0;
-    const unsigned int items = counters[kSegMid] * kSlots;
-    for (unsigned int it = seg_fetch(counters, kSegFetchMidMerge + pass, &slot); it < items;
-         it = seg_fetch(counters, kSegFetchMidMerge + pass, &slot)) {
-        const unsigned int s = lists[(size_t)kSegMid * nseg + it / kSlots];
-        const size_t base = off[s], len = off[s + 1] - base;
-        const int P = mid_passes(len, TILE);
-        const size_t out0 = (size_t)(it % kSlots) * W;
-        if (pass >= P || out0 >= len) continue;
-        const int cur = (P ^ pass) & 1;
-        K* bk[2] = {keys + base, tkeys + base};
-        uint32_t* bv[2] = {PAIRS ? vals + base : nullptr, PAIRS ? tvals + base : nullptr};
-        const K* src = bk[cur];
-        K* dst = bk[cur ^ 1];
-        const PassGeom g = pass_geom(out0, len, (size_t)TILE << pass);
-        const size_t d0 = out0 - g.pb;
-        const size_t dend = g.alen + g.blen;
-        const size_t d1 = (d0 + W < dend) ? d0 + W : dend;
-        const size_t a0 = splits[it];
-        const size_t a1 = (d1 == dend) ? g.alen : (size_t)splits[it + 1];  // the next block is in this pair
-        const int nA = (int)(a1 - a0);
-        const int nB = (int)(d1 - d0) - nA;
-        const size_t oA = g.pb + a0, oB = g.pb + g.alen + (d0 - a0);
-        const uint32_t* vA = PAIRS ? bv[cur] + oA : nullptr;
-        const uint32_t* vB = PAIRS ? bv[cur] + oB : nullptr;
-        uint32_t* vD = PAIRS ? bv[cur ^ 1] + out0 : nullptr;
-        const bool ok = (XF && pass + 1 == P)
-                            ? merge_block<K, PAIRS, THREADS, IPT, true>(src + oA, nA, src + oB, nB, vA, vB,
-                                                                        dst + out0, vD, smem_raw, &bar, phase,
-                                                                        status, xf)
-                            : merge_block<K, PAIRS, THREADS, IPT, false>(src + oA, nA, src + oB, nB, vA, vB,
-                                                                         dst + out0, vD, smem_raw, &bar, phase,
-                                                                         status, 0);
+    const unsigned int items = counters[kSegMidBlocks + pass];
+    if (t == 0 && blockIdx.x < items) {
+        for (int k = 0; k < 3; ++k)
+            cp_async16(reinterpret_cast<char*>(&desc[0]) + 16 * k,
+                       reinterpret_cast<const char*>(blocks + blockIdx.x) + 16 * k);
+        cp_async_commit();
+    }
+    int cur = 0;
+    for (unsigned int i = blockIdx.x; i < items; i += gridDim.x, cur ^= 1) {
+        if (t == 0) cp_async_wait_all();
+        __syncthreads();  // desc[cur] is in place; every thread is done with desc[cur ^ 1]
+        const MidBlock d = desc[cur];
+        if (t == 0 && i + gridDim.x < items) {
+            for (int k = 0; k < 3; ++k)
+                cp_async16(reinterpret_cast<char*>(&desc[cur ^ 1]) + 16 * k,
+                           reinterpret_cast<const char*>(blocks + i + gridDim.x) + 16 * k);
+            cp_async_commit();
+        }
+        const K* src = d.src ? tkeys : keys;
+        K* dst = d.src ? keys : tkeys;
+        const uint32_t* vs = PAIRS ? (d.src ? tvals : vals) : nullptr;
+        uint32_t* vd = PAIRS ? (d.src ? vals : tvals) : nullptr;
+        const bool ok = (XF && d.last)
+                            ? merge_block<K, PAIRS, THREADS, IPT, true>(
+                                  src + d.a, (int)d.na, src + d.b, (int)d.nb, PAIRS ? vs + d.a : nullptr,
+                                  PAIRS ? vs + d.b : nullptr, dst + d.d, PAIRS ? vd + d.d : nullptr, smem_raw, &bar,
+                                  phase, status, xf)
+                            : merge_block<K, PAIRS, THREADS, IPT, false>(
+                                  src + d.a, (int)d.na, src + d.b, (int)d.nb, PAIRS ? vs + d.a : nullptr,
+                                  PAIRS ? vs + d.b : nullptr, dst + d.d, PAIRS ? vd + d.d : nullptr, smem_raw, &bar,
+                                  phase, status, 0);
         if (!ok) return;
     }
 }
@@ -460,7 +527,7 @@ cudaError_t launch_large(K* keys, uint32_t* vals, K* tk, uint32_t* tv, const uns
 // Tiles of TH x IPT keys; merge blocks of MTH x IPT outputs.
 template <class K, bool PAIRS, int TH, int IPT, int MTH, bool XF>
 cudaError_t launch_mid_xf(K* keys, uint32_t* vals, K* tk, uint32_t* tv, const unsigned long long* off, size_t nseg,
-                          const unsigned int* lists, unsigned int* counters, unsigned long long* splits,
+                          const unsigned int* lists, unsigned int* counters, MidBlock* desc,
                           unsigned int* status, cudaStream_t st, int xf) {
     auto ft = k_seg_mid_tiles<K, PAIRS, TH, IPT, XF>;
     const size_t st_sm = tile_block_smem<K, PAIRS, TH>(TH * IPT);
@@ -469,28 +536,28 @@ cudaError_t launch_mid_xf(K* keys, uint32_t* vals, K* tk, uint32_t* tv, const un
     ft<<<persistent_blocks(ft, TH, st_sm), TH, st_sm, st>>>(keys, vals, tk, tv, off, nseg, lists, counters, status,
                                                             xf);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    auto fm = k_seg_mid_merge<K, PAIRS, MTH, IPT, XF, TH * IPT>;
+    auto fm = k_seg_mid_merge<K, PAIRS, MTH, IPT, XF>;
     const size_t m_sm = merge_block_smem<K, PAIRS, MTH, IPT>();
     if ((e = allow_smem(fm, m_sm)) != cudaSuccess) return e;
     const int mblocks = persistent_blocks(fm, MTH, m_sm);
     const size_t items = (size_t)kMidSlots * (TH / MTH) * nseg;
     for (int pass = 0; pass < kMidPasses; ++pass) {
         k_seg_mid_part<K><<<(unsigned)((items + 127) / 128), 128, 0, st>>>(
-            keys, tk, off, nseg, lists, counters, pass, (size_t)(TH * IPT), (size_t)(MTH * IPT), splits);
+            keys, tk, off, nseg, lists, counters, pass, (size_t)(TH * IPT), (size_t)(MTH * IPT), desc);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        fm<<<mblocks, MTH, m_sm, st>>>(keys, vals, tk, tv, off, nseg, lists, counters, pass, splits, status, xf);
+        fm<<<mblocks, MTH, m_sm, st>>>(keys, vals, tk, tv, counters, pass, desc, status, xf);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 template <class K, bool PAIRS, int TH, int IPT, int MTH = TH>
 cudaError_t launch_mid(K* keys, uint32_t* vals, K* tk, uint32_t* tv, const unsigned long long* off, size_t nseg,
-                       const unsigned int* lists, unsigned int* counters, unsigned long long* splits,
+                       const unsigned int* lists, unsigned int* counters, MidBlock* desc,
                        unsigned int* status, cudaStream_t st, int xf) {
     static_assert(TH % MTH == 0 && TH / MTH <= kMidMergeSplit, "merge blocks tile a medium tile");
-    return xf ? launch_mid_xf<K, PAIRS, TH, IPT, MTH, true>(keys, vals, tk, tv, off, nseg, lists, counters, splits,
+    return xf ? launch_mid_xf<K, PAIRS, TH, IPT, MTH, true>(keys, vals, tk, tv, off, nseg, lists, counters, desc,
                                                             status, st, xf)
-              : launch_mid_xf<K, PAIRS, TH, IPT, MTH, false>(keys, vals, tk, tv, off, nseg, lists, counters, splits,
+              : launch_mid_xf<K, PAIRS, TH, IPT, MTH, false>(keys, vals, tk, tv, off, nseg, lists, counters, desc,
                                                              status, st, 0);
 }
 constexpr int kMidLaunches = 1 + 2 * kMidPasses;
@@ -531,7 +598,7 @@ struct SegPlan<uint32_t, false> {
     }
     static cudaError_t run(const msort_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t* tk, uint32_t* tv,
                            const unsigned long long* off, size_t nseg, const unsigned int* lists,
-                           unsigned int* counters, unsigned long long* msplits, unsigned int* status, cudaStream_t st,
+                           unsigned int* counters, MidBlock* mdesc, unsigned int* status, cudaStream_t st,
                            int xf) {
         cudaError_t e;
         if (buckets(ctx).n == 6) {
@@ -549,7 +616,7 @@ struct SegPlan<uint32_t, false> {
                 return e;
         }
         if (ctx && ctx->seg_large_tile == 8448) {
-            if ((e = launch_mid<uint32_t, false, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, msplits,
+            if ((e = launch_mid<uint32_t, false, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, mdesc,
                                                           status, st, xf)))
                 return e;
             return launch_large<uint32_t, false, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, status,
@@ -557,7 +624,7 @@ struct SegPlan<uint32_t, false> {
         }
         // merge blocks of half a tile: 256 x 33 at 40 registers fits six
         // blocks per SM, the shape of the plain merge pass
-        if ((e = launch_mid<uint32_t, false, 512, 33, 256>(keys, vals, tk, tv, off, nseg, lists, counters, msplits,
+        if ((e = launch_mid<uint32_t, false, 512, 33, 256>(keys, vals, tk, tv, off, nseg, lists, counters, mdesc,
                                                            status, st, xf)))
             return e;
         return launch_large<uint32_t, false, 512, 33>(keys, vals, tk, tv, off, nseg, lists, counters, status, st, xf);
@@ -571,13 +638,13 @@ struct SegPlan<uint32_t, true> {
     }
     static cudaError_t run(const msort_ctx*, uint32_t* keys, uint32_t* vals, uint32_t* tk, uint32_t* tv,
                            const unsigned long long* off,
-                           size_t nseg, const unsigned int* lists, unsigned int* counters, unsigned long long* msplits,
+                           size_t nseg, const unsigned int* lists, unsigned int* counters, MidBlock* mdesc,
                            unsigned int* status, cudaStream_t st, int xf) {
         cudaError_t e;
         MSORT_SMALL2X_LAUNCHES(uint32_t, true)
         if ((e = launch_small<uint32_t, true, 512, 33>(keys, vals, off, nseg, lists, counters, 5, status, st, xf)))
             return e;
-        if ((e = launch_mid<uint32_t, true, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, msplits, status,
+        if ((e = launch_mid<uint32_t, true, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, mdesc, status,
                                                      st, xf)))
             return e;
         return launch_large<uint32_t, true, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, status, st, xf);
@@ -591,13 +658,13 @@ struct SegPlan<uint64_t, false> {
     }
     static cudaError_t run(const msort_ctx*, uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv,
                            const unsigned long long* off,
-                           size_t nseg, const unsigned int* lists, unsigned int* counters, unsigned long long* msplits,
+                           size_t nseg, const unsigned int* lists, unsigned int* counters, MidBlock* mdesc,
                            unsigned int* status, cudaStream_t st, int xf) {
         cudaError_t e;
         MSORT_SMALL2X_LAUNCHES(uint64_t, false)
         if ((e = launch_small<uint64_t, false, 512, 33>(keys, vals, off, nseg, lists, counters, 5, status, st, xf)))
             return e;
-        if ((e = launch_mid<uint64_t, false, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, msplits, status,
+        if ((e = launch_mid<uint64_t, false, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, mdesc, status,
                                                       st, xf)))
             return e;
         return launch_large<uint64_t, false, 256, 33>(keys, vals, tk, tv, off, nseg, lists, counters, status, st, xf);
@@ -611,11 +678,11 @@ struct SegPlan<uint64_t, true> {
     }
     static cudaError_t run(const msort_ctx*, uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv,
                            const unsigned long long* off,
-                           size_t nseg, const unsigned int* lists, unsigned int* counters, unsigned long long* msplits,
+                           size_t nseg, const unsigned int* lists, unsigned int* counters, MidBlock* mdesc,
                            unsigned int* status, cudaStream_t st, int xf) {
         cudaError_t e;
         MSORT_SMALL2X_LAUNCHES(uint64_t, true)
-        if ((e = launch_mid<uint64_t, true, 256, 17>(keys, vals, tk, tv, off, nseg, lists, counters, msplits, status,
+        if ((e = launch_mid<uint64_t, true, 256, 17>(keys, vals, tk, tv, off, nseg, lists, counters, mdesc, status,
                                                      st, xf)))
             return e;
         return launch_large<uint64_t, true, 256, 17>(keys, vals, tk, tv, off, nseg, lists, counters, status, st, xf);
@@ -623,7 +690,7 @@ struct SegPlan<uint64_t, true> {
 };
 
 struct SegLayout {
-    size_t keys, vals, lists, counters, msplits, end;
+    size_t keys, vals, lists, counters, mdesc, end;
 };
 
 template <class K, bool PAIRS>
@@ -633,8 +700,8 @@ SegLayout seg_layout(size_t n, size_t nseg) {
     l.vals = align_up(n * sizeof(K), 256);
     l.lists = l.vals + (PAIRS ? align_up(n * 4, 256) : 0);
     l.counters = l.lists + align_up((size_t)kSegLists * nseg * 4, 256);
-    l.msplits = l.counters + 256;
-    l.end = l.msplits + align_up((size_t)kMidSlots * kMidMergeSplit * nseg * sizeof(unsigned long long), 256);
+    l.mdesc = l.counters + 256;
+    l.end = l.mdesc + align_up(mid_block_cap(n, nseg) * sizeof(MidBlock), 256);
     return l;
 }
 
@@ -647,7 +714,7 @@ msort_status seg_enqueue(msort_ctx* ctx, K* keys, uint32_t* vals, const unsigned
     uint32_t* tv = PAIRS ? reinterpret_cast<uint32_t*>(sp + l.vals) : nullptr;
     unsigned int* lists = reinterpret_cast<unsigned int*>(sp + l.lists);
     unsigned int* counters = reinterpret_cast<unsigned int*>(sp + l.counters);
-    unsigned long long* msplits = reinterpret_cast<unsigned long long*>(sp + l.msplits);
+    MidBlock* mdesc = reinterpret_cast<MidBlock*>(sp + l.mdesc);
     cudaError_t e = cudaMemsetAsync(counters, 0, 256, st);
     if (e != cudaSuccess) return cuda_fail(e, "clearing segment counters");
     prof_begin(ctx, KK_SEGMENTED, st);
@@ -655,7 +722,7 @@ msort_status seg_enqueue(msort_ctx* ctx, K* keys, uint32_t* vals, const unsigned
                                                                    lists, counters, ctx->d_status);
     e = cudaGetLastError();
     if (e == cudaSuccess)
-        e = SegPlan<K, PAIRS>::run(ctx, keys, vals, tk, tv, off, nseg, lists, counters, msplits, ctx->d_status, st,
+        e = SegPlan<K, PAIRS>::run(ctx, keys, vals, tk, tv, off, nseg, lists, counters, mdesc, ctx->d_status, st,
                                    xf);
     prof_end(ctx, KK_SEGMENTED, st);
     ctx->launches += 1 + SegPlan<K, PAIRS>::buckets(ctx).n + kMidLaunches + 1;
