@@ -907,12 +907,13 @@ SERVING_SLOTS = 16
 SERVING_ARM = f"continuous_{SERVING_SLOTS}_slots"
 
 
-def form_serving(dev, reps, count, rho):
+def form_serving(dev, reps, count, rho, sweep=(0.3, 0.6)):
     """Sort requests with sizes log-uniform in [2^10, 2^24] (uniform uint32
     keys, 8 GB device budget): continuous batching (SERVING_SLOTS slots) against the
     same requests served one at a time in arrival order (1 slot, the plain
     sort per request), at saturation (all submitted at once) and under
-    Poisson arrivals at `rho` x the one-slot service rate."""
+    Poisson arrivals at `rho` x the one-slot service rate; then p50/p99 of
+    both arms at the lighter loads in `sweep`."""
     import numpy as np
     import torch
 
@@ -964,6 +965,11 @@ def form_serving(dev, reps, count, rho):
         res["saturation"][SERVING_ARM].append(run(SERVING_SLOTS, 0.0))
         res["poisson"]["fifo_1_slot"].append(run(1, rate))
         res["poisson"][SERVING_ARM].append(run(SERVING_SLOTS, rate))
+    lighter = {f"{x:g}": {"fifo_1_slot": [], SERVING_ARM: []} for x in sweep}
+    for _ in range(reps):
+        for x in sweep:
+            lighter[f"{x:g}"]["fifo_1_slot"].append(run(1, x * mu))
+            lighter[f"{x:g}"][SERVING_ARM].append(run(SERVING_SLOTS, x * mu))
     clocks = sampler.stop()
 
     def summary(runs):
@@ -971,6 +977,10 @@ def form_serving(dev, reps, count, rho):
             {"max_inflight": max(r["max_inflight"] for r in runs),
              "arena_high_water_gb": max(r["arena_high_water_gb"] for r in runs)}
     out = {ph: {arm: summary(v) for arm, v in d.items()} for ph, d in res.items()}
+    load_sweep = {x: {arm: {"p50_ms": statistics.median(r["p50_ms"] for r in v),
+                            "p99_ms": statistics.median(r["p99_ms"] for r in v),
+                            "p99_spread": _spread([r["p99_ms"] for r in v])}
+                      for arm, v in d.items()} for x, d in lighter.items()}
     sat_f = statistics.median(r["wall_ms"] for r in res["saturation"]["fifo_1_slot"])
     sat_c = statistics.median(r["wall_ms"] for r in res["saturation"][SERVING_ARM])
     p99_f = statistics.median(r["p99_ms"] for r in res["poisson"]["fifo_1_slot"])
@@ -986,6 +996,7 @@ def form_serving(dev, reps, count, rho):
                           "memory free",
             "poisson_rate_per_s": rate, "offered_load": rho,
             "saturation": out["saturation"], "poisson": out["poisson"],
+            "poisson_lighter_loads": load_sweep,
             "speedup": sat_f / sat_c,
             "speedup_meaning": f"saturation wall time, one slot / {SERVING_SLOTS} slots",
             "p50_ms": p50_c, "p99_ms": p99_c, "p99_fifo_ms": p99_f,
