@@ -509,8 +509,12 @@ __host__ __device__ constexpr size_t tile_block_smem(int T) {
 // Tile sort kernel: block b sorts kin[b*T, min((b+1)*T, n)) in place into
 // kout.  kin may equal kout (each block reads its whole tile first).  XF:
 // the instance that applies / undoes key transforms (signed and float keys).
+// The 64-bit key-value 256 x 17 tile is bounded to three blocks per SM (80
+// registers, a 28-byte spill) instead of the two its 98 registers allow:
+// on 2^27 pairs its tile sort takes 2.55 instead of 2.83 ms.  Four blocks
+// (64 registers) spilled 336 bytes and gained nothing.
 template <class K, bool PAIRS, int THREADS, int IPT, bool XF>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, (sizeof(K) == 8 && PAIRS && THREADS == 256 && IPT == 17) ? 3 : 0)
 k_tile_sort(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t n, unsigned int* status, int xf_in,
             int xf_out) {
     constexpr int T = THREADS * IPT;
