@@ -265,11 +265,12 @@ k_seg_large(K* keys, uint32_t* vals, K* tkeys, uint32_t* tvals, const unsigned l
 // Medium segments: more than one on-chip tile, at most kMidSlots tiles of
 // T = THREADS x IPT keys, so one or two merge passes.  Work item it of the
 // tile phase is tile it % kMidSlots of the segment at position
-// it / kMidSlots of the medium list; an item of a merge pass is output block
-// it % S (W keys, S = kMidSlots x T / W) of the segment at position it / S.
-// Slots past the end of a shorter segment are skipped.  A segment's tiles land in the buffer
-// its last pass does not write (keys for two passes, the scratch for one),
-// and each pass ping-pongs to the other, so the last pass writes the keys.
+// it / kMidSlots of the medium list; an item of a merge pass is output
+// block it % S (W keys, S = kMidSlots x T / W) of the segment at position
+// it / S.  Slots past the end of a shorter segment are skipped.  A
+// segment's tiles land in the buffer its last pass does not write (keys for
+// two passes, the scratch for one), and each pass ping-pongs to the other,
+// so the last pass writes the keys.
 __device__ __forceinline__ int mid_passes(size_t len, size_t T) { return len > 2 * T ? 2 : 1; }
 
 // XF: whether the keys take a transform (signed or floating-point keys);
