@@ -30,7 +30,10 @@ BOUNDARY_LENS = [0, 1, 2, 3, 17, 33, 543, 544, 545, 1087, 1088, 1089, 2175, 2176
                  # (q = 4608, 8704, 12800 of T = 16896; 2304, 4352, 6400 of 8448; 1280, 2304, 3328 of 4352)
                  21504, 21505, 55296, 55297, 63488, 63489,
                  10752, 10753, 27648, 27649, 14848, 14849, 31744, 31745,
-                 5632, 5633, 14336, 14337, 6656, 6657, 15360, 7680, 7681, 16384, 16385]
+                 5632, 5633, 14336, 14337, 6656, 6657, 15360, 7680, 7681, 16384, 16385,
+                 # an on-chip segment of at most three quarters of its bucket's shape takes the
+                 # three-quarter shape (32, 64, 128, 256 x 13 and 256, 512 x 25 keys)
+                 416, 417, 832, 833, 1664, 1665, 3328, 3329, 6400, 6401, 12800, 12801]
 
 
 @pytest.fixture(scope="module")
